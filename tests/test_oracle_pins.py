@@ -1,0 +1,309 @@
+"""Pins for the CPU oracle against facts fixed outside the oracle itself.
+
+Each test checks the oracle against something it does not compute the same way:
+a library generator (numpy's Philox), a library sort, exact rational arithmetic,
+a graph library's reachability sets, a 2D dominance count, closed forms for
+chains and antichains, hand-worked fixtures under tests/golden, exact identities,
+and the Myrheim-Meyer ordering fraction of a flat diamond.
+"""
+import itertools
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_03013_gb300 import inputs
+
+SQ6 = math.sqrt(6.0)
+
+
+# ----------------------------------------------------------------- RNG pins
+
+@pytest.mark.parametrize("key", [0, 1, 12345, (7 << 64) | 99, (1 << 128) - 1])
+@pytest.mark.parametrize("ctr", [1, 6, (3 << 64) | 17, (5 << 192) | (9 << 128) | (1 << 64) | 3])
+def test_philox_matches_numpy(key, ctr):
+    # numpy's Philox (4x64, 10 rounds) emits block(counter + 1) first.
+    bg = np.random.Philox(key=key, counter=ctr - 1)
+    want = [int(bg.random_raw()) for _ in range(4)]
+    words = [(ctr >> (64 * w)) & ((1 << 64) - 1) for w in range(4)]
+    kwords = [key & ((1 << 64) - 1), key >> 64]
+    got = [int(x) for x in oracle.philox4x64_10(words, kwords)]
+    assert got == want
+
+
+def test_sprinkle_uses_philox_words_d2():
+    # u, v are the top 53 bits of the first two words of block (e, 0, 0, 0).
+    coords = oracle.sprinkle(2, 5, seed=11, seq=3)
+    for e in range(5):
+        bg = np.random.Philox(key=11 | (3 << 64), counter=e - 1 if e > 0 else (1 << 256) - 1)
+        r = [int(bg.random_raw()) for _ in range(2)]
+        assert coords[2, e] == (r[0] >> 11) / 2.0 ** 53
+        assert coords[3, e] == (r[1] >> 11) / 2.0 ** 53
+
+
+# ------------------------------------------------------------ sprinkle pins
+
+def test_sprinkle_d2_uniform_and_light_cone_coords():
+    from scipy import stats
+    c = oracle.sprinkle(2, 20000, seed=5)
+    t, x, u, v = c
+    assert stats.kstest(u, "uniform").pvalue > 1e-4
+    assert stats.kstest(v, "uniform").pvalue > 1e-4
+    assert np.all((u >= 0) & (u < 1) & (v >= 0) & (v < 1))
+    # t and x are the diamond coordinates: |x| <= t <= 1 - |x|
+    assert np.all(np.abs(x) <= t) and np.all(t <= 1 - np.abs(x) + 1e-15)
+
+
+def test_sprinkle_d4_acceptance_and_marginal():
+    from scipy import stats
+    n = 20000
+    c, att = oracle.sprinkle(4, n, seed=6, with_attempts=True)
+    t, x, y, z = c
+    r = np.sqrt(x * x + y * y + z * z)
+    assert np.all(np.abs(t) + r <= 1.0)
+    # acceptance = vol(diamond) / vol([-1,1]^4) = (2 * pi/3 * 1/4 ... ) = 2*(4pi/3)/4 / 16 = pi/24
+    p = math.pi / 24.0
+    tries = int((att + 1).sum())
+    mean, sd = tries * p, math.sqrt(tries * p * (1 - p))
+    assert abs(n - mean) < 5 * sd
+    # time marginal of a uniform point in |t| + r <= 1: density (3/2)(1-|t|)^3 ... cdf of |t| is 1-(1-a)^4
+    a = np.abs(t)
+    assert stats.kstest(a, lambda q: 1 - (1 - q) ** 4).pvalue > 1e-4
+    # isotropy: the direction of (x,y,z) is uniform, so each component/r is U[-1,1]
+    assert stats.kstest(z / r, "uniform", args=(-1, 2)).pvalue > 1e-4
+
+
+def test_sprinkle_deterministic_and_seq_independent():
+    a = oracle.sprinkle(4, 100, seed=1, seq=0)
+    b = oracle.sprinkle(4, 100, seed=1, seq=0)
+    c = oracle.sprinkle(4, 100, seed=1, seq=1)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    # element e does not depend on N (counter-based)
+    d = oracle.sprinkle(4, 37, seed=1, seq=0)
+    assert np.array_equal(a[:, :37], d)
+
+
+# ---------------------------------------------------------------- sort pins
+
+def test_sort_matches_library_sort_with_ties():
+    rng = np.random.default_rng(0)
+    N = 300
+    coords = np.zeros((4, N))
+    coords[0] = rng.integers(0, 20, N) / 8.0  # many equal times
+    coords[2] = rng.integers(0, 5, N) / 4.0   # and equal u
+    coords[1] = rng.random(N)
+    coords[3] = rng.random(N)
+    for d in (2, 4):
+        _, perm = oracle.sort(d, coords)
+        if d == 2:
+            want = sorted(range(N), key=lambda e: (coords[0, e], coords[2, e], e))
+        else:
+            want = sorted(range(N), key=lambda e: (coords[0, e], e))
+        assert list(perm) == want
+
+
+def test_sort_permutes_all_rows():
+    c = oracle.sprinkle(4, 500, seed=2)
+    s, perm = oracle.sort(4, c)
+    assert np.array_equal(s, c[:, perm])
+    assert np.all(np.diff(s[0]) >= 0)
+
+
+# ---------------------------------------------------------------- link pins
+
+def _exact_related(d, c, i, j):
+    """Exact real-number light-cone test on the stored coordinates (rationals)."""
+    if d == 2:
+        ti, tj = Fraction(c[0, i]), Fraction(c[0, j])
+        xi, xj = Fraction(c[1, i]), Fraction(c[1, j])
+        dt = tj - ti
+        return dt > 0 and dt * dt > (xj - xi) ** 2
+    dt = Fraction(c[0, j]) - Fraction(c[0, i])
+    s = sum((Fraction(c[r, j]) - Fraction(c[r, i])) ** 2 for r in (1, 2, 3))
+    return dt > 0 and dt * dt > s
+
+
+@pytest.mark.parametrize("d", [2, 4])
+def test_link_matches_exact_light_cone(d):
+    c = oracle.sprinkle_sorted(d, 120, seed=7)
+    rel = oracle.link(d, c)
+    for i, j in itertools.combinations(range(120), 2):
+        assert rel[i, j] == _exact_related(d, c, i, j)
+
+
+@pytest.mark.parametrize("d", [2, 4])
+def test_link_symmetric_zero_diagonal_row_and_pair(d):
+    c = oracle.sprinkle_sorted(d, 200, seed=8)
+    rel = oracle.link(d, c)
+    assert np.array_equal(rel, rel.T) and not rel.diagonal().any()
+    for i in (0, 17, 199):
+        assert np.array_equal(oracle.link_row(d, c, i), rel[i])
+    # time order: a later label never precedes an earlier one (Sec. 2.2)
+    for i, j in itertools.combinations(range(200), 2):
+        if rel[i, j]:
+            assert c[0, i] <= c[0, j]
+
+
+@pytest.mark.parametrize("d,frac", [(2, 0.5), (4, 0.1)])
+def test_ordering_fraction_myrheim_meyer(d, frac):
+    # For iid uniform points in a flat diamond each pair is related with probability
+    # f(d) = Gamma(d+1) Gamma(d/2) / (2 Gamma(3d/2)): 1/2 in 1+1, 1/10 in 3+1.
+    f = math.gamma(d + 1) * math.gamma(d / 2) / (2 * math.gamma(3 * d / 2))
+    assert abs(f - frac) < 1e-12
+    N, seeds = 600, range(6)
+    Rs = [oracle.link(d, oracle.sprinkle_sorted(d, N, s)).sum() // 2 for s in seeds]
+    pairs = N * (N - 1) // 2
+    mean = np.mean(Rs) / pairs
+    # pair indicators are positively correlated; 5 binomial sigmas of the mean over
+    # 6 sets times a generous factor 8 for the correlation
+    sd = math.sqrt(frac * (1 - frac) / pairs / len(Rs)) * 8
+    assert abs(mean - frac) < 5 * sd
+
+
+# -------------------------------------------------------------- action pins
+
+def _nx_intervals(rel):
+    import networkx as nx
+    N = rel.shape[0]
+    g = nx.DiGraph()
+    g.add_nodes_from(range(N))
+    for i, j in zip(*np.nonzero(np.triu(rel, 1))):
+        g.add_edge(int(i), int(j))
+    desc = {v: nx.descendants(g, v) for v in range(N)}
+    anc = {v: nx.ancestors(g, v) for v in range(N)}
+    return g, desc, anc
+
+
+@pytest.mark.parametrize("d,N,seed", [(2, 48, 1), (4, 64, 2), (2, 64, 3), (4, 40, 4)])
+def test_action_matches_graph_library_brute_force(d, N, seed):
+    pytest.importorskip("networkx")
+    c = oracle.sprinkle_sorted(d, N, seed)
+    rel = oracle.link(d, c)
+    g, desc, anc = _nx_intervals(rel)
+    hist = np.zeros(max(N, 1), dtype=np.int64)
+    for i, j in g.edges():
+        hist[len(desc[i] & anc[j])] += 1
+    out = oracle.action(rel)
+    assert np.array_equal(out["hist"].astype(np.int64), hist)
+    assert out["R"] == g.number_of_edges()
+    # pair-by-pair entry points agree with the histogram
+    for i, j in list(g.edges())[:50]:
+        m = len(desc[i] & anc[j])
+        assert oracle.interval(rel, i, j) == m
+        assert oracle.interval_coords(d, c, i, j) == m
+
+
+def test_links_equal_transitive_reduction():
+    nx = pytest.importorskip("networkx")
+    for d, seed in ((2, 5), (4, 6)):
+        rel = oracle.link(d, oracle.sprinkle_sorted(d, 150, seed))
+        g, _, _ = _nx_intervals(rel)
+        assert oracle.action(rel)["Nk"][0] == nx.transitive_reduction(g).number_of_edges()
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 9, 64, 65, 130])
+def test_chain_closed_form(N):
+    out = oracle.action(inputs.chain_rel(N))
+    want = np.zeros(max(N, 1), dtype=np.uint64)
+    for k in range(N - 1):
+        want[k] = N - 1 - k  # pairs at distance k+1 along the chain
+    assert np.array_equal(out["hist"], want)
+    assert out["R"] == N * (N - 1) // 2
+    combo2, S2 = oracle.finalize(2, N, out["Nk"])
+    combo4, S4 = oracle.finalize(4, N, out["Nk"])
+    if N >= 4:
+        assert combo2 == N and S2 == 2.0 * N
+    if N >= 5:
+        assert combo4 == N - 1 and abs(S4 - 4 / SQ6 * (N - 1)) <= 1e-12 * abs(S4)
+
+
+@pytest.mark.parametrize("N", [0, 1, 7, 100])
+def test_antichain_closed_form(N):
+    out = oracle.action(inputs.antichain_rel(N))
+    assert out["R"] == 0 and not out["hist"].any()
+    assert oracle.finalize(2, N, out["Nk"]) == (N, 2.0 * N)
+    combo4, S4 = oracle.finalize(4, N, out["Nk"])
+    assert combo4 == N and abs(S4 - 4 / SQ6 * N) <= 1e-12 * max(abs(S4), 1)
+
+
+@pytest.mark.parametrize("name", ["diamond4.txt", "npos6.txt"])
+def test_golden_hand_worked(golden, name):
+    g = golden(name)
+    rel = inputs.rel_from_edges(g["N"], g["rel"])
+    out = oracle.action(rel)
+    assert list(out["Nk"]) == g["Nk"]
+    assert out["R"] == g["R"] and out["sum_m"] == g["sum_m"]
+    combo2, S2 = oracle.finalize(2, g["N"], out["Nk"])
+    combo4, S4 = oracle.finalize(4, g["N"], out["Nk"])
+    assert combo2 == g["combo2"] and combo4 == g["combo4"]
+    assert abs(S2 - g["S2"]) <= 1e-12 * abs(g["S2"])
+    assert abs(S4 - g["S4"]) <= 1e-12 * abs(g["S4"])
+
+
+@pytest.mark.parametrize("d,N,seed", [(2, 300, 1), (4, 400, 2)])
+def test_identities(d, N, seed):
+    rel = oracle.link(d, oracle.sprinkle_sorted(d, N, seed))
+    out = oracle.action(rel)
+    up = np.triu(rel, 1).astype(np.int64)
+    outdeg, indeg = up.sum(1), up.sum(0)
+    ks = np.arange(out["hist"].shape[0], dtype=np.int64)
+    assert int(out["hist"].sum()) == out["R"] == int(up.sum())
+    # sum_k k N_k counts 3-chains i<k<j, i.e. sum over middles of indeg * outdeg
+    assert int((ks * out["hist"].astype(np.int64)).sum()) == out["sum_m"] == int((indeg * outdeg).sum())
+    ii, jj = np.nonzero(up)
+    assert out["W"] == int((jj - ii - 1).sum())
+
+
+def test_2d_dominance_count():
+    # In 1+1 the light-cone sprinkle is a 2D order: m(i,j) is the number of points in
+    # the open rectangle (u_i,u_j) x (v_i,v_j), counted here with a prefix-sum table.
+    d, N = 2, 700
+    c = oracle.sprinkle_sorted(d, N, 9)
+    u, v = c[2], c[3]
+    ru = np.argsort(np.argsort(u))
+    rv = np.argsort(np.argsort(v))
+    grid = np.zeros((N + 1, N + 1), dtype=np.int64)
+    grid[ru + 1, rv + 1] = 1
+    P = grid.cumsum(0).cumsum(1)
+    rel = oracle.link(d, c)
+    hist = np.zeros(N, dtype=np.int64)
+    ii, jj = np.nonzero(np.triu(rel, 1))
+    a0, b0, a1, b1 = ru[ii] + 1, rv[ii] + 1, ru[jj], rv[jj]
+    m = P[a1, b1] - P[a0, b1] - P[a1, b0] + P[a0, b0]
+    np.add.at(hist, m, 1)
+    assert np.array_equal(oracle.action(rel)["hist"].astype(np.int64), hist)
+
+
+def test_2d_three_chain_expectation():
+    # E[# 3-chains] in a random 2D order is C(N,3)/6
+    N, Ns = 400, []
+    for s in range(8):
+        Ns.append(oracle.action(oracle.link(2, oracle.sprinkle_sorted(2, N, 100 + s)))["sum_m"])
+    want = math.comb(N, 3) / 6
+    assert abs(np.mean(Ns) / want - 1) < 0.05
+
+
+def test_rows_partition():
+    rel = oracle.link(4, oracle.sprinkle_sorted(4, 300, 3))
+    full = oracle.action(rel)
+    a = oracle.action(rel, rows=(0, 120))
+    b = oracle.action(rel, rows=(120, 300))
+    assert np.array_equal(a["hist"] + b["hist"], full["hist"])
+    assert a["R"] + b["R"] == full["R"] and a["W"] + b["W"] == full["W"]
+
+
+def test_pack_layout():
+    rel = inputs.random_upper_rel(130, 0.3, 1)
+    w = oracle.pack(rel)
+    assert w.shape == (130, 16)
+    for i in (0, 63, 64, 129):
+        for k in range(130):
+            assert ((int(w[i, k // 64]) >> (k % 64)) & 1) == rel[i, k]
+    assert np.array_equal(w, inputs.pack_rows(rel, 16))
+
+
+def test_finalize_rejects_bad_dimension():
+    with pytest.raises(RuntimeError):
+        oracle.finalize(3, 5, [0, 0, 0, 0])
