@@ -1,0 +1,312 @@
+#!/usr/bin/env python3
+"""Benchmark of the causal-set action path on GB300.
+
+One step is one pass of the whole path over one synthetic set: sprinkle N elements
+into the flat causal diamond, sort them by time, link them into the bit-packed
+causal matrix, count every related pair's interval (N_0..N_3, R, sum m, W) and form
+the action.  The default workload is the d=4 diamond with N=65536 (seed 1): its
+bitmap is 512 MiB, larger than the 129 MB L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  `value` is related-pair interval counts per second
+(R / step time) with the set generated on the device; `e2e` is the same metric
+through the public API from host coordinates (copied in every step) to the host
+result.  `roofline` is the action kernel against the integer-pipe popcount peak;
+`cpu_baseline` is the CPU oracle on a bounded sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "related-pair interval counts/s + p99 latency, served vs plain, bit-exact N_k"
+UNIT = "pairs/s"
+WORKLOAD = dict(d=4, N=65536, seed=1)
+WORKLOAD_NAME = "d=4 flat causal diamond, N=65536, seed 1 (sprinkle+sort+link+action)"
+
+# Popcount peak of the integer pipe: 16 32-bit POPC per SM per clock (CUDA C
+# Programming Guide throughput table), 32 bit-operations each.
+POPC_PER_SM_CLK = 16
+SMS = 152
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def launches_per_step(N: int) -> int:
+    # sprinkle+keys, chunk ranking, merge passes, gather; link; action; finalize
+    passes, w = 0, 1024
+    while w < N:
+        passes += 1
+        w *= 2
+    return 3 + passes + 1 + 2
+
+
+def cpu_baseline(threads: int = 0, rows_per_block: int = 64, blocks: int = 8):
+    """The oracle as it stands on a bounded sample: its link of the full set, then its
+    triple loop over `blocks` stratified blocks of rows."""
+    import numpy as np  # noqa: F401
+
+    import oracle
+    d, N, seed = WORKLOAD["d"], WORKLOAD["N"], WORKLOAD["seed"]
+    c = oracle.sprinkle_sorted(d, N, seed, 0)
+    rel = oracle.link(d, c, threads)
+    pairs, elapsed = 0, 0.0
+    for b in range(blocks):
+        lo = (N * b) // blocks
+        t0 = time.perf_counter()
+        out = oracle.action(rel, threads, rows=(lo, lo + rows_per_block))
+        elapsed += time.perf_counter() - t0
+        pairs += out["R"]
+    cores = threads or os.cpu_count()
+    return {"value": pairs / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{blocks} blocks of {rows_per_block} rows (first elements) spread over the N=65536 "
+                      f"d=4 set; {pairs} related pairs in {elapsed:.2f} s; matrix built by the oracle's link"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    d, N, seed = WORKLOAD["d"], WORKLOAD["N"], WORKLOAD["seed"]
+    c = oracle.sprinkle_sorted(d, N, seed, 0)
+    rel = oracle.link(d, c)
+    times, pairs = [], []
+    nblk = args.warmup + args.steps
+    for k in range(nblk):
+        lo = (N * (k % 8)) // 8
+        t0 = time.perf_counter()
+        out = oracle.action(rel, rows=(lo, lo + 32))
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            pairs.append(out["R"])
+    value = sum(pairs) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME + "; each step the oracle's triple loop over 32 rows",
+                       "d": d, "N": N, "seed": seed},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "per step 32 consecutive first elements, blocks spread over the set"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--method", default="popc", choices=["popc", "tc"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1709_03013_gb300 import csg
+
+    method = csg.POPC if args.method == "popc" else csg.TC
+    d, N, seed = WORKLOAD["d"], WORKLOAD["N"], WORKLOAD["seed"]
+    seq = rank  # replicas: each rank runs its own independent set
+    ctx = csg.Context(local)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        s = ctx.sprinkle(d, N, seed, seq)
+        s.link()
+        r = s.action(method)
+        s.free()
+        return r
+
+    for _ in range(args.warmup):
+        res = step()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timing (inputs are (d, N, seed); the set is generated on the GPU)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        results = [step() for _ in range(args.steps)]
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    R_total = sum(r.R for r in results)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        rt = torch.tensor([R_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(rt)
+        R_total = float(rt.item())
+    value = R_total / (ms / 1e3)
+
+    # ---- action kernel alone (dominant kernel): events around the action call
+    s = ctx.sprinkle(d, N, seed, seq).link()
+    s.action(method)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a0.record(stream)
+    for _ in range(args.steps):
+        ra = s.action(method)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    act_ms = a0.elapsed_time(a1) / args.steps
+    coords_host = s.coords()
+    s.free()
+
+    # ---- end to end through the public API from host coordinates (pinned)
+    pinned = torch.from_numpy(coords_host).pin_memory()
+    host_np = pinned.numpy()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    e_pairs = 0
+    for _ in range(args.steps):
+        se = ctx.set_from_coords(d, host_np)
+        se.link()
+        re_ = se.action(method)
+        se.free()
+        e_pairs += re_.R
+    e1.record(stream)
+    barrier()
+    e_ms = e0.elapsed_time(e1)
+
+    if rank != 0:
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    pk = peaks()
+    clocks = clk.summary()
+    sm_max = (clocks or {}).get("sm_max_mhz") or pk.get("sm_max_mhz") or 2070.0
+    peak_bitops = SMS * POPC_PER_SM_CLK * 32 * sm_max * 1e6
+    achieved = ra.W / (act_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "d": d, "N": N, "seed": seed, "method": args.method,
+                   "l2": "inputs larger than L2 (512 MiB bitmap per step)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "gpu_launches": launches_per_step(N) * args.steps,
+        "result": {"R": ra.R, "Nk": list(ra.Nk), "sum_m": ra.sum_m, "W": ra.W, "S": ra.S},
+        "bitops_per_s": ra.W / (act_ms / 1e3),
+        "action_ms": act_ms,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_bitops, "unit": "bit-ops/s",
+                     "frac": achieved / peak_bitops, "traffic": None,
+                     "peak_basis": f"{SMS} SMs x {POPC_PER_SM_CLK} POPC/clk x 32 bits x {sm_max:.0f} MHz"},
+        "e2e": {"value": e_pairs / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(host_np.nbytes),
+                "d2h_bytes_per_step": 88},
+    }
+    if clocks:
+        line["clocks"] = clocks
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,182 @@
+/*
+ * csg.h -- C ABI of the GB300 causal-set library.
+ *
+ * The library runs the data-parallel path of Cunningham & Krioukov, "Causal Set
+ * Generator and Action Computer" (arXiv:1709.03013) on one GPU:
+ *
+ *   csg_sprinkle  sprinkle N elements into a flat causal diamond and sort them by
+ *                 time (Sec. 2.1; Sec. 2.2 for the time order)
+ *   csg_link      build the symmetric bit-packed causal matrix (Sec. 2.2,
+ *                 "Optimized GPU Linking Algorithm")
+ *   csg_action    count, for every related pair i < j, the elements strictly
+ *                 between them, histogram the counts into N_0..N_3 and form the
+ *                 Benincasa-Dowker action (Sec. 4, Alg. 5; Eq. s_local)
+ *   csg_action_batch, csg_serve_submit / csg_serve_poll
+ *                 the same for many sets at once, and as a request service
+ *
+ * Conventions shared by every call
+ *   - Return value: CSG_OK (0) on success, CSG_PENDING (1) from csg_serve_poll while a
+ *     request is unfinished, a negative CSG_E_* code otherwise.  No C++ exception
+ *     crosses the ABI.  csg_strerror() names a code; csg_last_error() gives the
+ *     message of the last failure on the calling thread.
+ *   - Ownership: a context owns every device allocation it makes; a set handle stays
+ *     valid until csg_set_free (or csg_finalize of its context).  Result structs and
+ *     host buffers are caller-owned.
+ *   - Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     enqueue their kernels on it; calls that return results (csg_action,
+ *     csg_action_batch, exports) synchronise that stream before returning.
+ *   - Bitmap layout: row i of the N x N symmetric matrix is `stride_words` uint64
+ *     words at dev_rows + i*stride_words; entry (i,k) is bit k%64 of word k/64
+ *     (LSB first).  The diagonal is 0, bits k >= N are 0.  Elements are labelled in
+ *     time order, so i < k related means i precedes k (Sec. 2.2).  The library's own
+ *     sets use stride_words = ceil(N/64) rounded up to a multiple of 16 (128 bytes).
+ *   - Coordinates: [4][N] doubles on the device, rows (t, x, u, v) for d=2 and
+ *     (t, x, y, z) for d=4, sorted by time.
+ */
+#ifndef CSG_H
+#define CSG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CSG_OK 0
+#define CSG_PENDING 1
+#define CSG_E_INVAL (-1)   /* bad argument: d not 2/4, N out of range, NULL pointer ... */
+#define CSG_E_NOMEM (-2)   /* device allocation failed or over the context's HBM budget */
+#define CSG_E_CUDA (-3)    /* a CUDA runtime call or kernel launch failed */
+#define CSG_E_TIMEOUT (-4) /* a bounded wait expired (device-side or in csg_serve_poll) */
+#define CSG_E_BUSY (-5)    /* the service queue is full */
+#define CSG_E_REJECT (-6)  /* the d=4 sprinkle hit its 256-attempt rejection cap */
+#define CSG_E_NOTFOUND (-7) /* unknown or already collected ticket */
+#define CSG_E_CANCELLED (-8) /* request cancelled before it ran */
+
+/* Methods for the interval counts (csg_action, csg_action_batch). */
+#define CSG_POPC 0 /* AND + popcount of packed row words (Alg. 5 restated for the GPU) */
+#define CSG_TC 1   /* the same counts as a masked 0/1 matrix product on tensor cores */
+
+/* Largest N a set may have. */
+#define CSG_MAX_N (1 << 18)
+
+typedef struct csg_ctx csg_ctx; /* opaque, library-owned */
+typedef struct csg_set csg_set; /* opaque, library-owned */
+
+/* Result of one action computation.
+ *   R      number of related pairs i < j
+ *   Nk[k]  number of related pairs with exactly k elements strictly between them
+ *          (the paper's 1-based n_{k+1}; Sec. 1.2, Alg. 5)
+ *   sum_m  sum over related pairs of the interval size m
+ *   W      sum over related pairs of (j - i - 1): candidate bits inspected, the
+ *          algorithmic work of Alg. 5 in bit operations
+ *   combo  d=2: N - 2N0 + 4N1 - 2N2 (S = 2*combo, Eq. s_local)
+ *          d=4: N - N0 + 9N1 - 16N2 + 8N3 (S = 4/sqrt(6)*combo, the 3+1 BD action)
+ *   S      the action, formed once in double from the exact integer combo
+ *   status CSG_OK or the error of this set (batch and serve paths) */
+typedef struct {
+    int32_t d;
+    int32_t status;
+    int64_t N;
+    uint64_t R;
+    uint64_t Nk[4];
+    uint64_t sum_m;
+    uint64_t W;
+    int64_t combo;
+    double S;
+} csg_result;
+
+/* Create a context on `device` that may hold at most hbm_budget_bytes of set
+ * memory (0 = no limit).  *out receives the handle. */
+int csg_init(int device, size_t hbm_budget_bytes, csg_ctx **out);
+
+/* Stop the service thread (if any), free every set and all device memory. */
+void csg_finalize(csg_ctx *ctx);
+
+const char *csg_strerror(int code);
+const char *csg_last_error(void);
+
+/* Sprinkle N elements into the flat causal diamond of dimension d (2 or 4) and
+ * sort them by time (Secs. 2.1-2.2).  Element e draws Philox4x64-10 blocks with
+ * counter (e, attempt, 0, 0) and key (seed, seq):
+ *   d=2: u, v = top 53 bits of words 0, 1 of attempt 0 scaled by 2^-53;
+ *        t = (u+v)/2, x = (v-u)/2.
+ *   d=4: (t,x,y,z) = 2U-1 from the four words; the first attempt with
+ *        |t| + sqrt((x*x + y*y) + z*z) <= 1 is kept (at most 256, else CSG_E_REJECT).
+ * Sorting key: (t, u, e) for d=2, (t, e) for d=4.  1 <= N <= CSG_MAX_N.
+ * The new set has coordinates but no bitmap until csg_link. */
+int csg_sprinkle(csg_ctx *ctx, int d, int64_t N, uint64_t seed, uint64_t seq, void *stream,
+                 csg_set **out);
+
+/* Make a set from host coordinates [4][N] (layout above, any order): copies them
+ * to the device and sorts them by time like csg_sprinkle. */
+int csg_set_from_coords(csg_ctx *ctx, int d, int64_t N, const double *host_coords,
+                        void *stream, csg_set **out);
+
+/* Build the symmetric bit-packed causal matrix of a sprinkled set (Sec. 2.2):
+ *   d=2: i < k related iff u_i < u_k and v_i < v_k
+ *   d=4: i < k related iff t_k > t_i and dt*dt > (dx*dx + dy*dy) + dz*dz in IEEE
+ *        double without fused multiply-add (decided exactly; an fp32 screen with a
+ *        proven error margin settles most pairs first).
+ * Every row word up to the stride, padding included, is written. */
+int csg_link(csg_ctx *ctx, csg_set *set, void *stream);
+
+/* Wrap a caller-built bitmap (any time-ordered causal matrix, Sec. 1.3: the action
+ * uses the adjacency matrix only).  dev_rows is copied into library memory with
+ * the library's stride; stride_words >= ceil(N/64). d (2 or 4) picks the action's
+ * formula.  The caller keeps ownership of dev_rows. */
+int csg_set_from_bitmap(csg_ctx *ctx, int d, int64_t N, const uint64_t *dev_rows,
+                        int64_t stride_words, void *stream, csg_set **out);
+
+/* Interval abundances and action of one set (Alg. 5; Eq. s_local).  method is
+ * CSG_POPC or CSG_TC.  Synchronises `stream`, then fills *out. */
+int csg_action(csg_ctx *ctx, csg_set *set, int method, csg_result *out, void *stream);
+
+/* The same restricted to first elements i in [row_lo, row_hi): counts only pairs
+ * whose earlier element lies in the range (used to check sampled rows). */
+int csg_action_rows(csg_ctx *ctx, csg_set *set, int method, int64_t row_lo, int64_t row_hi,
+                    csg_result *out, void *stream);
+
+/* Full interval-size histogram: dev_hist[m] (m < nbins, device uint64 array owned by
+ * the caller) receives the number of related pairs with m interior elements; bins
+ * m >= nbins are not recorded.  Fills *out like csg_action. */
+int csg_action_hist(csg_ctx *ctx, csg_set *set, uint64_t *dev_hist, int64_t nbins,
+                    csg_result *out, void *stream);
+
+/* Actions of n sets in one pass: all sets' work in one persistent launch over a
+ * queue of (set, row group) items, longest first.  out[n] is filled in order. */
+int csg_action_batch(csg_ctx *ctx, csg_set *const *sets, int n, int method, csg_result *out,
+                     void *stream);
+
+/* Sprinkle + link + action for n (d, N, seed, seq) specs at once, with every step
+ * batched across the sets; the sets are freed before returning. */
+int csg_run_batch(csg_ctx *ctx, int n, const int32_t *d, const int64_t *N, const uint64_t *seed,
+                  const uint64_t *seq, int method, csg_result *out, void *stream);
+
+/* Request service (continuous batching).  submit queues a (d, N, seed, seq) request
+ * without blocking and returns a ticket; a worker thread admits queued requests
+ * while their bitmaps (N*N/8 bytes each) fit the context's budget, runs sprinkle,
+ * link and action for every admitted request in shared launches, and retires them.
+ * poll waits up to timeout_ms (0 = no wait, <0 = forever) and returns CSG_OK with
+ * *out filled, CSG_PENDING, or an error; a collected ticket is forgotten. */
+int csg_serve_submit(csg_ctx *ctx, int d, int64_t N, uint64_t seed, uint64_t seq,
+                     uint64_t *ticket);
+int csg_serve_poll(csg_ctx *ctx, uint64_t ticket, csg_result *out, int timeout_ms);
+int csg_serve_cancel(csg_ctx *ctx, uint64_t ticket);
+
+/* Copy a set's sorted coordinates ([4][N] doubles) or bitmap (N*stride words) to
+ * host memory; cap is the host buffer's capacity in elements. */
+int csg_export_coords(csg_set *set, double *host, size_t cap_doubles);
+int csg_export_bitmap(csg_set *set, uint64_t *host, size_t cap_words);
+
+/* Shape and device pointers of a set (pointers stay owned by the library). */
+int csg_set_info(const csg_set *set, int *d, int64_t *N, int64_t *stride_words,
+                 const uint64_t **dev_rows, const double **dev_coords);
+
+void csg_set_free(csg_set *set);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSG_H */

@@ -1,0 +1,272 @@
+"""Thin ctypes binding of the C ABI in include/csg.h (argument marshalling only).
+
+Every step of the path runs in the CUDA library ``libcsg.so``; this module only
+loads it, converts arguments and results, and raises on error codes.  There is
+no CPU fallback: importing the binding fails loudly when the library is missing.
+Streams are taken from PyTorch when it is available (``torch.cuda.current_stream``),
+which is the only role PyTorch plays here besides device memory.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcsg.so")
+
+OK, PENDING = 0, 1
+E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY, E_REJECT, E_NOTFOUND, E_CANCELLED = range(-1, -9, -1)
+POPC, TC = 0, 1
+MAX_N = 1 << 18
+
+
+class CsgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("status", ctypes.c_int32), ("N", ctypes.c_int64),
+                ("R", ctypes.c_uint64), ("Nk", ctypes.c_uint64 * 4), ("sum_m", ctypes.c_uint64),
+                ("W", ctypes.c_uint64), ("combo", ctypes.c_int64), ("S", ctypes.c_double)]
+
+
+@dataclass
+class Result:
+    d: int
+    N: int
+    R: int
+    Nk: tuple
+    sum_m: int
+    W: int
+    combo: int
+    S: float
+    status: int = 0
+
+    @staticmethod
+    def of(r: _Result) -> "Result":
+        return Result(d=r.d, N=r.N, R=r.R, Nk=tuple(int(x) for x in r.Nk), sum_m=r.sum_m, W=r.W,
+                      combo=r.combo, S=r.S, status=r.status)
+
+
+EXPORTS = [
+    "csg_init", "csg_finalize", "csg_strerror", "csg_last_error", "csg_sprinkle",
+    "csg_set_from_coords", "csg_link", "csg_set_from_bitmap", "csg_action", "csg_action_rows",
+    "csg_action_hist", "csg_action_batch", "csg_run_batch", "csg_serve_submit", "csg_serve_poll",
+    "csg_serve_cancel", "csg_export_coords", "csg_export_bitmap", "csg_set_info", "csg_set_free",
+]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcsg.so and declare its signatures.  Raises if the library is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -c \"import __graft_entry__ as g; "
+                          f"g.build()\"` (there is no CPU fallback)")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, u64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    R = ctypes.POINTER(_Result)
+    sig = {
+        "csg_init": (i32, [i32, sz, pp]),
+        "csg_finalize": (None, [vp]),
+        "csg_strerror": (ctypes.c_char_p, [i32]),
+        "csg_last_error": (ctypes.c_char_p, []),
+        "csg_sprinkle": (i32, [vp, i32, i64, u64, u64, vp, pp]),
+        "csg_set_from_coords": (i32, [vp, i32, i64, vp, vp, pp]),
+        "csg_link": (i32, [vp, vp, vp]),
+        "csg_set_from_bitmap": (i32, [vp, i32, i64, vp, i64, vp, pp]),
+        "csg_action": (i32, [vp, vp, i32, R, vp]),
+        "csg_action_rows": (i32, [vp, vp, i32, i64, i64, R, vp]),
+        "csg_action_hist": (i32, [vp, vp, vp, i64, R, vp]),
+        "csg_action_batch": (i32, [vp, pp, i32, i32, R, vp]),
+        "csg_run_batch": (i32, [vp, i32, vp, vp, vp, vp, i32, R, vp]),
+        "csg_serve_submit": (i32, [vp, i32, i64, u64, u64, ctypes.POINTER(u64)]),
+        "csg_serve_poll": (i32, [vp, u64, R, i32]),
+        "csg_serve_cancel": (i32, [vp, u64]),
+        "csg_export_coords": (i32, [vp, vp, sz]),
+        "csg_export_bitmap": (i32, [vp, vp, sz]),
+        "csg_set_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i64), pp, pp]),
+        "csg_set_free": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc < 0:
+        msg = load().csg_last_error().decode(errors="replace")
+        raise CsgError(rc, f"{what}: {load().csg_strerror(rc).decode()}: {msg}")
+    return rc
+
+
+def current_stream() -> int:
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(current_stream())
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class CausalSet:
+    """A set handle owned by a Context (coordinates and bitmap live on the device)."""
+
+    def __init__(self, ctx: "Context", handle: int):
+        self.ctx = ctx
+        self.handle = ctypes.c_void_p(handle)
+
+    def info(self):
+        d, N, stride = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        rows, coords = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(load().csg_set_info(self.handle, ctypes.byref(d), ctypes.byref(N), ctypes.byref(stride),
+                                   ctypes.byref(rows), ctypes.byref(coords)), "csg_set_info")
+        return dict(d=d.value, N=N.value, stride=stride.value, rows_ptr=rows.value,
+                    coords_ptr=coords.value)
+
+    @property
+    def N(self):
+        return self.info()["N"]
+
+    def link(self, stream=None):
+        _check(load().csg_link(self.ctx.handle, self.handle, _stream(stream)), "csg_link")
+        return self
+
+    def action(self, method: int = POPC, stream=None) -> Result:
+        r = _Result()
+        _check(load().csg_action(self.ctx.handle, self.handle, method, ctypes.byref(r), _stream(stream)),
+               "csg_action")
+        return Result.of(r)
+
+    def action_rows(self, lo: int, hi: int, method: int = POPC, stream=None) -> Result:
+        r = _Result()
+        _check(load().csg_action_rows(self.ctx.handle, self.handle, method, lo, hi, ctypes.byref(r),
+                                      _stream(stream)), "csg_action_rows")
+        return Result.of(r)
+
+    def action_hist(self, dev_hist_ptr: int, nbins: int, stream=None) -> Result:
+        r = _Result()
+        _check(load().csg_action_hist(self.ctx.handle, self.handle, ctypes.c_void_p(dev_hist_ptr), nbins,
+                                      ctypes.byref(r), _stream(stream)), "csg_action_hist")
+        return Result.of(r)
+
+    def coords(self) -> np.ndarray:
+        N = self.N
+        out = np.zeros((4, N), dtype=np.float64)
+        _check(load().csg_export_coords(self.handle, out.ctypes.data_as(ctypes.c_void_p), out.size),
+               "csg_export_coords")
+        return out
+
+    def bitmap(self) -> np.ndarray:
+        inf = self.info()
+        out = np.zeros((inf["N"], inf["stride"]), dtype=np.uint64)
+        _check(load().csg_export_bitmap(self.handle, out.ctypes.data_as(ctypes.c_void_p), out.size),
+               "csg_export_bitmap")
+        return out
+
+    def free(self):
+        if self.handle.value:
+            load().csg_set_free(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+
+class Context:
+    """A device context with an optional HBM budget for set memory (0 = unlimited)."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0):
+        h = ctypes.c_void_p()
+        _check(load().csg_init(device, budget_bytes, ctypes.byref(h)), "csg_init")
+        self.handle = h
+
+    def close(self):
+        if self.handle.value:
+            load().csg_finalize(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def sprinkle(self, d: int, N: int, seed: int, seq: int = 0, stream=None) -> CausalSet:
+        h = ctypes.c_void_p()
+        _check(load().csg_sprinkle(self.handle, d, N, seed, seq, _stream(stream), ctypes.byref(h)),
+               "csg_sprinkle")
+        return CausalSet(self, h.value)
+
+    def set_from_coords(self, d: int, coords: np.ndarray, stream=None) -> CausalSet:
+        c = np.ascontiguousarray(coords, dtype=np.float64)
+        if c.ndim != 2 or c.shape[0] != 4:
+            raise ValueError("coords must be [4, N]")
+        h = ctypes.c_void_p()
+        _check(load().csg_set_from_coords(self.handle, d, c.shape[1], c.ctypes.data_as(ctypes.c_void_p),
+                                          _stream(stream), ctypes.byref(h)), "csg_set_from_coords")
+        return CausalSet(self, h.value)
+
+    def set_from_bitmap(self, d: int, N: int, dev_rows_ptr: int, stride_words: int,
+                        stream=None) -> CausalSet:
+        h = ctypes.c_void_p()
+        _check(load().csg_set_from_bitmap(self.handle, d, N, ctypes.c_void_p(dev_rows_ptr), stride_words,
+                                          _stream(stream), ctypes.byref(h)), "csg_set_from_bitmap")
+        return CausalSet(self, h.value)
+
+    def action_batch(self, sets, method: int = POPC, stream=None) -> list[Result]:
+        n = len(sets)
+        arr = (ctypes.c_void_p * max(n, 1))(*[s.handle.value for s in sets])
+        res = (_Result * max(n, 1))()
+        _check(load().csg_action_batch(self.handle, arr, n, method, res, _stream(stream)),
+               "csg_action_batch")
+        return [Result.of(res[k]) for k in range(n)]
+
+    def run_batch(self, specs, method: int = POPC, stream=None) -> list[Result]:
+        """specs: iterable of (d, N, seed, seq)."""
+        specs = list(specs)
+        n = len(specs)
+        d = np.array([s[0] for s in specs], dtype=np.int32)
+        N = np.array([s[1] for s in specs], dtype=np.int64)
+        seed = np.array([s[2] for s in specs], dtype=np.uint64)
+        seq = np.array([s[3] for s in specs], dtype=np.uint64)
+        res = (_Result * max(n, 1))()
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(load().csg_run_batch(self.handle, n, p(d), p(N), p(seed), p(seq), method, res,
+                                    _stream(stream)), "csg_run_batch")
+        return [Result.of(res[k]) for k in range(n)]
+
+    def serve_submit(self, d: int, N: int, seed: int, seq: int = 0) -> int:
+        t = ctypes.c_uint64()
+        _check(load().csg_serve_submit(self.handle, d, N, seed, seq, ctypes.byref(t)), "csg_serve_submit")
+        return t.value
+
+    def serve_poll(self, ticket: int, timeout_ms: int = -1):
+        """Returns a Result, or None while the request is pending."""
+        r = _Result()
+        rc = load().csg_serve_poll(self.handle, ticket, ctypes.byref(r), timeout_ms)
+        if rc == PENDING:
+            return None
+        _check(rc, "csg_serve_poll")
+        return Result.of(r)
+
+    def serve_cancel(self, ticket: int) -> int:
+        return load().csg_serve_cancel(self.handle, ticket)

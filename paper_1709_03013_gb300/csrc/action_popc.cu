@@ -1,0 +1,281 @@
+// Interval abundances by AND + popcount of packed row words (Sec. 4.3, Alg. 5,
+// restated for the GPU).
+//
+// For a related pair i < j of time-ordered elements, the elements strictly between
+// them are the k with i < k < j set in both row i (future of i) and row j (past of
+// j), so m(i,j) = popcount(row_i AND row_j) over bits i < k < j (Fig. 2).
+//
+// Work decomposition: a work item is a group of G consecutive rows I = [i0, i0+G)
+// (G divides 64, so the group sits inside one 64-bit word of every row).  The CTA
+// bulk-copies the group's rows, from the group's word to the end, into shared
+// memory with TMA and clears every bit k <= i of row i, so each staged row holds
+// only the future of its element.  Warps then sweep the later elements j in runs
+// of 32: one load of word w0 of each row j gives the G-bit mask of group rows
+// related to j, unrelated j are skipped at once (Alg. 5 skips unrelated pairs),
+// and for every j with a nonempty mask the warp streams row j's words up to j
+// (coalesced) and ANDs each with the staged row of every related i in the mask.
+// One read of a word of row j thus serves all related rows of the group.
+//
+// The lanes' partial counts of a pair are summed with warp shuffles; the pair's m
+// goes into per-lane counters (N_0..N_3, R, sum m, W) flushed with 64-bit atomics,
+// and optionally into a full histogram in global memory.  Work items come from an
+// atomic queue (persistent CTAs), in ascending i0, which is roughly longest first.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "csg_internal.cuh"
+#include "ptx.cuh"
+
+namespace csg {
+namespace {
+
+constexpr int kWarps = 16;
+constexpr int kThreads = kWarps * 32;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s for a bulk copy to land
+
+struct Smem {
+    uint64_t bar;
+    int item;
+    int stop;
+};
+
+template <int G>
+__global__ void __launch_bounds__(kThreads, 1)
+action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict__ items,
+                   int n_items, int pitch, unsigned int *__restrict__ queue,
+                   unsigned long long *__restrict__ hist, long long nbins) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem *ctl = reinterpret_cast<Smem *>(smem_raw);
+    uint64_t *A = reinterpret_cast<uint64_t *>(smem_raw + 128);  // G rows x pitch words
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(&ctl->bar, 1);
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+
+    uint32_t phase = 0;
+    for (;;) {
+        if (threadIdx.x == 0) ctl->item = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int k = ctl->item;
+        if (k >= n_items) break;
+        const WorkItem it = items[k];
+        const SetDesc S = sets[it.set];
+        const int64_t N = S.N, stride = S.stride, i0 = it.i0;
+        const uint64_t *__restrict__ rows = S.rows;
+        const int64_t w0 = i0 >> 6;
+        const int64_t w0a = w0 & ~int64_t(1);
+        const int64_t wN = (N + 63) >> 6;
+        const int nwa = (int)(((wN - w0a) + 1) & ~int64_t(1));
+        // rows of the group that are counted
+        uint32_t gmask = 0;
+#pragma unroll
+        for (int r = 0; r < G; ++r) {
+            const int64_t i = i0 + r;
+            if (i < N && i >= S.row_lo && i < S.row_hi) gmask |= 1u << r;
+        }
+        if (gmask == 0) {
+            __syncthreads();
+            continue;
+        }
+
+        // ---- stage the group's rows with bulk copies
+        if (threadIdx.x == 0) {
+            ptx::fence_proxy_async_smem();
+            const uint32_t bytes = (uint32_t)nwa * 8u;
+            ptx::mbar_arrive_expect_tx(&ctl->bar, bytes * (uint32_t)__popc(gmask));
+            for (int r = 0; r < G; ++r)
+                if (gmask >> r & 1u)
+                    ptx::bulk_g2s(A + (size_t)r * pitch, rows + (i0 + r) * stride + w0a, bytes,
+                                  &ctl->bar);
+        }
+        const bool landed = ptx::mbar_wait_bounded(&ctl->bar, phase, kWaitLimitNs);
+        if (__syncthreads_or(!landed)) {
+            // a copy did not land in time: record it, keep the CTA alive until the
+            // copy lands (bounded again), then stop
+            if (threadIdx.x == 0) {
+                atomicExch(&S.counters[CNT_ERR], 1ull);
+                ptx::mbar_wait_bounded(&ctl->bar, phase, kWaitLimitNs);
+            }
+            __syncthreads();
+            break;
+        }
+        phase ^= 1u;
+        // keep only the future of each row: clear bits k <= i
+        const int lead = (int)(w0 - w0a);  // 0 or 1 words before the group's word
+        if (threadIdx.x < G && (gmask >> threadIdx.x & 1u)) {
+            const int r = threadIdx.x;
+            const int b = (int)((i0 + r) & 63);
+            uint64_t *a = A + (size_t)r * pitch;
+            if (lead) a[0] = 0;
+            a[lead] &= ~((2ull << b) - 1ull);  // b == 63 clears the whole word
+        }
+        __syncthreads();
+
+        // ---- sweep later elements j in runs of 32 per warp
+        unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, cR = 0, cM = 0, cW = 0;
+        const int gshift = (int)(i0 & 63);
+        const uint32_t Gbits = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
+        for (int64_t jb = i0 + 1 + 32 * (int64_t)warp; jb < N; jb += 32 * kWarps) {
+            const int64_t jl = jb + lane;
+            uint32_t my = 0;
+            if (jl < N) {
+                const uint64_t word = __ldg(rows + jl * stride + w0);
+                my = (uint32_t)(word >> gshift) & Gbits & gmask;
+                const int64_t off = jl - i0;  // elements of the group after j do not precede it
+                if (off < G) my &= (1u << off) - 1u;
+            }
+            uint32_t todo = __ballot_sync(0xffffffffu, my != 0);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const uint32_t mask = __shfl_sync(0xffffffffu, my, src);
+                const int64_t j = jb + src;
+                const int wj = (int)((j >> 6) - w0a);     // last word, relative
+                const uint64_t lastmask = (1ull << (j & 63)) - 1ull;  // bits k < j
+                const uint64_t *__restrict__ bj = rows + j * stride + w0a;
+                uint32_t acc[G];
+#pragma unroll
+                for (int r = 0; r < G; ++r) acc[r] = 0;
+                int w = lane;
+                for (; w + 32 <= wj; w += 64) {
+                    const uint64_t b0 = __ldg(bj + w);
+                    const uint64_t b1 = __ldg(bj + w + 32);  // may be the last word
+                    const uint64_t b1m = (w + 32 == wj) ? (b1 & lastmask) : b1;
+#pragma unroll
+                    for (int r = 0; r < G; ++r) {
+                        if (mask >> r & 1u) {
+                            const uint64_t *a = A + (size_t)r * pitch;
+                            acc[r] += __popcll(a[w] & b0) + __popcll(a[w + 32] & b1m);
+                        }
+                    }
+                }
+                if (w <= wj) {
+                    uint64_t b0 = __ldg(bj + w);
+                    if (w == wj) b0 &= lastmask;
+#pragma unroll
+                    for (int r = 0; r < G; ++r)
+                        if (mask >> r & 1u) acc[r] += __popcll(A[(size_t)r * pitch + w] & b0);
+                }
+#pragma unroll
+                for (int r = 0; r < G; ++r) {
+                    if (mask >> r & 1u) {
+                        uint32_t m = acc[r];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+                        if (lane == 0) {
+                            c0 += (m == 0);
+                            c1 += (m == 1);
+                            c2 += (m == 2);
+                            c3 += (m == 3);
+                            cR += 1;
+                            cM += m;
+                            cW += (unsigned long long)(j - (i0 + r) - 1);
+                            if (hist != nullptr && (long long)m < nbins) atomicAdd(&hist[m], 1ull);
+                        }
+                    }
+                }
+            }
+        }
+        if (lane == 0 && cR != 0) {
+            unsigned long long *cnt = S.counters;
+            if (c0) atomicAdd(&cnt[CNT_N0], c0);
+            if (c1) atomicAdd(&cnt[CNT_N1], c1);
+            if (c2) atomicAdd(&cnt[CNT_N2], c2);
+            if (c3) atomicAdd(&cnt[CNT_N3], c3);
+            atomicAdd(&cnt[CNT_R], cR);
+            atomicAdd(&cnt[CNT_SUM_M], cM);
+            atomicAdd(&cnt[CNT_W], cW);
+        }
+        __syncthreads();  // the staged rows are reused by the next item
+    }
+}
+
+template <int G>
+int launch_g(const SetDesc *d_sets, const WorkItem *d_items, int n_items, int pitch,
+             unsigned int *queue, unsigned long long *hist, int64_t nbins, cudaStream_t st) {
+    const size_t smem = 128 + (size_t)G * pitch * sizeof(uint64_t);
+    auto kern = action_popc_kernel<G>;
+    CSG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    CSG_CUDA_TRY(cudaGetDevice(&dev));
+    CSG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CSG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+    if (per_sm < 1) {
+        set_error("action_popc: %zu bytes of shared memory per CTA do not fit", smem);
+        return CSG_E_INVAL;
+    }
+    int grid = sms * per_sm;
+    if (grid > n_items) grid = n_items;
+    kern<<<grid, kThreads, smem, st>>>(d_sets, d_items, n_items, pitch, queue, hist,
+                                       (long long)nbins);
+    CSG_CUDA_TRY(cudaGetLastError());
+    return CSG_OK;
+}
+
+}  // namespace
+
+// Shared-memory budget for the staged rows of one CTA.
+static constexpr size_t kRowBudget = 200 * 1024;
+
+int action_popc(const SetDesc *sets, int n_sets, cudaStream_t st, unsigned long long *dev_hist,
+                int64_t nbins) {
+    if (n_sets <= 0) return CSG_OK;
+    int64_t maxw = 0;
+    for (int s = 0; s < n_sets; ++s) {
+        int64_t w = (sets[s].N + 63) / 64 + 2;
+        if (w > maxw) maxw = w;
+    }
+    const int pitch = (int)((maxw + 1) & ~int64_t(1));
+    int G = 16;
+    while (G > 1 && (size_t)G * pitch * 8 > kRowBudget) G >>= 1;
+    if ((size_t)G * pitch * 8 > kRowBudget) {
+        set_error("action_popc: rows of %lld words do not fit shared memory", (long long)maxw);
+        return CSG_E_INVAL;
+    }
+    // work items: groups of G rows over each set's row range, sets in order
+    std::vector<WorkItem> items;
+    for (int s = 0; s < n_sets; ++s) {
+        int64_t lo = sets[s].row_lo, hi = sets[s].row_hi;
+        if (hi > sets[s].N) hi = sets[s].N;
+        if (lo < 0) lo = 0;
+        for (int64_t i0 = lo / G * G; i0 < hi; i0 += G) items.push_back(WorkItem{s, 0, i0});
+    }
+    if (items.empty()) return CSG_OK;
+    if (items.size() > 0x7fffffff) {
+        set_error("action_popc: too many work items");
+        return CSG_E_INVAL;
+    }
+    const int n_items = (int)items.size();
+    // longest first: an item's work grows with the number of later rows
+    std::stable_sort(items.begin(), items.end(), [&](const WorkItem &a, const WorkItem &b) {
+        const int64_t ra = sets[a.set].N - a.i0, rb = sets[b.set].N - b.i0;
+        return ra * (sets[a.set].N) > rb * (sets[b.set].N);
+    });
+    char *scratch = nullptr;
+    const size_t bytes = 256 + n_sets * sizeof(SetDesc) + items.size() * sizeof(WorkItem);
+    CSG_CUDA_TRY(cudaMallocAsync((void **)&scratch, bytes, st));
+    unsigned int *queue = reinterpret_cast<unsigned int *>(scratch);
+    SetDesc *d_sets = reinterpret_cast<SetDesc *>(scratch + 256);
+    WorkItem *d_items = reinterpret_cast<WorkItem *>(scratch + 256 + n_sets * sizeof(SetDesc));
+    cudaMemsetAsync(queue, 0, 256, st);
+    cudaMemcpyAsync(d_sets, sets, n_sets * sizeof(SetDesc), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                    st);
+    int rc;
+    switch (G) {
+        case 16: rc = launch_g<16>(d_sets, d_items, n_items, pitch, queue, dev_hist, nbins, st); break;
+        case 8: rc = launch_g<8>(d_sets, d_items, n_items, pitch, queue, dev_hist, nbins, st); break;
+        case 4: rc = launch_g<4>(d_sets, d_items, n_items, pitch, queue, dev_hist, nbins, st); break;
+        case 2: rc = launch_g<2>(d_sets, d_items, n_items, pitch, queue, dev_hist, nbins, st); break;
+        default: rc = launch_g<1>(d_sets, d_items, n_items, pitch, queue, dev_hist, nbins, st); break;
+    }
+    cudaFreeAsync(scratch, st);
+    return rc;
+}
+
+}  // namespace csg

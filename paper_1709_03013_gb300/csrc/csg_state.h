@@ -1,0 +1,55 @@
+// Host-side state behind the opaque handles of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <set>
+
+#include "../../include/csg.h"
+
+struct csg_set {
+    csg_ctx *ctx = nullptr;
+    int d = 0;
+    int64_t N = 0;
+    int64_t stride = 0;          // words per bitmap row
+    double *coords = nullptr;    // [4][N] sorted coordinates (device)
+    uint64_t *rows = nullptr;    // N x stride bitmap words (device)
+    size_t bytes = 0;            // charged against the context budget
+    bool linked = false;
+    bool from_bitmap = false;
+    double coord_scale = 1.0;    // max(1, max |coordinate|)
+};
+
+namespace csg {
+struct ServeState;
+}
+
+struct csg_ctx {
+    int device = 0;
+    size_t budget = 0;  // 0 = unlimited
+    size_t used = 0;
+    std::mutex mu;      // guards used and sets
+    std::set<csg_set *> sets;
+    std::mutex serve_mu;
+    csg::ServeState *serve = nullptr;
+};
+
+namespace csg {
+
+int alloc_set(csg_ctx *ctx, int d, int64_t N, csg_set **out);
+void free_set(csg_set *s);
+
+// Action for n linked sets; writes n host results and synchronises st.
+int run_actions(csg_set *const *sets, int n, int method, int64_t row_lo, int64_t row_hi,
+                unsigned long long *dev_hist, int64_t nbins, csg_result *out, cudaStream_t st);
+
+// Sprinkle + sort + link + action for n allocated sets with the given seeds, all
+// steps batched across the sets; synchronises st.
+int run_pipeline(csg_set *const *sets, int n, const uint64_t *seed, const uint64_t *seq, int method,
+                 csg_result *out, cudaStream_t st);
+
+void serve_shutdown(csg_ctx *ctx);
+
+}  // namespace csg

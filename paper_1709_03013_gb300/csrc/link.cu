@@ -1,0 +1,275 @@
+// Linking: the symmetric bit-packed causal matrix of sorted coordinates (Sec. 2.2,
+// "Optimized GPU Linking Algorithm": tiles of the adjacency matrix, coordinates
+// staged in shared memory, dense output).
+//
+// A CTA owns a 256 x 256 tile (row block bi <= column block bj) of the upper
+// triangle.  Thread r evaluates the 256 pairs (R+r, K+c) with column coordinates
+// read from shared memory (broadcast) and keeps the four row words in registers.
+// The lower triangle is the same tile transposed: a warp ballot over its 32 rows
+// per column gives 32 bits of the mirrored row, staged in shared memory and
+// written as 32-byte row segments.  Column blocks run to the row stride, so every
+// word of every row -- padding included -- is written exactly once and no memset
+// is needed.
+//
+// d=4 decisions are the exact IEEE double ones (t_k > t_i and dt*dt > (dx*dx +
+// dy*dy) + dz*dz, separately rounded).  A float screen settles almost every pair
+// first: with coordinates in [-1, 1] the float value of dt^2 - |dx|^2 is within
+// 100 * 2^-24 (< 6e-6) of the real value, and the double expression within
+// 40 * 2^-53 of it, so a float difference beyond +-1e-5 fixes the double decision.
+// Pairs inside the margin are decided in double.  Every error term scales with the
+// square of the coordinate range, so sets whose coordinates exceed 1 in magnitude
+// use the margin 1e-5 * max|coordinate|^2 (coordinates are limited to 1e15, far
+// below float overflow of the squares).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "csg_internal.cuh"
+
+namespace csg {
+namespace {
+
+constexpr int kTile = 256;      // rows and columns per tile
+constexpr int kTileWords = 4;   // 64-bit words per tile row
+
+struct LinkRow {
+    int32_t d;
+    int32_t pad;
+    int64_t N, stride;
+    const double *coords;
+    uint64_t *rows;
+    int64_t tile_off;
+    int64_t nb, nbc;  // row blocks, column blocks
+    float screen;     // d=4 float-screen margin: 1e-5 * max(1, max |coordinate|)^2
+    float pad2;
+};
+
+__device__ __forceinline__ int find_set(const int64_t *__restrict__ starts, int n, int64_t g) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (starts[mid] <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// tiles before row block b: sum_{q<b} (nbc - q)
+__device__ __forceinline__ int64_t tiles_before(int64_t b, int64_t nbc) {
+    return b * nbc - b * (b - 1) / 2;
+}
+
+// order-preserving encoding of a double (no NaN); -0 is folded onto +0, so that
+// integer order equals IEEE order
+__device__ __forceinline__ uint64_t order_key(double x) {
+    if (x == 0.0) x = 0.0;
+    uint64_t b = (uint64_t)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+
+__device__ __forceinline__ bool exact4(double ti, double xi, double yi, double zi, double tk,
+                                       double xk, double yk, double zk) {
+    if (!(tk > ti)) return false;
+    double dt = __dsub_rn(tk, ti);
+    double dx = __dsub_rn(xk, xi), dy = __dsub_rn(yk, yi), dz = __dsub_rn(zk, zi);
+    double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return __dmul_rn(dt, dt) > s;
+}
+
+__global__ void __launch_bounds__(kTile)
+link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts, int n) {
+    __shared__ double cd[4][kTile];       // column coordinates (d=4: t,x,y,z)
+    __shared__ uint64_t ck[2][kTile];     // column order keys of u and v (d=2)
+    __shared__ float cf[4][kTile];        // column coordinates in float (d=4)
+    __shared__ uint32_t tb[kTile][9];     // mirrored bits: tb[c][w] = rows 32w..32w+31 of column c
+
+    const int s = find_set(starts, n, blockIdx.x);
+    const LinkRow S = sets[s];
+    const int64_t t = blockIdx.x - S.tile_off;
+    // row block: largest b with tiles_before(b) <= t
+    int64_t lo = 0, hi = S.nb - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (tiles_before(mid, S.nbc) <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const int64_t bi = lo;
+    const int64_t bj = bi + (t - tiles_before(bi, S.nbc));
+    const int64_t R = bi * kTile, K = bj * kTile;
+    const int64_t N = S.N;
+    const bool diag = (bi == bj);
+    const int r = threadIdx.x;
+    const int lane = r & 31, warp = r >> 5;
+    const int64_t i = R + r;
+    const int64_t kc = K + r;  // column staged by this thread
+
+    // stage column coordinates
+    if (S.d == 2) {
+        if (kc < N) {
+            ck[0][r] = order_key(S.coords[2 * N + kc]);
+            ck[1][r] = order_key(S.coords[3 * N + kc]);
+        }
+    } else {
+        if (kc < N) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                double v = S.coords[q * N + kc];
+                cd[q][r] = v;
+                cf[q][r] = __double2float_rn(v);
+            }
+        }
+    }
+    __syncthreads();
+
+    uint64_t w[kTileWords] = {0, 0, 0, 0};
+    // columns valid for this tile: [0, ncol)
+    const int64_t ncol_l = N - K;
+    const int ncol = ncol_l <= 0 ? 0 : (ncol_l >= kTile ? kTile : (int)ncol_l);
+    if (i < N) {
+        // first column index strictly after row i within the tile (diagonal tiles)
+        const int c0 = diag ? r + 1 : 0;
+        if (S.d == 2) {
+            const uint64_t ui = order_key(S.coords[2 * N + i]);
+            const uint64_t vi = order_key(S.coords[3 * N + i]);
+            const uint64_t *cu = ck[0];
+            const uint64_t *cv = ck[1];
+#pragma unroll
+            for (int q = 0; q < kTileWords; ++q) {
+                uint64_t acc = 0;
+#pragma unroll 16
+                for (int b = 0; b < 64; ++b) {
+                    const int c = q * 64 + b;
+                    if (c >= c0 && c < ncol && (ui < cu[c]) && (vi < cv[c])) acc |= 1ull << b;
+                }
+                w[q] = acc;
+            }
+        } else {
+            const double ti = S.coords[i], xi = S.coords[N + i], yi = S.coords[2 * N + i],
+                         zi = S.coords[3 * N + i];
+            const float screen = S.screen;
+            const float tf = __double2float_rn(ti), xf = __double2float_rn(xi),
+                        yf = __double2float_rn(yi), zf = __double2float_rn(zi);
+#pragma unroll
+            for (int q = 0; q < kTileWords; ++q) {
+                uint64_t acc = 0;
+#pragma unroll 8
+                for (int b = 0; b < 64; ++b) {
+                    const int c = q * 64 + b;
+                    if (c >= c0 && c < ncol) {
+                        float dt = __fsub_rn(cf[0][c], tf);
+                        float dx = __fsub_rn(cf[1][c], xf);
+                        float dy = __fsub_rn(cf[2][c], yf);
+                        float dz = __fsub_rn(cf[3][c], zf);
+                        float a = __fmul_rn(dt, dt);
+                        float bsum = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)),
+                                               __fmul_rn(dz, dz));
+                        float diff = __fsub_rn(a, bsum);
+                        bool rel;
+                        if (diff > screen)
+                            rel = true;
+                        else if (diff < -screen)
+                            rel = false;
+                        else
+                            rel = exact4(ti, xi, yi, zi, cd[0][c], cd[1][c], cd[2][c], cd[3][c]);
+                        if (rel) acc |= 1ull << b;
+                    }
+                }
+                w[q] = acc;
+            }
+        }
+    }
+
+    // mirrored half: bit r of row (K + c), word R/64 + warp/2, is w_r bit c
+    uint32_t keep[kTile / 32];
+#pragma unroll
+    for (int c = 0; c < kTile; ++c) {
+        uint32_t b = __ballot_sync(0xffffffffu, (uint32_t)(w[c >> 6] >> (c & 63)) & 1u);
+        if ((c & 31) == lane) keep[c >> 5] = b;
+    }
+#pragma unroll
+    for (int q = 0; q < kTile / 32; ++q) tb[lane + 32 * q][warp] = keep[q];
+    __syncthreads();
+
+    uint64_t *rows = S.rows;
+    const int64_t stride = S.stride;
+    if (diag) {
+        // both halves land in the same words: OR them
+        if (i < N) {
+            uint64_t *dst = rows + i * stride + K / 64;
+#pragma unroll
+            for (int q = 0; q < kTileWords; ++q) {
+                uint64_t m = (uint64_t)tb[r][2 * q] | ((uint64_t)tb[r][2 * q + 1] << 32);
+                dst[q] = w[q] | m;
+            }
+        }
+    } else {
+        if (i < N) {
+            uint64_t *dst = rows + i * stride + K / 64;
+            reinterpret_cast<ulonglong2 *>(dst)[0] = make_ulonglong2(w[0], w[1]);
+            reinterpret_cast<ulonglong2 *>(dst)[1] = make_ulonglong2(w[2], w[3]);
+        }
+        if (kc < N) {
+            uint64_t m[kTileWords];
+#pragma unroll
+            for (int q = 0; q < kTileWords; ++q)
+                m[q] = (uint64_t)tb[r][2 * q] | ((uint64_t)tb[r][2 * q + 1] << 32);
+            uint64_t *dst = rows + kc * stride + R / 64;
+            reinterpret_cast<ulonglong2 *>(dst)[0] = make_ulonglong2(m[0], m[1]);
+            reinterpret_cast<ulonglong2 *>(dst)[1] = make_ulonglong2(m[2], m[3]);
+        }
+    }
+}
+
+}  // namespace
+
+int link_batch(const LinkSpec *specs, int n, cudaStream_t st) {
+    if (n <= 0) return CSG_OK;
+    std::vector<LinkRow> rows(n);
+    std::vector<int64_t> starts(n);
+    int64_t T = 0;
+    for (int s = 0; s < n; ++s) {
+        LinkRow &L = rows[s];
+        L.d = specs[s].d;
+        L.pad = 0;
+        L.N = specs[s].N;
+        L.stride = specs[s].stride;
+        L.coords = specs[s].coords;
+        L.rows = specs[s].rows;
+        L.nb = (L.N + kTile - 1) / kTile;
+        L.nbc = L.stride / kTileWords;
+        L.tile_off = T;
+        L.screen = 1e-5f * (float)(specs[s].coord_scale * specs[s].coord_scale);
+        L.pad2 = 0.f;
+        starts[s] = T;
+        if (L.stride % 16 != 0 || L.nbc < L.nb) {
+            set_error("link: stride %lld does not cover N=%lld", (long long)L.stride,
+                      (long long)L.N);
+            return CSG_E_INVAL;
+        }
+        T += L.nb * L.nbc - L.nb * (L.nb - 1) / 2;
+    }
+    if (T == 0) return CSG_OK;
+    if (T > 0x7fffffffLL) {
+        set_error("link: %lld tiles exceed one launch", (long long)T);
+        return CSG_E_INVAL;
+    }
+    char *tab = nullptr;
+    CSG_CUDA_TRY(cudaMallocAsync((void **)&tab, n * (sizeof(LinkRow) + sizeof(int64_t)), st));
+    LinkRow *d_rows = (LinkRow *)tab;
+    int64_t *d_starts = (int64_t *)(tab + n * sizeof(LinkRow));
+    cudaMemcpyAsync(d_rows, rows.data(), n * sizeof(LinkRow), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_starts, starts.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    link_kernel<<<(unsigned)T, kTile, 0, st>>>(d_rows, d_starts, n);
+    cudaError_t le = cudaGetLastError();
+    cudaFreeAsync(tab, st);
+    if (le != cudaSuccess) {
+        set_error("link launch: %s", cudaGetErrorString(le));
+        return CSG_E_CUDA;
+    }
+    return CSG_OK;
+}
+
+}  // namespace csg

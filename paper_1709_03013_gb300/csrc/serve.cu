@@ -1,0 +1,295 @@
+// Batched pipeline (sprinkle + sort + link + action for many sets) and the request
+// service built on it.
+//
+// The service does continuous batching: csg_serve_submit only queues a request.
+// A small pool of worker threads, each with its own CUDA stream, repeatedly takes
+// the queued requests that fit the context's memory budget (admission by the set's
+// footprint, N*N/8 bytes of bitmap plus coordinates), up to a work cap per batch,
+// and runs the whole path for them in shared launches.  Requests that arrive while
+// other batches are on the GPU are admitted by the next free worker as soon as
+// memory frees up, so their kernels overlap on the device.  Results are kept per
+// ticket until csg_serve_poll collects them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <thread>
+#include <vector>
+
+#include "csg_internal.cuh"
+#include "csg_state.h"
+
+namespace csg {
+
+int run_pipeline(csg_set *const *sets, int n, const uint64_t *seed, const uint64_t *seq, int method,
+                 csg_result *out, cudaStream_t st) {
+    if (n <= 0) return CSG_OK;
+    std::vector<SprinkleSpec> sp(n);
+    std::vector<LinkSpec> lk(n);
+    for (int s = 0; s < n; ++s) {
+        sp[s] = SprinkleSpec{sets[s]->d, 0, sets[s]->N, seed[s], seq[s], sets[s]->coords, 0};
+        lk[s] = LinkSpec{sets[s]->d, 0, sets[s]->N, sets[s]->stride, sets[s]->coords, sets[s]->rows,
+                         0, 1.0};
+    }
+    int rc = sprinkle_sort_batch(sp.data(), n, st, nullptr);
+    if (rc != CSG_OK) return rc;
+    rc = link_batch(lk.data(), n, st);
+    if (rc != CSG_OK) return rc;
+    for (int s = 0; s < n; ++s) sets[s]->linked = true;
+    return run_actions(sets, n, method, -1, -1, nullptr, 0, out, st);
+}
+
+// ------------------------------------------------------------------ service
+
+namespace {
+
+enum ReqState { Q_QUEUED, Q_RUNNING, Q_DONE, Q_CANCELLED };
+
+struct Req {
+    int d;
+    int64_t N;
+    uint64_t seed, seq;
+    ReqState state;
+    int rc;
+    csg_result res;
+};
+
+size_t footprint(int64_t N) {
+    return (size_t)N * 4 * sizeof(double) + (size_t)N * stride_for(N) * sizeof(uint64_t);
+}
+
+// rough work of a request in bit operations: ~0.12 N^3 (d=2), ~0.035 N^3 (d=4)
+double work_of(int d, int64_t N) {
+    double n = (double)N;
+    return (d == 2 ? 0.12 : 0.035) * n * n * n;
+}
+
+}  // namespace
+
+struct ServeState {
+    csg_ctx *ctx = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_work;   // workers wait for queued requests / memory
+    std::condition_variable cv_done;   // pollers wait for results
+    std::deque<uint64_t> queue;        // queued tickets, arrival order
+    std::map<uint64_t, Req> reqs;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    size_t reserved = 0;               // bytes admitted by running batches
+    std::vector<std::thread> workers;
+    size_t max_queue = 1 << 20;
+    double batch_work_cap = 4e12;      // bit operations per batch (about 30-60 ms)
+    int batch_max_sets = 4096;
+};
+
+namespace {
+
+void worker_main(ServeState *S) {
+    csg_ctx *ctx = S->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    std::vector<uint64_t> batch;
+    for (;;) {
+        batch.clear();
+        size_t bytes = 0;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            for (;;) {
+                if (S->stop) break;
+                // admit from the head of the queue while memory and the work cap allow
+                double work = 0.0;
+                while (!S->queue.empty() && (int)batch.size() < S->batch_max_sets) {
+                    const uint64_t t = S->queue.front();
+                    Req &r = S->reqs[t];
+                    if (r.state == Q_CANCELLED) {
+                        S->queue.pop_front();
+                        continue;
+                    }
+                    const size_t need = footprint(r.N);
+                    size_t used;
+                    {
+                        std::lock_guard<std::mutex> g(ctx->mu);
+                        used = ctx->used;
+                    }
+                    const bool fits = ctx->budget == 0 || used + S->reserved + bytes + need <= ctx->budget;
+                    const double w = work_of(r.d, r.N);
+                    if (!fits) break;
+                    if (!batch.empty() && work + w > S->batch_work_cap) break;
+                    S->queue.pop_front();
+                    r.state = Q_RUNNING;
+                    batch.push_back(t);
+                    bytes += need;
+                    work += w;
+                }
+                if (!batch.empty()) break;
+                S->cv_work.wait(lk);
+            }
+            if (batch.empty() && S->stop) break;
+            S->reserved += bytes;
+        }
+        // run the batch
+        const int n = (int)batch.size();
+        std::vector<csg_set *> sets;
+        std::vector<uint64_t> seeds(n), seqs(n);
+        std::vector<csg_result> res(n);
+        int rc = CSG_OK;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (int q = 0; q < n; ++q) {
+                const Req &r = S->reqs[batch[q]];
+                seeds[q] = r.seed;
+                seqs[q] = r.seq;
+            }
+        }
+        for (int q = 0; q < n && rc == CSG_OK; ++q) {
+            int d;
+            int64_t N;
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                d = S->reqs[batch[q]].d;
+                N = S->reqs[batch[q]].N;
+            }
+            csg_set *x = nullptr;
+            rc = alloc_set(ctx, d, N, &x);
+            if (rc == CSG_OK) sets.push_back(x);
+        }
+        {
+            // the sets now hold the memory that admission reserved
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->reserved -= bytes;
+        }
+        if (rc == CSG_OK) rc = run_pipeline(sets.data(), n, seeds.data(), seqs.data(), CSG_POPC,
+                                            res.data(), st);
+        for (csg_set *x : sets) free_set(x);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (int q = 0; q < n; ++q) {
+                Req &r = S->reqs[batch[q]];
+                r.state = Q_DONE;
+                r.rc = rc;
+                if (rc == CSG_OK) r.res = res[q];
+            }
+        }
+        S->cv_done.notify_all();
+        S->cv_work.notify_all();
+    }
+    cudaStreamDestroy(st);
+}
+
+ServeState *ensure_serve(csg_ctx *ctx) {
+    std::lock_guard<std::mutex> g(ctx->serve_mu);
+    if (!ctx->serve) {
+        ServeState *S = new ServeState();
+        S->ctx = ctx;
+        const int workers = 3;
+        for (int w = 0; w < workers; ++w) S->workers.emplace_back(worker_main, S);
+        ctx->serve = S;
+    }
+    return ctx->serve;
+}
+
+}  // namespace
+
+void serve_shutdown(csg_ctx *ctx) {
+    ServeState *S = nullptr;
+    {
+        std::lock_guard<std::mutex> g(ctx->serve_mu);
+        S = ctx->serve;
+        ctx->serve = nullptr;
+    }
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    for (auto &t : S->workers) t.join();
+    delete S;
+}
+
+}  // namespace csg
+
+using namespace csg;
+
+extern "C" {
+
+int csg_serve_submit(csg_ctx *ctx, int d, int64_t N, uint64_t seed, uint64_t seq, uint64_t *ticket) {
+    if (!ctx || !ticket || (d != 2 && d != 4) || N < 1 || N > CSG_MAX_N) {
+        set_error("csg_serve_submit: bad arguments");
+        return CSG_E_INVAL;
+    }
+    if (ctx->budget && footprint(N) > ctx->budget) {
+        set_error("csg_serve_submit: request of %zu bytes can never fit the budget", footprint(N));
+        return CSG_E_NOMEM;
+    }
+    ServeState *S = ensure_serve(ctx);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->queue.size() >= S->max_queue) {
+            set_error("csg_serve_submit: queue full");
+            return CSG_E_BUSY;
+        }
+        const uint64_t t = S->next_ticket++;
+        Req r{};
+        r.d = d;
+        r.N = N;
+        r.seed = seed;
+        r.seq = seq;
+        r.state = Q_QUEUED;
+        r.rc = CSG_PENDING;
+        S->reqs[t] = r;
+        S->queue.push_back(t);
+        *ticket = t;
+    }
+    S->cv_work.notify_one();
+    return CSG_OK;
+}
+
+int csg_serve_poll(csg_ctx *ctx, uint64_t ticket, csg_result *out, int timeout_ms) {
+    if (!ctx || !out) return CSG_E_INVAL;
+    ServeState *S = ensure_serve(ctx);
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return CSG_E_NOTFOUND;
+    auto ready = [&] {
+        auto f = S->reqs.find(ticket);
+        return f == S->reqs.end() || f->second.state == Q_DONE || f->second.state == Q_CANCELLED;
+    };
+    if (!ready()) {
+        if (timeout_ms == 0) return CSG_PENDING;
+        if (timeout_ms < 0)
+            S->cv_done.wait(lk, ready);
+        else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+            return CSG_PENDING;
+    }
+    it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return CSG_E_NOTFOUND;
+    if (it->second.state == Q_CANCELLED) {
+        S->reqs.erase(it);
+        return CSG_E_CANCELLED;
+    }
+    const int rc = it->second.rc;
+    if (rc == CSG_OK) *out = it->second.res;
+    S->reqs.erase(it);
+    return rc;
+}
+
+int csg_serve_cancel(csg_ctx *ctx, uint64_t ticket) {
+    if (!ctx) return CSG_E_INVAL;
+    ServeState *S = ensure_serve(ctx);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->reqs.find(ticket);
+        if (it == S->reqs.end()) return CSG_E_NOTFOUND;
+        if (it->second.state != Q_QUEUED) return CSG_E_BUSY;  // already admitted
+        it->second.state = Q_CANCELLED;
+    }
+    S->cv_done.notify_all();
+    return CSG_OK;
+}
+
+}  // extern "C"

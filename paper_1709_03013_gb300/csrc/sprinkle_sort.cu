@@ -1,0 +1,341 @@
+// Sprinkling into a flat causal diamond (Sec. 2.1) and time ordering (Sec. 2.2),
+// batched over many sets: every kernel walks a flattened element space with a
+// small per-set table, so one launch sequence serves one set or thousands.
+//
+// Sort: composite keys (t, u, e) for d=2 and (t, e) for d=4 are encoded as two
+// order-preserving uint64 words plus the element index, so every key is unique
+// and the order is total.  Chunks of 1024 keys are ranked in shared memory, then
+// sorted runs are merged pairwise: an element's place in the merged run is its
+// rank in its own run plus the number of smaller keys in the sibling run (a
+// binary search).  All of it is exact integer work.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "csg_internal.cuh"
+
+namespace csg {
+namespace {
+
+constexpr int kChunk = 1024;
+constexpr int kSortThreads = 256;
+
+// ------------------------------------------------------------ Philox4x64-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+// (SC'11): ten rounds, each two 64x64->128 products, keys bumped by Weyl constants.
+struct U64x4 {
+    uint64_t w[4];
+};
+
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                                uint64_t k0, uint64_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t m0 = 0xD2E7470EE14C6C93ULL, m1 = 0xCA5A826395121157ULL;
+        uint64_t hi0 = __umul64hi(m0, c0), lo0 = m0 * c0;
+        uint64_t hi1 = __umul64hi(m1, c2), lo1 = m1 * c2;
+        uint64_t n0 = hi1 ^ c1 ^ k0;
+        uint64_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B97F4A7C15ULL;
+        k1 += 0xBB67AE8584CAA73BULL;
+    }
+    U64x4 out;
+    out.w[0] = c0;
+    out.w[1] = c1;
+    out.w[2] = c2;
+    out.w[3] = c3;
+    return out;
+}
+
+// top 53 bits scaled into [0, 1): exact conversion and power-of-two scaling
+__device__ __forceinline__ double unit53(uint64_t x) {
+    return __dmul_rn(__ull2double_rn(x >> 11), 0x1.0p-53);
+}
+
+// order-preserving encoding of a double (no NaN); -0 is folded onto +0
+__device__ __forceinline__ uint64_t order_key(double x) {
+    if (x == 0.0) x = 0.0;
+    uint64_t b = (uint64_t)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+
+// ------------------------------------------------------------ batch tables
+
+struct SetRow {
+    int32_t d;
+    int32_t pad;
+    int64_t N;
+    uint64_t seed, seq;
+    double *coords;      // sorted output [4][N]
+    int64_t off;         // element offset in the flattened batch
+    int64_t chunk_off;   // first chunk index of the set
+};
+
+__device__ __forceinline__ int find_set(const int64_t *__restrict__ starts, int n, int64_t g) {
+    // largest s with starts[s] <= g
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (starts[mid] <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+struct Keys {
+    uint64_t *k1, *k2;
+    uint32_t *idx;
+};
+
+// Sprinkle (or take host coordinates) into the unsorted buffer and emit sort keys.
+// tmp is [4][E] (row r of set s at tmp + r*E + off).
+__global__ void sprinkle_keys_kernel(const SetRow *__restrict__ sets, const int64_t *__restrict__ starts,
+                                     int n, int64_t E, double *__restrict__ tmp, Keys keys,
+                                     int from_coords, int *__restrict__ err) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < E;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int s = find_set(starts, n, g);
+        const SetRow S = sets[s];
+        const int64_t e = g - S.off;
+        double c0, c1, c2, c3;
+        if (from_coords) {
+            c0 = tmp[g];
+            c1 = tmp[E + g];
+            c2 = tmp[2 * E + g];
+            c3 = tmp[3 * E + g];
+        } else if (S.d == 2) {
+            U64x4 r = philox4x64_10((uint64_t)e, 0, 0, 0, S.seed, S.seq);
+            double u = unit53(r.w[0]), v = unit53(r.w[1]);
+            c0 = __dmul_rn(__dadd_rn(u, v), 0.5);
+            c1 = __dmul_rn(__dsub_rn(v, u), 0.5);
+            c2 = u;
+            c3 = v;
+        } else {
+            bool found = false;
+            c0 = c1 = c2 = c3 = 0.0;
+            for (int a = 0; a < 256 && !found; ++a) {
+                U64x4 r = philox4x64_10((uint64_t)e, (uint64_t)a, 0, 0, S.seed, S.seq);
+                double t = __dsub_rn(__dmul_rn(2.0, unit53(r.w[0])), 1.0);
+                double x = __dsub_rn(__dmul_rn(2.0, unit53(r.w[1])), 1.0);
+                double y = __dsub_rn(__dmul_rn(2.0, unit53(r.w[2])), 1.0);
+                double z = __dsub_rn(__dmul_rn(2.0, unit53(r.w[3])), 1.0);
+                double rr = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)),
+                                                 __dmul_rn(z, z)));
+                if (__dadd_rn(fabs(t), rr) <= 1.0) {
+                    c0 = t;
+                    c1 = x;
+                    c2 = y;
+                    c3 = z;
+                    found = true;
+                }
+            }
+            if (!found) atomicExch(err, CSG_E_REJECT);
+        }
+        if (!from_coords) {
+            tmp[g] = c0;
+            tmp[E + g] = c1;
+            tmp[2 * E + g] = c2;
+            tmp[3 * E + g] = c3;
+        }
+        keys.k1[g] = order_key(c0);
+        keys.k2[g] = (S.d == 2) ? order_key(c2) : 0ULL;
+        keys.idx[g] = (uint32_t)e;
+    }
+}
+
+__device__ __forceinline__ bool key_less(uint64_t a1, uint64_t a2, uint32_t ai, uint64_t b1,
+                                         uint64_t b2, uint32_t bi) {
+    if (a1 != b1) return a1 < b1;
+    if (a2 != b2) return a2 < b2;
+    return ai < bi;
+}
+
+// Rank each key of a chunk among the chunk's keys (all distinct) and scatter.
+__global__ void __launch_bounds__(kSortThreads)
+chunk_sort_kernel(const SetRow *__restrict__ sets, const int64_t *__restrict__ chunk_starts, int n,
+                  Keys in, Keys out) {
+    __shared__ uint64_t s1[kChunk], s2[kChunk];
+    __shared__ uint32_t si[kChunk];
+    const int s = find_set(chunk_starts, n, blockIdx.x);
+    const SetRow S = sets[s];
+    const int64_t c = blockIdx.x - S.chunk_off;
+    const int64_t base = S.off + c * kChunk;
+    const int64_t rem = S.N - c * kChunk;
+    const int len = rem < kChunk ? (int)rem : kChunk;
+    for (int t = threadIdx.x; t < len; t += kSortThreads) {
+        s1[t] = in.k1[base + t];
+        s2[t] = in.k2[base + t];
+        si[t] = in.idx[base + t];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < len; t += kSortThreads) {
+        const uint64_t a1 = s1[t], a2 = s2[t];
+        const uint32_t ai = si[t];
+        int rank = 0;
+        for (int q = 0; q < len; ++q) rank += key_less(s1[q], s2[q], si[q], a1, a2, ai);
+        out.k1[base + rank] = a1;
+        out.k2[base + rank] = a2;
+        out.idx[base + rank] = ai;
+    }
+}
+
+// One merge pass with run width w: runs [2q w, (2q+1) w) and [(2q+1) w, (2q+2) w).
+__global__ void merge_pass_kernel(const SetRow *__restrict__ sets, const int64_t *__restrict__ starts,
+                                  int n, int64_t E, int64_t w, Keys in, Keys out) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < E;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int s = find_set(starts, n, g);
+        const SetRow S = sets[s];
+        const int64_t p = g - S.off;
+        const uint64_t a1 = in.k1[g], a2 = in.k2[g];
+        const uint32_t ai = in.idx[g];
+        int64_t dst = p;
+        if (S.N > w) {
+            const int64_t run = p / w;
+            const int64_t sib = run ^ 1;
+            const int64_t sib_lo = sib * w;
+            if (sib_lo < S.N) {
+                const int64_t sib_hi = (sib_lo + w < S.N) ? sib_lo + w : S.N;
+                // number of sibling keys below a (keys distinct)
+                int64_t lo = sib_lo, hi = sib_hi;
+                while (lo < hi) {
+                    int64_t mid = (lo + hi) >> 1;
+                    const int64_t gm = S.off + mid;
+                    if (key_less(in.k1[gm], in.k2[gm], in.idx[gm], a1, a2, ai))
+                        lo = mid + 1;
+                    else
+                        hi = mid;
+                }
+                const int64_t pair_lo = (run < sib ? run : sib) * w;
+                dst = pair_lo + (p - run * w) + (lo - sib_lo);
+            }
+        }
+        out.k1[S.off + dst] = a1;
+        out.k2[S.off + dst] = a2;
+        out.idx[S.off + dst] = ai;
+    }
+}
+
+// coords_sorted[r][p] = tmp[r][idx[p]]
+__global__ void gather_kernel(const SetRow *__restrict__ sets, const int64_t *__restrict__ starts,
+                              int n, int64_t E, const double *__restrict__ tmp,
+                              const uint32_t *__restrict__ idx) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < E;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int s = find_set(starts, n, g);
+        const SetRow S = sets[s];
+        const int64_t p = g - S.off;
+        const int64_t src = S.off + idx[g];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) S.coords[r * S.N + p] = tmp[r * E + src];
+    }
+}
+
+int grid_for(int64_t E, int threads) {
+    int64_t b = (E + threads - 1) / threads;
+    if (b > 152 * 64) b = 152 * 64;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int sprinkle_sort_batch(const SprinkleSpec *specs, int n, cudaStream_t st,
+                        const double *const *host_coords) {
+    if (n <= 0) return CSG_OK;
+    std::vector<SetRow> rows(n);
+    std::vector<int64_t> starts(n), chunk_starts(n);
+    int64_t E = 0, C = 0, maxN = 0;
+    for (int s = 0; s < n; ++s) {
+        rows[s].d = specs[s].d;
+        rows[s].pad = 0;
+        rows[s].N = specs[s].N;
+        rows[s].seed = specs[s].seed;
+        rows[s].seq = specs[s].seq;
+        rows[s].coords = specs[s].coords;
+        rows[s].off = E;
+        rows[s].chunk_off = C;
+        starts[s] = E;
+        chunk_starts[s] = C;
+        E += specs[s].N;
+        C += (specs[s].N + kChunk - 1) / kChunk;
+        if (specs[s].N > maxN) maxN = specs[s].N;
+    }
+    if (E == 0) return CSG_OK;
+    // one device block: set table, starts, chunk starts, error word
+    size_t tab_bytes = n * sizeof(SetRow) + 2 * n * sizeof(int64_t) + 16;
+    char *tab = nullptr;
+    double *tmp = nullptr;
+    uint64_t *kb = nullptr;
+    uint32_t *ib = nullptr;
+    CSG_CUDA_TRY(cudaMallocAsync((void **)&tab, tab_bytes, st));
+    cudaError_t e1 = cudaMallocAsync((void **)&tmp, 4 * E * sizeof(double), st);
+    cudaError_t e2 = cudaMallocAsync((void **)&kb, 4 * E * sizeof(uint64_t), st);
+    cudaError_t e3 = cudaMallocAsync((void **)&ib, 2 * E * sizeof(uint32_t), st);
+    int rc = CSG_OK;
+    int err_host = 0;
+    SetRow *d_rows = (SetRow *)tab;
+    int64_t *d_starts = (int64_t *)(tab + n * sizeof(SetRow));
+    int64_t *d_cstarts = d_starts + n;
+    int *d_err = (int *)(d_cstarts + n);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        set_error("sprinkle: scratch allocation of %lld elements failed", (long long)E);
+        rc = CSG_E_NOMEM;
+        goto done;
+    }
+    {
+        // the host tables are pageable; cudaMemcpyAsync stages them before returning
+        cudaMemcpyAsync(d_rows, rows.data(), n * sizeof(SetRow), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(d_starts, starts.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(d_cstarts, chunk_starts.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice,
+                        st);
+        cudaMemsetAsync(d_err, 0, sizeof(int), st);
+        if (host_coords) {
+            for (int s = 0; s < n; ++s)
+                for (int r = 0; r < 4; ++r)
+                    cudaMemcpyAsync(tmp + r * E + rows[s].off, host_coords[s] + r * rows[s].N,
+                                    rows[s].N * sizeof(double), cudaMemcpyHostToDevice, st);
+        }
+        Keys a{kb, kb + E, ib}, b{kb + 2 * E, kb + 3 * E, ib + E};
+        const int T = 256;
+        sprinkle_keys_kernel<<<grid_for(E, T), T, 0, st>>>(d_rows, d_starts, n, E, tmp, a,
+                                                           host_coords ? 1 : 0, d_err);
+        chunk_sort_kernel<<<(unsigned)C, kSortThreads, 0, st>>>(d_rows, d_cstarts, n, a, b);
+        Keys cur = b, nxt = a;
+        for (int64_t w = kChunk; w < maxN; w *= 2) {
+            merge_pass_kernel<<<grid_for(E, T), T, 0, st>>>(d_rows, d_starts, n, E, w, cur, nxt);
+            Keys t = cur;
+            cur = nxt;
+            nxt = t;
+        }
+        gather_kernel<<<grid_for(E, T), T, 0, st>>>(d_rows, d_starts, n, E, tmp, cur.idx);
+        cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) {
+            set_error("sprinkle/sort launch: %s", cudaGetErrorString(le));
+            rc = CSG_E_CUDA;
+            goto done;
+        }
+        cudaMemcpyAsync(&err_host, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    }
+done:
+    if (tmp) cudaFreeAsync(tmp, st);
+    if (kb) cudaFreeAsync(kb, st);
+    if (ib) cudaFreeAsync(ib, st);
+    cudaFreeAsync(tab, st);
+    cudaError_t se = cudaStreamSynchronize(st);
+    if (rc == CSG_OK && se != cudaSuccess) {
+        set_error("sprinkle/sort: %s", cudaGetErrorString(se));
+        rc = CSG_E_CUDA;
+    }
+    if (rc == CSG_OK && err_host != 0) {
+        set_error("sprinkle: an element hit the 256-attempt rejection cap");
+        rc = err_host;
+    }
+    return rc;
+}
+
+}  // namespace csg

@@ -1,0 +1,71 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads, and
+exports every symbol that include/csg.h declares, and the binding agrees with the
+header's constants."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "csg.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(csg_[a-z_0-9]+)\s*\(", text)))
+
+
+def _defines():
+    out = {}
+    for m in re.finditer(r"#define\s+(CSG_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", open(HEADER).read()):
+        out[m.group(1)] = int(m.group(2))
+    return out
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1709_03013_gb300 import _build
+    return ctypes.CDLL(_build.build())
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header():
+    from paper_1709_03013_gb300 import csg
+    assert sorted(csg.EXPORTS) == _declared()
+
+
+def test_constants_match_header():
+    from paper_1709_03013_gb300 import csg
+    d = _defines()
+    assert d["CSG_OK"] == csg.OK and d["CSG_PENDING"] == csg.PENDING
+    assert d["CSG_E_INVAL"] == csg.E_INVAL and d["CSG_E_NOMEM"] == csg.E_NOMEM
+    assert d["CSG_E_CUDA"] == csg.E_CUDA and d["CSG_E_TIMEOUT"] == csg.E_TIMEOUT
+    assert d["CSG_E_BUSY"] == csg.E_BUSY and d["CSG_E_REJECT"] == csg.E_REJECT
+    assert d["CSG_E_NOTFOUND"] == csg.E_NOTFOUND and d["CSG_E_CANCELLED"] == csg.E_CANCELLED
+    assert d["CSG_POPC"] == csg.POPC and d["CSG_TC"] == csg.TC
+    assert csg.MAX_N == 1 << 18
+
+
+def test_result_struct_layout():
+    from paper_1709_03013_gb300 import csg
+    assert ctypes.sizeof(csg._Result) == 88
+
+
+def test_strerror_and_argument_errors_without_gpu(lib):
+    from paper_1709_03013_gb300 import csg
+    L = csg.load()
+    assert L.csg_strerror(csg.E_INVAL) == b"invalid argument"
+    # null context / bad arguments are rejected before any CUDA call
+    t = ctypes.c_uint64()
+    assert L.csg_serve_submit(None, 2, 10, 0, 0, ctypes.byref(t)) == csg.E_INVAL
+    assert L.csg_link(None, None, None) == csg.E_INVAL
+    assert L.csg_action(None, None, 0, None, None) == csg.E_INVAL
+    assert L.csg_set_info(None, None, None, None, None, None) == csg.E_INVAL

@@ -1,0 +1,207 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Sprinkled coordinates, the bitmap C, R, N_0..N_3, sum m, W and the full
+histogram must match bit for bit; the actions are exact integer combinations
+scaled once in double, so they must match to 1e-12 relative (they are in fact
+identical).  Sizes span several 256-element link tiles, several 16-row action
+groups and ragged tails; the degenerate sizes N = 1, 2, 3 are included.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_03013_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_S = 1e-12
+
+
+@pytest.fixture(scope="module")
+def csg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_03013_gb300 import csg as m
+    m.load()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(csg):
+    c = csg.Context(0)
+    yield c
+    c.close()
+
+
+def _dev_words(words):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(words).view(np.int64)).cuda()
+
+
+def _check_result(res, want, d, N):
+    assert res.d == d and res.N == N and res.status == 0
+    assert res.R == want["R"]
+    assert list(res.Nk) == [int(x) for x in want["Nk"]]
+    assert res.sum_m == want["sum_m"]
+    assert res.W == want["W"]
+    combo, S = oracle.finalize(d, N, want["Nk"])
+    assert res.combo == combo
+    assert abs(res.S - S) <= TOL_S * max(abs(S), 1.0)
+
+
+SIZES = [(2, 1), (2, 2), (2, 3), (4, 3), (2, 64), (4, 65), (2, 255), (4, 257), (2, 1000),
+         (4, 1000), (2, 2048), (4, 2500), (2, 4099), (4, 5000)]
+
+
+@pytest.mark.parametrize("d,N", SIZES)
+def test_sprinkle_link_action_match_oracle(ctx, d, N):
+    seed, seq = 1000 + N, d
+    s = ctx.sprinkle(d, N, seed, seq)
+    want_c = oracle.sprinkle_sorted(d, N, seed, seq)
+    assert np.array_equal(s.coords(), want_c)           # bit-exact coordinates and order
+    s.link()
+    rel = oracle.link(d, want_c)
+    got = s.bitmap()
+    assert np.array_equal(got, oracle.pack(rel, got.shape[1]))  # every word, padding included
+    _check_result(s.action(), oracle.action(rel), d, N)
+    s.free()
+
+
+@pytest.mark.parametrize("d,N", [(2, 700), (4, 1500), (2, 3000)])
+def test_full_histogram(ctx, d, N):
+    import torch
+    s = ctx.sprinkle(d, N, 7, 0).link()
+    want = oracle.action(oracle.link(d, oracle.sprinkle_sorted(d, N, 7, 0)))
+    h = torch.zeros(N, dtype=torch.int64, device="cuda")
+    res = s.action_hist(h.data_ptr(), N)
+    assert np.array_equal(h.cpu().numpy().astype(np.uint64), want["hist"])
+    _check_result(res, want, d, N)
+    # a short histogram keeps the low bins only
+    h4 = torch.zeros(3, dtype=torch.int64, device="cuda")
+    s.action_hist(h4.data_ptr(), 3)
+    assert np.array_equal(h4.cpu().numpy().astype(np.uint64), want["hist"][:3])
+    s.free()
+
+
+@pytest.mark.parametrize("name,rel", [
+    ("chain1", inputs.chain_rel(1)), ("chain5", inputs.chain_rel(5)), ("chain200", inputs.chain_rel(200)),
+    ("chain1030", inputs.chain_rel(1030)), ("antichain77", inputs.antichain_rel(77)),
+    ("random300", inputs.random_upper_rel(300, 0.3, 1)), ("random2000", inputs.random_upper_rel(2000, 0.05, 2)),
+    ("layered1200", inputs.layered_order_rel(1200, 3)),
+])
+def test_action_from_bitmap(ctx, name, rel):
+    N = rel.shape[0]
+    stride = max(1, (N + 63) // 64) + 3  # a caller stride unlike the library's
+    dev = _dev_words(inputs.pack_rows(rel, stride))
+    want = oracle.action(rel)
+    for d in (2, 4):
+        s = ctx.set_from_bitmap(d, N, dev.data_ptr(), stride)
+        _check_result(s.action(), want, d, N)
+        s.free()
+
+
+@pytest.mark.parametrize("name", ["diamond4.txt", "npos6.txt"])
+def test_golden_fixtures_on_gpu(ctx, golden, name):
+    g = golden(name)
+    rel = inputs.rel_from_edges(g["N"], g["rel"])
+    dev = _dev_words(inputs.pack_rows(rel, 16))
+    for d, key in ((2, "S2"), (4, "S4")):
+        s = ctx.set_from_bitmap(d, g["N"], dev.data_ptr(), 16)
+        r = s.action()
+        assert list(r.Nk) == g["Nk"] and r.R == g["R"] and r.sum_m == g["sum_m"]
+        assert r.combo == g["combo2" if d == 2 else "combo4"]
+        assert abs(r.S - g[key]) <= TOL_S * abs(g[key])
+        s.free()
+
+
+@pytest.mark.parametrize("d", [2, 4])
+def test_set_from_host_coords(ctx, d):
+    N = 1777
+    c = oracle.sprinkle(d, N, 31, 5)            # unsorted, as sprinkled
+    scale = 1000.0                              # exact power-free scale keeps order; margins scale
+    cs = c * scale
+    s = ctx.set_from_coords(d, cs)
+    sorted_c, _ = oracle.sort(d, cs)
+    assert np.array_equal(s.coords(), sorted_c)
+    s.link()
+    rel = oracle.link(d, sorted_c)
+    assert np.array_equal(s.bitmap(), oracle.pack(rel, s.info()["stride"]))
+    _check_result(s.action(), oracle.action(rel), d, N)
+    s.free()
+
+
+@pytest.mark.parametrize("d,N", [(2, 3000), (4, 4100)])
+def test_action_rows(ctx, d, N):
+    s = ctx.sprinkle(d, N, 99, 1).link()
+    rel = oracle.link(d, oracle.sprinkle_sorted(d, N, 99, 1))
+    for lo, hi in [(0, 1), (5, 40), (1000, 1017), (N - 70, N), (N - 1, N)]:
+        _check_result(s.action_rows(lo, hi), oracle.action(rel, rows=(lo, hi)), d, N)
+    s.free()
+
+
+def test_batch_equals_single(ctx):
+    specs = inputs.batch_workload(n_sets=24, seed=3, lo=64, hi=3000)
+    sets = [ctx.sprinkle(sp.d, sp.N, sp.seed, sp.seq).link() for sp in specs]
+    single = [s.action() for s in sets]
+    batch = ctx.action_batch(sets)
+    assert batch == single
+    run = ctx.run_batch([(sp.d, sp.N, sp.seed, sp.seq) for sp in specs])
+    assert run == single
+    for sp, r in list(zip(specs, single))[:6]:
+        want = oracle.run(sp.d, sp.N, sp.seed, sp.seq)
+        _check_result(r, want, sp.d, sp.N)
+    for s in sets:
+        s.free()
+
+
+def test_serve_alone_equals_in_mix(ctx, csg):
+    specs = inputs.batch_workload(n_sets=40, seed=11, lo=32, hi=2500)
+    alone = [ctx.run_batch([(sp.d, sp.N, sp.seed, sp.seq)])[0] for sp in specs]
+    tickets = [ctx.serve_submit(sp.d, sp.N, sp.seed, sp.seq) for sp in specs]
+    mixed = [ctx.serve_poll(t, timeout_ms=60000) for t in tickets]
+    assert mixed == alone
+    for sp, r in list(zip(specs, alone))[:4]:
+        _check_result(r, oracle.run(sp.d, sp.N, sp.seed, sp.seq), sp.d, sp.N)
+
+
+def test_errors(ctx, csg):
+    with pytest.raises(csg.CsgError) as e:
+        ctx.sprinkle(3, 10, 0)
+    assert e.value.code == csg.E_INVAL
+    with pytest.raises(csg.CsgError):
+        ctx.sprinkle(2, 0, 0)
+    with pytest.raises(csg.CsgError):
+        ctx.sprinkle(2, csg.MAX_N + 1, 0)
+    s = ctx.sprinkle(2, 100, 0)
+    with pytest.raises(csg.CsgError):
+        s.action()                     # not linked yet
+    s.free()
+    small = csg.Context(0, budget_bytes=1 << 20)
+    try:
+        with pytest.raises(csg.CsgError) as e:
+            small.sprinkle(2, 8192, 0)     # 8 MiB bitmap over a 1 MiB budget
+        assert e.value.code == csg.E_NOMEM
+        with pytest.raises(csg.CsgError) as e:
+            small.serve_submit(2, 8192, 0)
+        assert e.value.code == csg.E_NOMEM
+    finally:
+        small.close()
+
+
+def test_cancel_and_unknown_ticket(ctx, csg):
+    with pytest.raises(csg.CsgError) as e:
+        ctx.serve_poll(987654321, 0)
+    assert e.value.code == csg.E_NOTFOUND
+    big = [ctx.serve_submit(4, 12000, 5, q) for q in range(4)]
+    t = ctx.serve_submit(2, 500, 1, 1)
+    rc = ctx.serve_cancel(t)
+    if rc == 0:
+        with pytest.raises(csg.CsgError) as e:
+            ctx.serve_poll(t, 0)
+        assert e.value.code == csg.E_CANCELLED
+    else:
+        assert rc == csg.E_BUSY  # already admitted
+        assert ctx.serve_poll(t, 60000) is not None
+    for b in big:
+        assert ctx.serve_poll(b, 120000) is not None
