@@ -168,6 +168,23 @@ def run_reference(args):
     return 0
 
 
+def profile_action(args):
+    """A small fixed workload for ncu captures: sprinkle (seed 1), link, then
+    --reps action launches of the chosen method (the first one warms up)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1709_03013_gb300 import csg
+    method = csg.POPC if args.method == "popc" else csg.TC
+    with csg.Context(0) as ctx:
+        s = ctx.sprinkle(args.d, args.n, 1, 0).link()
+        for r in range(args.reps):
+            t0 = time.perf_counter()
+            res = s.action(method)
+            print(r, res.R, res.Nk, res.W, f"{(time.perf_counter() - t0) * 1e3:.2f} ms", flush=True)
+        s.free()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -176,7 +193,14 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--method", default="popc", choices=["popc", "tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-action", action="store_true",
+                    help="profiling driver: one sprinkled set, then --reps action launches")
+    ap.add_argument("--d", type=int, default=4)
+    ap.add_argument("--n", type=int, default=40000)
+    ap.add_argument("--reps", type=int, default=2)
     args = ap.parse_args()
+    if args.profile_action:
+        return profile_action(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -138,10 +138,11 @@ int csg_action(csg_ctx *ctx, csg_set *set, int method, csg_result *out, void *st
 int csg_action_rows(csg_ctx *ctx, csg_set *set, int method, int64_t row_lo, int64_t row_hi,
                     csg_result *out, void *stream);
 
-/* Full interval-size histogram: dev_hist[m] (m < nbins, device uint64 array owned by
- * the caller) receives the number of related pairs with m interior elements; bins
- * m >= nbins are not recorded.  Fills *out like csg_action. */
-int csg_action_hist(csg_ctx *ctx, csg_set *set, uint64_t *dev_hist, int64_t nbins,
+/* Full interval-size histogram (the abundances the smeared action of Eq. s_smeared
+ * needs, Sec. 4.1): dev_hist[m] (m < nbins, device uint64 array owned by the caller,
+ * zeroed by the call) receives the number of related pairs with m interior elements;
+ * bins m >= nbins are not recorded.  Fills *out like csg_action. */
+int csg_action_hist(csg_ctx *ctx, csg_set *set, int method, uint64_t *dev_hist, int64_t nbins,
                     csg_result *out, void *stream);
 
 /* Actions of n sets in one pass: all sets' work in one persistent launch over a

@@ -86,7 +86,7 @@ def load(path: str = LIB_PATH):
         "csg_set_from_bitmap": (i32, [vp, i32, i64, vp, i64, vp, pp]),
         "csg_action": (i32, [vp, vp, i32, R, vp]),
         "csg_action_rows": (i32, [vp, vp, i32, i64, i64, R, vp]),
-        "csg_action_hist": (i32, [vp, vp, vp, i64, R, vp]),
+        "csg_action_hist": (i32, [vp, vp, i32, vp, i64, R, vp]),
         "csg_action_batch": (i32, [vp, pp, i32, i32, R, vp]),
         "csg_run_batch": (i32, [vp, i32, vp, vp, vp, vp, i32, R, vp]),
         "csg_serve_submit": (i32, [vp, i32, i64, u64, u64, ctypes.POINTER(u64)]),
@@ -165,10 +165,10 @@ class CausalSet:
                                       _stream(stream)), "csg_action_rows")
         return Result.of(r)
 
-    def action_hist(self, dev_hist_ptr: int, nbins: int, stream=None) -> Result:
+    def action_hist(self, dev_hist_ptr: int, nbins: int, method: int = POPC, stream=None) -> Result:
         r = _Result()
-        _check(load().csg_action_hist(self.ctx.handle, self.handle, ctypes.c_void_p(dev_hist_ptr), nbins,
-                                      ctypes.byref(r), _stream(stream)), "csg_action_hist")
+        _check(load().csg_action_hist(self.ctx.handle, self.handle, method, ctypes.c_void_p(dev_hist_ptr),
+                                      nbins, ctypes.byref(r), _stream(stream)), "csg_action_hist")
         return Result.of(r)
 
     def coords(self) -> np.ndarray:

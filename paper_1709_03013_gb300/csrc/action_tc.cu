@@ -1,11 +1,526 @@
-// Tensor-core form of the interval counts (placeholder until the tcgen05 kernel lands).
+// Interval counts as a masked 0/1 matrix product on the tcgen05 tensor cores.
+//
+// With elements in time order, the interval size of a related pair i < j is
+//   m(i,j) = sum_k U[i][k] * P[j][k],   U[i][k] = S[i][k] [k > i],  P[j][k] = S[j][k] [k < j]
+// where S is the symmetric causal matrix: U holds each element's future, P its past
+// (Fig. 2: the inner product of rows i and j between columns i and j).  X = U P^T is
+// a dense contraction, so it runs on the tensor cores; only the entries with
+// S[i][j] = 1, i < j, are histogrammed (Alg. 5 counts related pairs only).
+//
+// Exactness: the operands are 0 and 1 in fp8 e4m3 (0x00, 0x38); products are exact
+// and the fp32 accumulator holds integers up to 2^24 exactly, far above the largest
+// interval (N - 2 <= 2^18).  The result is converted back to an integer before it is
+// used, so the counts are bit-exact.
+//
+// Pass 1 (expand): one thread per packed word writes the 64 fp8 bytes of U and of P
+// it covers; only the column ranges the product reads are written.
+// Pass 2 (product): persistent CTAs, one per SM, walk a list of output tiles
+// (128 rows i x 256 columns j, upper triangle only, K from the first row of the
+// tile to the last column) in a longest-first, 2048 x 2048 block-rasterised order.
+// Warp roles per CTA:
+//   warp 0     TMA producer: 128-byte-swizzled K tiles of U (128 x 128) and P
+//              (256 x 128) into a 4-stage shared-memory ring (mbarrier complete_tx)
+//   warp 1     allocates 512 TMEM columns; one lane issues tcgen05.mma
+//              (kind::f8f6f4, M=128, N=256, K=32, fp32 accumulate) and commits
+//              each stage back to the producer and each finished tile to the epilogue
+//   warps 2-5  epilogue: tcgen05.ld of the tile from TMEM (each thread owns one
+//              row), the S bits of the row select the related pairs, counters and
+//              the optional full histogram are updated; two TMEM accumulators let
+//              the epilogue of one tile overlap the product of the next.
+// Every wait is bounded (globaltimer); on expiry the kernel records an error in the
+// set's counters and winds down instead of spinning.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "csg_internal.cuh"
+#include "ptx.cuh"
 
 namespace csg {
+namespace {
 
-int action_tc(const SetDesc *, int, cudaStream_t) {
-    set_error("tensor-core action is not available in this build");
-    return CSG_E_INVAL;
+constexpr int BM = 128;          // rows i per tile
+constexpr int BN = 256;          // columns j per tile
+constexpr int BK = 128;          // K elements (= bytes) per stage
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK;
+constexpr int B_BYTES = BN * BK;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int EPI_WARPS = 4;
+constexpr int THREADS = (2 + EPI_WARPS) * 32;
+constexpr uint32_t TMEM_COLS = 2 * BN;
+constexpr uint64_t kWaitNs = 4000000000ull;
+constexpr uint8_t kOne = 0x38;   // 1.0 in fp8 e4m3
+constexpr int SUPER = 2048;      // rasterisation block (elements per side)
+
+struct TcTile {
+    int32_t ti, tj;  // rows [BM ti, BM ti + BM), columns [BN tj, BN tj + BN)
+};
+
+struct TcArgs {
+    const uint64_t *rows;  // packed symmetric bitmap
+    int64_t N, stride;
+    int64_t row_lo, row_hi;
+    unsigned long long *counters;
+    unsigned long long *hist;
+    long long nbins;
+    const TcTile *tiles;
+    int n_tiles;
+};
+
+// ------------------------------------------------------------------ expand
+
+__global__ void expand_kernel(const uint64_t *__restrict__ rows, int64_t N, int64_t stride,
+                              int64_t kp, uint8_t *__restrict__ U, uint8_t *__restrict__ P) {
+    const int64_t wpr = kp / 64;  // words per expanded row
+    const int64_t total = N * wpr;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = g / wpr, w = g - i * wpr;
+        const int64_t k0 = w * 64;
+        const uint64_t word = rows[i * stride + w];
+        // U row i is read from column BM*floor(i/BM); P row i up to column BN*(floor(i/BN)+1)
+        const bool needU = k0 + 64 > (i / BM) * BM;
+        const bool needP = k0 < (i / BN + 1) * BN;
+        if (needU) {
+            uint64_t m = word;
+            if (k0 + 63 <= i) m = 0;
+            else if (k0 <= i) m &= ~((2ull << (i - k0)) - 1ull);  // keep k > i
+            uint4 *dst = reinterpret_cast<uint4 *>(U + i * kp + k0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t v[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const uint32_t nib = (uint32_t)(m >> (16 * q + 4 * h)) & 0xFu;
+                    v[h] = ((nib & 1u) ? (uint32_t)kOne : 0u) | ((nib & 2u) ? (uint32_t)kOne << 8 : 0u) |
+                           ((nib & 4u) ? (uint32_t)kOne << 16 : 0u) | ((nib & 8u) ? (uint32_t)kOne << 24 : 0u);
+                }
+                dst[q] = make_uint4(v[0], v[1], v[2], v[3]);
+            }
+        }
+        if (needP) {
+            uint64_t m = word;
+            if (k0 >= i) m = 0;
+            else if (k0 + 63 >= i) m &= (1ull << (i - k0)) - 1ull;  // keep k < i
+            uint4 *dst = reinterpret_cast<uint4 *>(P + i * kp + k0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t v[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const uint32_t nib = (uint32_t)(m >> (16 * q + 4 * h)) & 0xFu;
+                    v[h] = ((nib & 1u) ? (uint32_t)kOne : 0u) | ((nib & 2u) ? (uint32_t)kOne << 8 : 0u) |
+                           ((nib & 4u) ? (uint32_t)kOne << 16 : 0u) | ((nib & 8u) ? (uint32_t)kOne << 24 : 0u);
+                }
+                dst[q] = make_uint4(v[0], v[1], v[2], v[3]);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ product
+
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);   // start address
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused, K-major SW128)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                     // descriptor version
+    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    return d;
+}
+
+// kind::f8f6f4, A = B = e4m3, D = f32, K-major A and B, M = 128, N = 256
+constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            ptx::smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(ptx::smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     ptx::smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_addr(bar)) : "memory");
+}
+
+#define TMEM_LD32(addr, v)                                                                          \
+    asm volatile(                                                                                   \
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17," \
+        "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                        \
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),       \
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), \
+          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),            \
+          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),            \
+          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])             \
+        : "r"(addr))
+
+__device__ __forceinline__ void k_range(const TcTile &t, int64_t N, int &kt0, int &kt1) {
+    const int64_t I0 = (int64_t)t.ti * BM;
+    const int64_t J1 = min((int64_t)(t.tj + 1) * BN, N);
+    kt0 = (int)(I0 / BK);
+    kt1 = (int)((J1 + BK - 1) / BK);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+action_tc_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmP,
+                 const TcArgs args) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + STAGES * STAGE_BYTES);
+    uint64_t *full = bars, *empty = bars + STAGES, *tfull = bars + 2 * STAGES,
+             *tempty = bars + 2 * STAGES + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 4);
+    int *bad_flag = reinterpret_cast<int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            ptx::mbar_init(&full[s], 1);
+            ptx::mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(&tfull[b], 1);
+            ptx::mbar_init(&tempty[b], EPI_WARPS * 32);
+        }
+        *bad_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         ptx::smem_addr(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int64_t N = args.N;
+    bool bad = false;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            for (int t = blockIdx.x; t < args.n_tiles && !bad; t += gridDim.x) {
+                const TcTile tile = args.tiles[t];
+                int kt0, kt1;
+                k_range(tile, N, kt0, kt1);
+                for (int kt = kt0; kt < kt1; ++kt) {
+                    if (!ptx::mbar_wait_bounded(&empty[s], ph ^ 1u, kWaitNs)) {
+                        bad = true;
+                        break;
+                    }
+                    ptx::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                    unsigned char *st = base + s * STAGE_BYTES;
+                    tma_load_2d(st, &tmU, kt * BK, tile.ti * BM, &full[s]);
+                    tma_load_2d(st + A_BYTES, &tmP, kt * BK, tile.tj * BN, &full[s]);
+                    if (++s == STAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0, b = 0, bph = 0;
+            for (int t = blockIdx.x; t < args.n_tiles && !bad; t += gridDim.x) {
+                const TcTile tile = args.tiles[t];
+                int kt0, kt1;
+                k_range(tile, N, kt0, kt1);
+                if (!ptx::mbar_wait_bounded(&tempty[b], bph ^ 1u, kWaitNs)) {
+                    bad = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem + b * BN;
+                for (int kt = kt0; kt < kt1; ++kt) {
+                    if (!ptx::mbar_wait_bounded(&full[s], ph, kWaitNs)) {
+                        bad = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = ptx::smem_addr(base + s * STAGE_BYTES);
+#pragma unroll
+                    for (int k = 0; k < BK / 32; ++k) {
+                        const uint64_t ad = smem_desc_sw128(sa + 32 * k);
+                        const uint64_t bd = smem_desc_sw128(sa + A_BYTES + 32 * k);
+                        mma_f8(dt, ad, bd, (kt > kt0 || k > 0) ? 1u : 0u);
+                    }
+                    mma_commit(&empty[s]);
+                    if (++s == STAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (bad) break;
+                mma_commit(&tfull[b]);
+                b ^= 1u;
+                if (b == 0) bph ^= 1u;
+            }
+        }
+    } else {
+        // epilogue: TMEM lane quarter of this warp
+        const int q = warp & 3;
+        const int r = q * 32 + lane;
+        unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, cR = 0, cM = 0, cW = 0;
+        uint32_t b = 0, bph = 0;
+        for (int t = blockIdx.x; t < args.n_tiles; t += gridDim.x) {
+            const TcTile tile = args.tiles[t];
+            const bool ok = ptx::mbar_wait_bounded(&tfull[b], bph, kWaitNs);
+            if (!__all_sync(0xffffffffu, ok)) {
+                bad = true;
+                break;
+            }
+            tc_fence_after();
+            const int64_t i = (int64_t)tile.ti * BM + r;
+            const int64_t J0 = (int64_t)tile.tj * BN;
+            const bool row_ok = i < N && i >= args.row_lo && i < args.row_hi;
+            uint64_t w4[4] = {0, 0, 0, 0};
+            if (row_ok) {
+                const uint64_t *src = args.rows + i * args.stride + J0 / 64;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) w4[u] = (J0 + 64 * u < N) ? __ldg(src + u) : 0ull;
+            }
+#pragma unroll
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t v[32];
+                const uint32_t addr = tmem + b * BN + (uint32_t)c + ((uint32_t)(q * 32) << 16);
+                TMEM_LD32(addr, v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                uint32_t bits = (uint32_t)(w4[c >> 6] >> (c & 32));
+                // only columns j > i
+                const int64_t rel = i - (J0 + c);  // bits q with q > rel survive
+                if (rel >= 31)
+                    bits = 0;
+                else if (rel >= 0)
+                    bits &= ~((2u << rel) - 1u);
+                if (bits) {
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) {
+                        if (bits >> u & 1u) {
+                            const uint32_t m = __float2uint_rn(__uint_as_float(v[u]));
+                            c0 += (m == 0);
+                            c1 += (m == 1);
+                            c2 += (m == 2);
+                            c3 += (m == 3);
+                            cR += 1;
+                            cM += m;
+                            cW += (unsigned long long)(J0 + c + u - i - 1);
+                            if (args.hist != nullptr && (long long)m < args.nbins)
+                                atomicAdd(&args.hist[m], 1ull);
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tempty[b]);
+            b ^= 1u;
+            if (b == 0) bph ^= 1u;
+        }
+        // warp-reduce the counters and flush
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+            c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+            c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+            c3 += __shfl_xor_sync(0xffffffffu, c3, o);
+            cR += __shfl_xor_sync(0xffffffffu, cR, o);
+            cM += __shfl_xor_sync(0xffffffffu, cM, o);
+            cW += __shfl_xor_sync(0xffffffffu, cW, o);
+        }
+        if (lane == 0 && cR) {
+            unsigned long long *cnt = args.counters;
+            atomicAdd(&cnt[CNT_N0], c0);
+            atomicAdd(&cnt[CNT_N1], c1);
+            atomicAdd(&cnt[CNT_N2], c2);
+            atomicAdd(&cnt[CNT_N3], c3);
+            atomicAdd(&cnt[CNT_R], cR);
+            atomicAdd(&cnt[CNT_SUM_M], cM);
+            atomicAdd(&cnt[CNT_W], cW);
+        }
+    }
+    if (bad) atomicExch(bad_flag, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (*bad_flag && threadIdx.x == 0) atomicExch(&args.counters[CNT_ERR], 1ull);
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+int make_map(CUtensorMap *m, void *base, int64_t rows, int64_t kp, int box_rows) {
+    auto enc = get_encoder();
+    if (!enc) {
+        set_error("action_tc: cuTensorMapEncodeTiled is unavailable");
+        return CSG_E_CUDA;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kp};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("action_tc: tensor map encoding failed (%d)", (int)r);
+        return CSG_E_CUDA;
+    }
+    return CSG_OK;
+}
+
+// Output tiles of the upper triangle, longest K first at the granularity of
+// SUPER x SUPER blocks, column-major inside a block (tiles sharing a P panel run
+// together).
+std::vector<TcTile> make_tiles(int64_t N, int64_t row_lo, int64_t row_hi) {
+    const int NI = (int)((N + BM - 1) / BM), NJ = (int)((N + BN - 1) / BN);
+    struct Key {
+        int64_t ext;
+        int bi, bj, tj, ti;
+    };
+    std::vector<Key> keys;
+    for (int ti = 0; ti < NI; ++ti) {
+        const int64_t I0 = (int64_t)ti * BM, I1 = I0 + BM;
+        if (I1 <= row_lo || I0 >= row_hi) continue;
+        for (int tj = ti / 2; tj < NJ; ++tj) {
+            const int64_t J1 = std::min<int64_t>((int64_t)(tj + 1) * BN, N);
+            if (J1 <= I0 + 1) continue;  // no pair i < j in the tile
+            const int bi = (int)(I0 / SUPER), bj = (int)(((int64_t)tj * BN) / SUPER);
+            const int64_t ext = (int64_t)(bj + 1) * SUPER - (int64_t)bi * SUPER;
+            keys.push_back(Key{ext, bi, bj, tj, ti});
+        }
+    }
+    std::sort(keys.begin(), keys.end(), [](const Key &a, const Key &b) {
+        if (a.ext != b.ext) return a.ext > b.ext;
+        if (a.bi != b.bi) return a.bi < b.bi;
+        if (a.bj != b.bj) return a.bj < b.bj;
+        if (a.tj != b.tj) return a.tj < b.tj;
+        return a.ti < b.ti;
+    });
+    std::vector<TcTile> tiles(keys.size());
+    for (size_t k = 0; k < keys.size(); ++k) tiles[k] = TcTile{keys[k].ti, keys[k].tj};
+    return tiles;
+}
+
+}  // namespace
+
+// Largest N the tensor form accepts: its fp8 operands take 2 N^2 bytes of scratch.
+static constexpr int64_t kTcMaxN = 1 << 17;
+
+int action_tc(const SetDesc *sets, int n_sets, cudaStream_t st, unsigned long long *dev_hist,
+              int64_t nbins) {
+    for (int s = 0; s < n_sets; ++s) {
+        const SetDesc &S = sets[s];
+        const int64_t N = S.N;
+        if (N > kTcMaxN) {
+            set_error("action_tc: N=%lld exceeds the tensor form's limit %lld", (long long)N,
+                      (long long)kTcMaxN);
+            return CSG_E_INVAL;
+        }
+        const int64_t lo = std::max<int64_t>(0, S.row_lo), hi = std::min<int64_t>(N, S.row_hi);
+        if (hi <= lo) continue;
+        const int64_t kp = (N + BK - 1) / BK * BK;  // expanded row pitch in bytes
+        std::vector<TcTile> tiles = make_tiles(N, lo, hi);
+        if (tiles.empty()) continue;
+        uint8_t *ops = nullptr;
+        TcTile *d_tiles = nullptr;
+        const size_t op_bytes = 2 * (size_t)N * kp;
+        CSG_CUDA_TRY(cudaMallocAsync((void **)&ops, op_bytes, st));
+        cudaError_t e = cudaMallocAsync((void **)&d_tiles, tiles.size() * sizeof(TcTile), st);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(ops, st);
+            set_error("action_tc: tile list allocation failed");
+            return CSG_E_NOMEM;
+        }
+        uint8_t *U = ops, *P = ops + (size_t)N * kp;
+        cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice, st);
+        const int64_t words = N * (kp / 64);
+        int blocks = (int)std::min<int64_t>((words + 255) / 256, 152 * 32);
+        expand_kernel<<<blocks, 256, 0, st>>>(S.rows, N, S.stride, kp, U, P);
+        CUtensorMap mU, mP;
+        int rc = make_map(&mU, U, N, kp, BM);
+        if (rc == CSG_OK) rc = make_map(&mP, P, N, kp, BN);
+        if (rc == CSG_OK) {
+            TcArgs a;
+            a.rows = S.rows;
+            a.N = N;
+            a.stride = S.stride;
+            a.row_lo = lo;
+            a.row_hi = hi;
+            a.counters = S.counters;
+            a.hist = dev_hist;
+            a.nbins = nbins;
+            a.tiles = d_tiles;
+            a.n_tiles = (int)tiles.size();
+            const size_t smem = 1024 + STAGES * STAGE_BYTES + 256;
+            cudaError_t ae =
+                cudaFuncSetAttribute(action_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int grid = (int)std::min<int64_t>(sms, (int64_t)tiles.size());
+            if (ae == cudaSuccess) {
+                action_tc_kernel<<<grid, THREADS, smem, st>>>(mU, mP, a);
+                ae = cudaGetLastError();
+            }
+            if (ae != cudaSuccess) {
+                set_error("action_tc launch: %s", cudaGetErrorString(ae));
+                rc = CSG_E_CUDA;
+            }
+        }
+        cudaFreeAsync(d_tiles, st);
+        cudaFreeAsync(ops, st);
+        if (rc != CSG_OK) return rc;
+    }
+    return CSG_OK;
 }
 
 }  // namespace csg

@@ -91,7 +91,7 @@ int run_actions(csg_set *const *sets, int n, int method, int64_t row_lo, int64_t
     if (method == CSG_POPC)
         rc = action_popc(desc.data(), n, st, dev_hist, nbins);
     else
-        rc = action_tc(desc.data(), n, st);
+        rc = action_tc(desc.data(), n, st, dev_hist, nbins);
     if (rc == CSG_OK) {
         finalize_kernel<<<(n + 127) / 128, 128, 0, st>>>(d_fin, n, d_out);
         cudaError_t le = cudaGetLastError();
@@ -212,6 +212,12 @@ int csg_init(int device, size_t hbm_budget_bytes, csg_ctx **out) {
         return CSG_E_INVAL;
     }
     CSG_CUDA_TRY(cudaSetDevice(device));
+    // keep stream-ordered scratch (the tensor form's operands) cached between calls
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     csg_ctx *c = new csg_ctx();
     c->device = device;
     c->budget = hbm_budget_bytes;
@@ -357,7 +363,7 @@ int csg_action_rows(csg_ctx *ctx, csg_set *set, int method, int64_t row_lo, int6
     return action_common(ctx, set, method, row_lo, row_hi, nullptr, 0, out, stream);
 }
 
-int csg_action_hist(csg_ctx *ctx, csg_set *set, uint64_t *dev_hist, int64_t nbins,
+int csg_action_hist(csg_ctx *ctx, csg_set *set, int method, uint64_t *dev_hist, int64_t nbins,
                     csg_result *out, void *stream) {
     if (!dev_hist || nbins < 1) {
         set_error("csg_action_hist: bad histogram");
@@ -367,7 +373,7 @@ int csg_action_hist(csg_ctx *ctx, csg_set *set, uint64_t *dev_hist, int64_t nbin
         set_error("csg_action_hist: histogram memset failed");
         return CSG_E_CUDA;
     }
-    return action_common(ctx, set, CSG_POPC, -1, -1, (unsigned long long *)dev_hist, nbins, out,
+    return action_common(ctx, set, method, -1, -1, (unsigned long long *)dev_hist, nbins, out,
                          stream);
 }
 

@@ -89,8 +89,10 @@ int link_batch(const LinkSpec *specs_host, int n, cudaStream_t st);
 int action_popc(const SetDesc *sets_host, int n_sets, cudaStream_t st,
                 unsigned long long *dev_hist, int64_t nbins);
 
-// Tensor-core action (masked 0/1 product on tcgen05).
-int action_tc(const SetDesc *sets_host, int n_sets, cudaStream_t st);
+// Tensor-core action (masked 0/1 product on tcgen05).  counters must be zeroed by
+// the caller; dev_hist (optional) receives the full interval-size histogram.
+int action_tc(const SetDesc *sets_host, int n_sets, cudaStream_t st, unsigned long long *dev_hist,
+              int64_t nbins);
 
 // ---------------------------------------------------------------- errors
 

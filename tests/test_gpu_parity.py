@@ -55,7 +55,7 @@ SIZES = [(2, 1), (2, 2), (2, 3), (4, 3), (2, 64), (4, 65), (2, 255), (4, 257), (
 
 
 @pytest.mark.parametrize("d,N", SIZES)
-def test_sprinkle_link_action_match_oracle(ctx, d, N):
+def test_sprinkle_link_action_match_oracle(ctx, csg, d, N):
     seed, seq = 1000 + N, d
     s = ctx.sprinkle(d, N, seed, seq)
     want_c = oracle.sprinkle_sorted(d, N, seed, seq)
@@ -64,22 +64,25 @@ def test_sprinkle_link_action_match_oracle(ctx, d, N):
     rel = oracle.link(d, want_c)
     got = s.bitmap()
     assert np.array_equal(got, oracle.pack(rel, got.shape[1]))  # every word, padding included
-    _check_result(s.action(), oracle.action(rel), d, N)
+    want = oracle.action(rel)
+    _check_result(s.action(csg.POPC), want, d, N)
+    _check_result(s.action(csg.TC), want, d, N)
     s.free()
 
 
+@pytest.mark.parametrize("method", [0, 1])
 @pytest.mark.parametrize("d,N", [(2, 700), (4, 1500), (2, 3000)])
-def test_full_histogram(ctx, d, N):
+def test_full_histogram(ctx, d, N, method):
     import torch
     s = ctx.sprinkle(d, N, 7, 0).link()
     want = oracle.action(oracle.link(d, oracle.sprinkle_sorted(d, N, 7, 0)))
-    h = torch.zeros(N, dtype=torch.int64, device="cuda")
-    res = s.action_hist(h.data_ptr(), N)
+    h = torch.full((N,), 7, dtype=torch.int64, device="cuda")  # the call zeroes it
+    res = s.action_hist(h.data_ptr(), N, method)
     assert np.array_equal(h.cpu().numpy().astype(np.uint64), want["hist"])
     _check_result(res, want, d, N)
     # a short histogram keeps the low bins only
     h4 = torch.zeros(3, dtype=torch.int64, device="cuda")
-    s.action_hist(h4.data_ptr(), 3)
+    s.action_hist(h4.data_ptr(), 3, method)
     assert np.array_equal(h4.cpu().numpy().astype(np.uint64), want["hist"][:3])
     s.free()
 
@@ -90,28 +93,30 @@ def test_full_histogram(ctx, d, N):
     ("random300", inputs.random_upper_rel(300, 0.3, 1)), ("random2000", inputs.random_upper_rel(2000, 0.05, 2)),
     ("layered1200", inputs.layered_order_rel(1200, 3)),
 ])
-def test_action_from_bitmap(ctx, name, rel):
+def test_action_from_bitmap(ctx, csg, name, rel):
     N = rel.shape[0]
     stride = max(1, (N + 63) // 64) + 3  # a caller stride unlike the library's
     dev = _dev_words(inputs.pack_rows(rel, stride))
     want = oracle.action(rel)
     for d in (2, 4):
         s = ctx.set_from_bitmap(d, N, dev.data_ptr(), stride)
-        _check_result(s.action(), want, d, N)
+        _check_result(s.action(csg.POPC), want, d, N)
+        _check_result(s.action(csg.TC), want, d, N)
         s.free()
 
 
 @pytest.mark.parametrize("name", ["diamond4.txt", "npos6.txt"])
-def test_golden_fixtures_on_gpu(ctx, golden, name):
+def test_golden_fixtures_on_gpu(ctx, csg, golden, name):
     g = golden(name)
     rel = inputs.rel_from_edges(g["N"], g["rel"])
     dev = _dev_words(inputs.pack_rows(rel, 16))
     for d, key in ((2, "S2"), (4, "S4")):
         s = ctx.set_from_bitmap(d, g["N"], dev.data_ptr(), 16)
-        r = s.action()
-        assert list(r.Nk) == g["Nk"] and r.R == g["R"] and r.sum_m == g["sum_m"]
-        assert r.combo == g["combo2" if d == 2 else "combo4"]
-        assert abs(r.S - g[key]) <= TOL_S * abs(g[key])
+        for method in (csg.POPC, csg.TC):
+            r = s.action(method)
+            assert list(r.Nk) == g["Nk"] and r.R == g["R"] and r.sum_m == g["sum_m"]
+            assert r.combo == g["combo2" if d == 2 else "combo4"]
+            assert abs(r.S - g[key]) <= TOL_S * abs(g[key])
         s.free()
 
 
@@ -131,16 +136,17 @@ def test_set_from_host_coords(ctx, d):
     s.free()
 
 
+@pytest.mark.parametrize("method", [0, 1])
 @pytest.mark.parametrize("d,N", [(2, 3000), (4, 4100)])
-def test_action_rows(ctx, d, N):
+def test_action_rows(ctx, d, N, method):
     s = ctx.sprinkle(d, N, 99, 1).link()
     rel = oracle.link(d, oracle.sprinkle_sorted(d, N, 99, 1))
     for lo, hi in [(0, 1), (5, 40), (1000, 1017), (N - 70, N), (N - 1, N)]:
-        _check_result(s.action_rows(lo, hi), oracle.action(rel, rows=(lo, hi)), d, N)
+        _check_result(s.action_rows(lo, hi, method), oracle.action(rel, rows=(lo, hi)), d, N)
     s.free()
 
 
-def test_batch_equals_single(ctx):
+def test_batch_equals_single(ctx, csg):
     specs = inputs.batch_workload(n_sets=24, seed=3, lo=64, hi=3000)
     sets = [ctx.sprinkle(sp.d, sp.N, sp.seed, sp.seq).link() for sp in specs]
     single = [s.action() for s in sets]
@@ -148,6 +154,7 @@ def test_batch_equals_single(ctx):
     assert batch == single
     run = ctx.run_batch([(sp.d, sp.N, sp.seed, sp.seq) for sp in specs])
     assert run == single
+    assert ctx.action_batch(sets, csg.TC) == single
     for sp, r in list(zip(specs, single))[:6]:
         want = oracle.run(sp.d, sp.N, sp.seed, sp.seq)
         _check_result(r, want, sp.d, sp.N)
