@@ -177,6 +177,30 @@ int csg_set_info(const csg_set *set, int *d, int64_t *N, int64_t *stride_words,
 
 void csg_set_free(csg_set *set);
 
+/* The popcount action for callers that cannot let the library allocate device
+ * memory.  The paper has no counterpart to this call; it exists for callers such as
+ * code recording a CUDA graph (a cudaMalloc there breaks the capture), applications
+ * that give all of HBM to their own arena, and multi-stream servers that cannot
+ * afford the device-wide synchronisation of a cudaFree.
+ *
+ * Inputs: dev_rows, an N x stride_words bitmap in the layout above (16-byte aligned,
+ * even stride_words >= ceil(N/64)), and d (2 or 4) for the action's formula.
+ * Output: *dev_out, a csg_result in device memory owned by the caller, written when
+ * the stream reaches the call's kernels; the call returns without synchronising.
+ * The result equals csg_action(..., CSG_POPC, ...) on the same bitmap.
+ *
+ * The call allocates nothing: its scratch (a work-queue counter and partial counters
+ * for each group of 16 rows) lives in one fixed device array of 256 KiB + 16 bytes,
+ * which every GPU that loads the library holds until the process exits.  Hence N is
+ * limited to 1 <= N <= 65536; larger N returns CSG_E_INVAL with a message.  The
+ * first call on a device looks up that array's device address (cudaGetSymbolAddress)
+ * and caches it, so make that first call before any stream capture.  All calls on a
+ * device share the array and each call clears the parts that must start at zero;
+ * calls whose kernels overlap on the GPU (different streams, no ordering between
+ * them) race on it and must not be issued. */
+int csg_action_noalloc(int d, int64_t N, const uint64_t *dev_rows, int64_t stride_words,
+                       csg_result *dev_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

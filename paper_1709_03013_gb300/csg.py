@@ -58,6 +58,7 @@ EXPORTS = [
     "csg_set_from_coords", "csg_link", "csg_set_from_bitmap", "csg_action", "csg_action_rows",
     "csg_action_hist", "csg_action_batch", "csg_run_batch", "csg_serve_submit", "csg_serve_poll",
     "csg_serve_cancel", "csg_export_coords", "csg_export_bitmap", "csg_set_info", "csg_set_free",
+    "csg_action_noalloc",
 ]
 
 _lib = None
@@ -96,6 +97,7 @@ def load(path: str = LIB_PATH):
         "csg_export_bitmap": (i32, [vp, vp, sz]),
         "csg_set_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i64), pp, pp]),
         "csg_set_free": (None, [vp]),
+        "csg_action_noalloc": (i32, [i32, i64, vp, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -128,6 +130,25 @@ def _stream(stream):
     if hasattr(stream, "cuda_stream"):
         return ctypes.c_void_p(stream.cuda_stream)
     return ctypes.c_void_p(int(stream))
+
+
+NOALLOC_MAX_N = 65536
+RESULT_BYTES = 88
+
+
+def action_noalloc(d: int, N: int, dev_rows_ptr: int, stride_words: int, dev_out_ptr: int,
+                   stream=None) -> None:
+    """Popcount action that allocates nothing (see csg_action_noalloc in include/csg.h).
+
+    For callers that cannot let a library allocate device memory.  The result (a
+    csg_result, RESULT_BYTES bytes) is written to dev_out_ptr in stream order; read it
+    after synchronising the stream, e.g. with result_from_bytes()."""
+    _check(load().csg_action_noalloc(d, N, ctypes.c_void_p(dev_rows_ptr), stride_words,
+                                     ctypes.c_void_p(dev_out_ptr), _stream(stream)), "csg_action_noalloc")
+
+
+def result_from_bytes(buf: bytes) -> Result:
+    return Result.of(_Result.from_buffer_copy(bytes(buf)[:RESULT_BYTES]))
 
 
 class CausalSet:
