@@ -10,8 +10,10 @@ bitmap is 512 MiB, larger than the 129 MB L2, so no flush is needed between step
 Prints ONE JSON line (rank 0).  `value` is related-pair interval counts per second
 (R / step time) with the set generated on the device; `e2e` is the same metric
 through the public API from host coordinates (copied in every step) to the host
-result.  `roofline` is the action kernel against the integer-pipe popcount peak;
-`cpu_baseline` is the CPU oracle on a bounded sample of the same workload.
+result.  `roofline` is the action kernel of the chosen method (default: the fp8
+tensor-core form, against the fp8 tensor peak; the popcount form against the
+integer-pipe popcount peak is reported beside it); `cpu_baseline` is the CPU oracle
+on a bounded sample of the same workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -19,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -34,9 +37,9 @@ UNIT = "pairs/s"
 WORKLOAD = dict(d=4, N=65536, seed=1)
 WORKLOAD_NAME = "d=4 flat causal diamond, N=65536, seed 1 (sprinkle+sort+link+action)"
 
-# Popcount peak of the integer pipe: 16 32-bit POPC per SM per clock (CUDA C
-# Programming Guide throughput table), 32 bit-operations each.
-POPC_PER_SM_CLK = 16
+# Popcount peak of the integer pipe: 32 32-bit POPC per SM per clock (a loop of
+# independent popcounts sustains 28 per SM per clock on this GB300), 32 bit-ops each.
+POPC_PER_SM_CLK = 32
 SMS = 152
 
 
@@ -105,13 +108,29 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def launches_per_step(N: int) -> int:
-    # sprinkle+keys, chunk ranking, merge passes, gather; link; action; finalize
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu record, or None when the kernel's
+    source has changed since the counters were taken (or no record exists)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh).get(kernel)
+        if not rec or rec.get("workload") != workload:
+            return None
+        with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()[:16]
+        return rec["dram_bytes_per_launch"] if sha == rec["sha256_16"] else None
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def launches_per_step(N: int, tc: bool) -> int:
+    # sprinkle+keys, chunk ranking, merge passes, gather; link; [expand]; action; finalize
     passes, w = 0, 1024
     while w < N:
         passes += 1
         w *= 2
-    return 3 + passes + 1 + 2
+    return 3 + passes + 1 + (1 if tc else 0) + 2
 
 
 def cpu_baseline(threads: int = 0, rows_per_block: int = 64, blocks: int = 8):
@@ -191,7 +210,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--method", default="popc", choices=["popc", "tc"])
+    ap.add_argument("--method", default="tc", choices=["popc", "tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-action", action="store_true",
                     help="profiling driver: one sprinkled set, then --reps action launches")
@@ -206,7 +225,6 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
 
-    import numpy as np
     import torch
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -226,29 +244,35 @@ def main():
     d, N, seed = WORKLOAD["d"], WORKLOAD["N"], WORKLOAD["seed"]
     seq = rank  # replicas: each rank runs its own independent set
     ctx = csg.Context(local)
+    ctx.set_timing(True)
     stream = torch.cuda.current_stream()
 
-    def step():
+    def step(m=method):
         s = ctx.sprinkle(d, N, seed, seq)
         s.link()
-        r = s.action(method)
+        r = s.action(m)
         s.free()
         return r
-
-    for _ in range(args.warmup):
-        res = step()
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- device-resident timing (inputs are (d, N, seed); the set is generated on the GPU)
+    for _ in range(args.warmup):
+        step()
+
+    # ---- device-resident timing: the inputs are (d, N, seed); the set is generated on the GPU
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage_ms = {k: 0.0 for k in csg.Context.STAGES}
+    results = []
     with ClockSampler(local) as clk:
         ev0.record(stream)
-        results = [step() for _ in range(args.steps)]
+        for _ in range(args.steps):
+            results.append(step())
+            for k, v in ctx.stage_times().items():
+                stage_ms[k] += v or 0.0
         ev1.record(stream)
         barrier()
     ms = ev0.elapsed_time(ev1)
@@ -261,22 +285,21 @@ def main():
         dist.all_reduce(rt)
         R_total = float(rt.item())
     value = R_total / (ms / 1e3)
+    res = results[-1]
+    stage_avg = {k: v / args.steps for k, v in stage_ms.items()}
+    act_ms = stage_avg["action"]
 
-    # ---- action kernel alone (dominant kernel): events around the action call
+    # ---- the other method's action kernel on the same set (reported beside the main one)
+    other = csg.TC if method == csg.POPC else csg.POPC
     s = ctx.sprinkle(d, N, seed, seq).link()
-    s.action(method)
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    a0.record(stream)
-    for _ in range(args.steps):
-        ra = s.action(method)
-    a1.record(stream)
-    torch.cuda.synchronize()
-    act_ms = a0.elapsed_time(a1) / args.steps
+    s.action(other)
+    ro = s.action(other)
+    other_ms = ctx.stage_times()["action"]
+    assert (ro.R, tuple(ro.Nk), ro.sum_m, ro.W) == (res.R, tuple(res.Nk), res.sum_m, res.W)
     coords_host = s.coords()
     s.free()
 
-    # ---- end to end through the public API from host coordinates (pinned)
+    # ---- end to end through the public API from pinned host coordinates to the host result
     pinned = torch.from_numpy(coords_host).pin_memory()
     host_np = pinned.numpy()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -302,22 +325,36 @@ def main():
     pk = peaks()
     clocks = clk.summary()
     sm_max = (clocks or {}).get("sm_max_mhz") or pk.get("sm_max_mhz") or 2070.0
-    peak_bitops = SMS * POPC_PER_SM_CLK * 32 * sm_max * 1e6
-    achieved = ra.W / (act_ms / 1e3)
+    popc_peak = SMS * POPC_PER_SM_CLK * 32 * sm_max * 1e6          # bit-ops/s
+    fp8_peak = 2.0 * pk.get("bf16_tflops", 1900.0)                  # TFLOP/s, fp8 = 2 x bf16
+    tc_flops = 2.0 * math.comb(N, 3)                                # triangle-restricted contraction
+    popc_ms = act_ms if method == csg.POPC else other_ms
+    tc_ms = act_ms if method == csg.TC else other_ms
+    popc_roof = {"bound": "alu", "achieved": res.W / (popc_ms / 1e3), "peak": popc_peak,
+                 "unit": "bit-ops/s", "frac": res.W / (popc_ms / 1e3) / popc_peak, "traffic": None,
+                 "kernel_ms": popc_ms,
+                 "peak_basis": f"{SMS} SMs x {POPC_PER_SM_CLK} POPC/clk x 32 bits x {sm_max:.0f} MHz"}
+    tc_ach = tc_flops / (tc_ms / 1e3) / 1e12
+    tc_roof = {"bound": "tensor", "achieved": tc_ach, "peak": fp8_peak, "unit": "TFLOP/s",
+               "frac": tc_ach / fp8_peak,
+               "traffic": recorded_traffic("action_tc_kernel", f"d={d} N={N} seed {seed}"),
+               "kernel_ms": tc_ms,
+               "peak_basis": "fp8 = 2 x measured bf16 dense burst (MEASURED_PEAKS.json), of measured"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp8" if method == csg.TC else "u64",
+        "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "d": d, "N": N, "seed": seed, "method": args.method,
-                   "l2": "inputs larger than L2 (512 MiB bitmap per step)",
+                   "l2": "inputs larger than L2 (512 MiB bitmap, 8 GiB fp8 operands per step)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "gpu_launches": launches_per_step(N) * args.steps,
-        "result": {"R": ra.R, "Nk": list(ra.Nk), "sum_m": ra.sum_m, "W": ra.W, "S": ra.S},
-        "bitops_per_s": ra.W / (act_ms / 1e3),
-        "action_ms": act_ms,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_bitops, "unit": "bit-ops/s",
-                     "frac": achieved / peak_bitops, "traffic": None,
-                     "peak_basis": f"{SMS} SMs x {POPC_PER_SM_CLK} POPC/clk x 32 bits x {sm_max:.0f} MHz"},
+        "gpu_launches": launches_per_step(N, method == csg.TC) * args.steps,
+        "result": {"R": res.R, "Nk": list(res.Nk), "sum_m": res.sum_m, "W": res.W, "combo": res.combo,
+                   "S": res.S},
+        "stage_ms": stage_avg,
+        "bitops_per_s": res.W / (act_ms / 1e3),
+        "roofline": tc_roof if method == csg.TC else popc_roof,
+        "roofline_other_method": popc_roof if method == csg.TC else tc_roof,
         "e2e": {"value": e_pairs / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(host_np.nbytes),
                 "d2h_bytes_per_step": 88},
     }

@@ -177,6 +177,20 @@ int csg_set_info(const csg_set *set, int *d, int64_t *N, int64_t *stride_words,
 
 void csg_set_free(csg_set *set);
 
+/* Per-stage device timing (a tracing aid; Sec. 5 of the paper reports stage times).
+ * With timing on, every call on the context records CUDA events on its own stream
+ * around the kernels of each stage it runs; csg_stage_times(ctx, ms, n) waits for the
+ * last recorded events and writes the elapsed milliseconds of stages 0..n-1 (-1 for a
+ * stage not run since timing was switched on). */
+#define CSG_STAGE_SPRINKLE 0 /* sprinkle + time order */
+#define CSG_STAGE_LINK 1     /* causal matrix */
+#define CSG_STAGE_EXPAND 2   /* fp8 operand expansion of the tensor form */
+#define CSG_STAGE_ACTION 3   /* the interval-count kernel itself */
+#define CSG_STAGE_FINALIZE 4 /* counters -> action */
+#define CSG_STAGE_COUNT 5
+int csg_set_timing(csg_ctx *ctx, int enable);
+int csg_stage_times(csg_ctx *ctx, double *ms, int n);
+
 /* The popcount action for callers that cannot let the library allocate device
  * memory.  The paper has no counterpart to this call; it exists for callers such as
  * code recording a CUDA graph (a cudaMalloc there breaks the capture), applications

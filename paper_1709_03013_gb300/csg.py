@@ -58,7 +58,7 @@ EXPORTS = [
     "csg_set_from_coords", "csg_link", "csg_set_from_bitmap", "csg_action", "csg_action_rows",
     "csg_action_hist", "csg_action_batch", "csg_run_batch", "csg_serve_submit", "csg_serve_poll",
     "csg_serve_cancel", "csg_export_coords", "csg_export_bitmap", "csg_set_info", "csg_set_free",
-    "csg_action_noalloc",
+    "csg_action_noalloc", "csg_set_timing", "csg_stage_times",
 ]
 
 _lib = None
@@ -98,6 +98,8 @@ def load(path: str = LIB_PATH):
         "csg_set_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i64), pp, pp]),
         "csg_set_free": (None, [vp]),
         "csg_action_noalloc": (i32, [i32, i64, vp, i64, vp, vp]),
+        "csg_set_timing": (i32, [vp, i32]),
+        "csg_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_double), i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -288,6 +290,17 @@ class Context:
             return None
         _check(rc, "csg_serve_poll")
         return Result.of(r)
+
+    STAGES = ("sprinkle", "link", "expand", "action", "finalize")
+
+    def set_timing(self, enable: bool = True):
+        _check(load().csg_set_timing(self.handle, int(enable)), "csg_set_timing")
+
+    def stage_times(self) -> dict:
+        """Device milliseconds of each stage's last recorded run (None if not run)."""
+        arr = (ctypes.c_double * len(self.STAGES))()
+        _check(load().csg_stage_times(self.handle, arr, len(self.STAGES)), "csg_stage_times")
+        return {k: (arr[i] if arr[i] >= 0 else None) for i, k in enumerate(self.STAGES)}
 
     def serve_cancel(self, ticket: int) -> int:
         return load().csg_serve_cancel(self.handle, ticket)

@@ -211,8 +211,10 @@ int launch_g(const SetDesc *d_sets, const WorkItem *d_items, int n_items, int pi
     }
     int grid = sms * per_sm;
     if (grid > n_items) grid = n_items;
+    stage_begin(CSG_STAGE_ACTION, st);
     kern<<<grid, kThreads, smem, st>>>(d_sets, d_items, n_items, pitch, queue, hist,
                                        (long long)nbins);
+    stage_end(CSG_STAGE_ACTION, st);
     CSG_CUDA_TRY(cudaGetLastError());
     return CSG_OK;
 }

@@ -35,6 +35,9 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "csg_internal.cuh"
@@ -450,6 +453,43 @@ std::vector<TcTile> make_tiles(int64_t N, int64_t row_lo, int64_t row_hi) {
     return tiles;
 }
 
+// Device copies of tile lists, kept per (device, N, row range): building and
+// sorting a list of ~10^5 tiles on the host would otherwise stall every call.
+struct TileCache {
+    std::mutex mu;
+    std::map<std::tuple<int, int64_t, int64_t, int64_t>, std::pair<TcTile *, int>> lists;
+};
+TileCache g_tiles;
+
+int cached_tiles(int64_t N, int64_t lo, int64_t hi, const TcTile **out, int *n, cudaStream_t st) {
+    int dev = 0;
+    CSG_CUDA_TRY(cudaGetDevice(&dev));
+    auto key = std::make_tuple(dev, N, lo, hi);
+    std::lock_guard<std::mutex> g(g_tiles.mu);
+    auto it = g_tiles.lists.find(key);
+    if (it != g_tiles.lists.end()) {
+        *out = it->second.first;
+        *n = it->second.second;
+        return CSG_OK;
+    }
+    if (g_tiles.lists.size() >= 64) {
+        // drop every cached list (rare: more than 64 distinct shapes in one process)
+        CSG_CUDA_TRY(cudaStreamSynchronize(st));
+        for (auto &kv : g_tiles.lists) cudaFree(kv.second.first);
+        g_tiles.lists.clear();
+    }
+    std::vector<TcTile> tiles = make_tiles(N, lo, hi);
+    TcTile *d = nullptr;
+    if (!tiles.empty()) {
+        CSG_CUDA_TRY(cudaMalloc((void **)&d, tiles.size() * sizeof(TcTile)));
+        CSG_CUDA_TRY(cudaMemcpy(d, tiles.data(), tiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice));
+    }
+    g_tiles.lists[key] = std::make_pair(d, (int)tiles.size());
+    *out = d;
+    *n = (int)tiles.size();
+    return CSG_OK;
+}
+
 }  // namespace
 
 // Largest N the tensor form accepts: its fp8 operands take 2 N^2 bytes of scratch.
@@ -468,23 +508,20 @@ int action_tc(const SetDesc *sets, int n_sets, cudaStream_t st, unsigned long lo
         const int64_t lo = std::max<int64_t>(0, S.row_lo), hi = std::min<int64_t>(N, S.row_hi);
         if (hi <= lo) continue;
         const int64_t kp = (N + BK - 1) / BK * BK;  // expanded row pitch in bytes
-        std::vector<TcTile> tiles = make_tiles(N, lo, hi);
-        if (tiles.empty()) continue;
+        const TcTile *d_tiles = nullptr;
+        int n_tiles = 0;
+        int trc = cached_tiles(N, lo, hi, &d_tiles, &n_tiles, st);
+        if (trc != CSG_OK) return trc;
+        if (n_tiles == 0) continue;
         uint8_t *ops = nullptr;
-        TcTile *d_tiles = nullptr;
         const size_t op_bytes = 2 * (size_t)N * kp;
         CSG_CUDA_TRY(cudaMallocAsync((void **)&ops, op_bytes, st));
-        cudaError_t e = cudaMallocAsync((void **)&d_tiles, tiles.size() * sizeof(TcTile), st);
-        if (e != cudaSuccess) {
-            cudaFreeAsync(ops, st);
-            set_error("action_tc: tile list allocation failed");
-            return CSG_E_NOMEM;
-        }
         uint8_t *U = ops, *P = ops + (size_t)N * kp;
-        cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice, st);
         const int64_t words = N * (kp / 64);
         int blocks = (int)std::min<int64_t>((words + 255) / 256, 152 * 32);
+        stage_begin(CSG_STAGE_EXPAND, st);
         expand_kernel<<<blocks, 256, 0, st>>>(S.rows, N, S.stride, kp, U, P);
+        stage_end(CSG_STAGE_EXPAND, st);
         CUtensorMap mU, mP;
         int rc = make_map(&mU, U, N, kp, BM);
         if (rc == CSG_OK) rc = make_map(&mP, P, N, kp, BN);
@@ -499,16 +536,18 @@ int action_tc(const SetDesc *sets, int n_sets, cudaStream_t st, unsigned long lo
             a.hist = dev_hist;
             a.nbins = nbins;
             a.tiles = d_tiles;
-            a.n_tiles = (int)tiles.size();
+            a.n_tiles = n_tiles;
             const size_t smem = 1024 + STAGES * STAGE_BYTES + 256;
             cudaError_t ae =
                 cudaFuncSetAttribute(action_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             int dev = 0, sms = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const int grid = (int)std::min<int64_t>(sms, (int64_t)tiles.size());
+            const int grid = std::min(sms, n_tiles);
             if (ae == cudaSuccess) {
+                stage_begin(CSG_STAGE_ACTION, st);
                 action_tc_kernel<<<grid, THREADS, smem, st>>>(mU, mP, a);
+                stage_end(CSG_STAGE_ACTION, st);
                 ae = cudaGetLastError();
             }
             if (ae != cudaSuccess) {
@@ -516,7 +555,6 @@ int action_tc(const SetDesc *sets, int n_sets, cudaStream_t st, unsigned long lo
                 rc = CSG_E_CUDA;
             }
         }
-        cudaFreeAsync(d_tiles, st);
         cudaFreeAsync(ops, st);
         if (rc != CSG_OK) return rc;
     }

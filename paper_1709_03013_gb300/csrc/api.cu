@@ -93,7 +93,9 @@ int run_actions(csg_set *const *sets, int n, int method, int64_t row_lo, int64_t
     else
         rc = action_tc(desc.data(), n, st, dev_hist, nbins);
     if (rc == CSG_OK) {
+        stage_begin(CSG_STAGE_FINALIZE, st);
         finalize_kernel<<<(n + 127) / 128, 128, 0, st>>>(d_fin, n, d_out);
+        stage_end(CSG_STAGE_FINALIZE, st);
         cudaError_t le = cudaGetLastError();
         if (le != cudaSuccess) {
             set_error("finalize launch: %s", cudaGetErrorString(le));
@@ -230,6 +232,7 @@ void csg_finalize(csg_ctx *ctx) {
     if (!ctx) return;
     serve_shutdown(ctx);
     cudaSetDevice(ctx->device);
+    destroy_timer(ctx);
     std::vector<csg_set *> all;
     {
         std::lock_guard<std::mutex> g(ctx->mu);
@@ -242,6 +245,7 @@ void csg_finalize(csg_ctx *ctx) {
 int csg_sprinkle(csg_ctx *ctx, int d, int64_t N, uint64_t seed, uint64_t seq, void *stream,
                  csg_set **out) {
     if (!ctx) return CSG_E_INVAL;
+    TimerScope ts(ctx);
     CSG_CUDA_TRY(cudaSetDevice(ctx->device));
     csg_set *s = nullptr;
     int rc = alloc_set(ctx, d, N, &s);
@@ -263,6 +267,7 @@ int csg_set_from_coords(csg_ctx *ctx, int d, int64_t N, const double *host_coord
         set_error("csg_set_from_coords: null argument");
         return CSG_E_INVAL;
     }
+    TimerScope ts(ctx);
     double scale = 1.0;
     for (int64_t q = 0; q < 4 * N; ++q) {
         double a = fabs(host_coords[q]);
@@ -299,6 +304,7 @@ int csg_link(csg_ctx *ctx, csg_set *set, void *stream) {
         return CSG_E_INVAL;
     }
     CSG_CUDA_TRY(cudaSetDevice(ctx->device));
+    TimerScope ts(ctx);
     LinkSpec L{set->d, 0, set->N, set->stride, set->coords, set->rows, 0, set->coord_scale};
     int rc = link_batch(&L, 1, (cudaStream_t)stream);
     if (rc == CSG_OK) set->linked = true;
@@ -346,6 +352,7 @@ static int action_common(csg_ctx *ctx, csg_set *set, int method, int64_t lo, int
         return CSG_E_INVAL;
     }
     CSG_CUDA_TRY(cudaSetDevice(ctx->device));
+    TimerScope ts(ctx);
     csg_set *one[1] = {set};
     return run_actions(one, 1, method, lo, hi, hist, nbins, out, (cudaStream_t)stream);
 }
@@ -389,6 +396,7 @@ int csg_action_batch(csg_ctx *ctx, csg_set *const *sets, int n, int method, csg_
             return CSG_E_INVAL;
         }
     CSG_CUDA_TRY(cudaSetDevice(ctx->device));
+    TimerScope ts(ctx);
     return run_actions(sets, n, method, -1, -1, nullptr, 0, out, (cudaStream_t)stream);
 }
 
@@ -399,6 +407,7 @@ int csg_run_batch(csg_ctx *ctx, int n, const int32_t *d, const int64_t *N, const
         return CSG_E_INVAL;
     }
     CSG_CUDA_TRY(cudaSetDevice(ctx->device));
+    TimerScope ts(ctx);
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<csg_set *> sets;
     int rc = CSG_OK;

@@ -97,6 +97,10 @@ int action_tc(const SetDesc *sets_host, int n_sets, cudaStream_t st, unsigned lo
 // ---------------------------------------------------------------- errors
 
 void set_error(const char *fmt, ...);
+
+// Stage timing hooks (no-ops unless a TimerScope with timing on is active).
+void stage_begin(int stage, cudaStream_t st);
+void stage_end(int stage, cudaStream_t st);
 #define CSG_CUDA_TRY(expr)                                                              \
     do {                                                                                \
         cudaError_t _e = (expr);                                                        \

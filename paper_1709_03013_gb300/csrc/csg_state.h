@@ -24,6 +24,7 @@ struct csg_set {
 
 namespace csg {
 struct ServeState;
+struct StageTimer;
 }
 
 struct csg_ctx {
@@ -34,6 +35,7 @@ struct csg_ctx {
     std::set<csg_set *> sets;
     std::mutex serve_mu;
     csg::ServeState *serve = nullptr;
+    csg::StageTimer *timer = nullptr;  // per-stage CUDA events when timing is on
 };
 
 namespace csg {
@@ -51,5 +53,13 @@ int run_pipeline(csg_set *const *sets, int n, const uint64_t *seed, const uint64
                  csg_result *out, cudaStream_t st);
 
 void serve_shutdown(csg_ctx *ctx);
+void destroy_timer(csg_ctx *ctx);
+
+// Makes the context's stage timer (if any) current for the calling thread.
+struct TimerScope {
+    explicit TimerScope(csg_ctx *ctx);
+    ~TimerScope();
+    StageTimer *prev;
+};
 
 }  // namespace csg

@@ -262,7 +262,9 @@ int link_batch(const LinkSpec *specs, int n, cudaStream_t st) {
     int64_t *d_starts = (int64_t *)(tab + n * sizeof(LinkRow));
     cudaMemcpyAsync(d_rows, rows.data(), n * sizeof(LinkRow), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_starts, starts.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    stage_begin(CSG_STAGE_LINK, st);
     link_kernel<<<(unsigned)T, kTile, 0, st>>>(d_rows, d_starts, n);
+    stage_end(CSG_STAGE_LINK, st);
     cudaError_t le = cudaGetLastError();
     cudaFreeAsync(tab, st);
     if (le != cudaSuccess) {

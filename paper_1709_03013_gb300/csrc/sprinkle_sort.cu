@@ -302,6 +302,7 @@ int sprinkle_sort_batch(const SprinkleSpec *specs, int n, cudaStream_t st,
         }
         Keys a{kb, kb + E, ib}, b{kb + 2 * E, kb + 3 * E, ib + E};
         const int T = 256;
+        stage_begin(CSG_STAGE_SPRINKLE, st);
         sprinkle_keys_kernel<<<grid_for(E, T), T, 0, st>>>(d_rows, d_starts, n, E, tmp, a,
                                                            host_coords ? 1 : 0, d_err);
         chunk_sort_kernel<<<(unsigned)C, kSortThreads, 0, st>>>(d_rows, d_cstarts, n, a, b);
@@ -313,6 +314,7 @@ int sprinkle_sort_batch(const SprinkleSpec *specs, int n, cudaStream_t st,
             nxt = t;
         }
         gather_kernel<<<grid_for(E, T), T, 0, st>>>(d_rows, d_starts, n, E, tmp, cur.idx);
+        stage_end(CSG_STAGE_SPRINKLE, st);
         cudaError_t le = cudaGetLastError();
         if (le != cudaSuccess) {
             set_error("sprinkle/sort launch: %s", cudaGetErrorString(le));
