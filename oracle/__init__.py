@@ -67,8 +67,10 @@ def _load():
         lib.orc_interval_coords.restype = i64
         lib.orc_action_rows.argtypes = [i64, vp, i64, i64, vp, vp, vp, vp, i32]
         lib.orc_finalize.argtypes = [i32, i64, vp, vp, vp]
+        lib.orc_action_rows_coords.argtypes = [i32, i64, vp, i64, i64, vp, vp, vp, vp, i32]
         for f in (lib.orc_sprinkle, lib.orc_sort, lib.orc_link, lib.orc_link_row,
-                  lib.orc_related, lib.orc_pack, lib.orc_action_rows, lib.orc_finalize):
+                  lib.orc_related, lib.orc_pack, lib.orc_action_rows, lib.orc_finalize,
+                  lib.orc_action_rows_coords):
             f.restype = i32
         _lib = lib
         return lib
@@ -180,6 +182,23 @@ def action(rel: np.ndarray, threads: int = 0, rows: tuple[int, int] | None = Non
     rc = _load().orc_action_rows(N, _p(r), lo, hi, _p(hist), _p(R), _p(S), _p(W), threads)
     if rc != OK:
         raise RuntimeError(f"orc_action_rows failed: {rc}")
+    Nk = np.zeros(4, np.uint64)
+    n = min(4, hist.shape[0])
+    Nk[:n] = hist[:n]
+    return dict(hist=hist, Nk=Nk, R=int(R[0]), sum_m=int(S[0]), W=int(W[0]))
+
+
+def action_rows_coords(d: int, coords: np.ndarray, lo: int, hi: int, threads: int = 0) -> dict:
+    """Abundances of rows [lo, hi) straight from sorted coordinates (no N x N matrix)."""
+    c = np.ascontiguousarray(coords, dtype=np.float64)
+    N = c.shape[1]
+    hist = np.zeros(max(N, 1), dtype=np.uint64)
+    R = np.zeros(1, np.uint64)
+    S = np.zeros(1, np.uint64)
+    W = np.zeros(1, np.uint64)
+    rc = _load().orc_action_rows_coords(d, N, _p(c), lo, hi, _p(hist), _p(R), _p(S), _p(W), threads)
+    if rc != OK:
+        raise RuntimeError(f"orc_action_rows_coords failed: {rc}")
     Nk = np.zeros(4, np.uint64)
     n = min(4, hist.shape[0])
     Nk[:n] = hist[:n]

@@ -308,6 +308,61 @@ int orc_action_rows(int64_t N, const uint8_t *rel, int64_t row_lo, int64_t row_h
     return ORC_OK;
 }
 
+/* The same abundances for rows [row_lo, row_hi), computed straight from the sorted
+ * coordinates with no N*N matrix: for each related pair i < j with i in the range,
+ * m counts the k with i < k < j related to both (Sec. 4.1).  O(N^2) per row; used
+ * to check sampled rows of sets too large for the matrix. */
+int orc_action_rows_coords(int d, int64_t N, const double *coords, int64_t row_lo, int64_t row_hi,
+                           uint64_t *hist, uint64_t *R, uint64_t *sum_m, uint64_t *W, int threads) {
+    if ((d != 2 && d != 4) || N < 0 || row_lo < 0 || row_hi > N || row_lo > row_hi) return ORC_EINVAL;
+    int64_t bins = N > 0 ? N : 1;
+    memset(hist, 0, (size_t)bins * sizeof(uint64_t));
+    uint64_t tR = 0, tS = 0, tW = 0;
+#ifdef _OPENMP
+    int T = threads > 0 ? threads : omp_get_max_threads();
+#else
+    int T = 1;
+#endif
+    (void)threads;
+    uint64_t *priv = (uint64_t *)calloc((size_t)T * (size_t)bins, sizeof(uint64_t));
+    uint8_t *fut = (uint8_t *)malloc((size_t)(N > 0 ? N : 1));
+    if (!priv || !fut) {
+        free(priv);
+        free(fut);
+        return ORC_ENOMEM;
+    }
+    for (int64_t i = row_lo; i < row_hi; ++i) {
+        for (int64_t k = 0; k < N; ++k) fut[k] = (uint8_t)(k > i && orc_precedes(d, N, coords, i, k));
+#pragma omp parallel num_threads(T) reduction(+ : tR, tS, tW)
+        {
+#ifdef _OPENMP
+            uint64_t *h = priv + (size_t)omp_get_thread_num() * (size_t)bins;
+#else
+            uint64_t *h = priv;
+#endif
+#pragma omp for schedule(dynamic, 64)
+            for (int64_t j = i + 1; j < N; ++j) {
+                if (!fut[j]) continue;
+                int64_t m = 0;
+                for (int64_t k = i + 1; k < j; ++k)
+                    if (fut[k]) m += orc_precedes(d, N, coords, k, j);
+                h[m] += 1;
+                tR += 1;
+                tS += (uint64_t)m;
+                tW += (uint64_t)(j - i - 1);
+            }
+        }
+    }
+    for (int t = 0; t < T; ++t)
+        for (int64_t b = 0; b < bins; ++b) hist[b] += priv[(size_t)t * (size_t)bins + b];
+    free(priv);
+    free(fut);
+    *R = tR;
+    *sum_m = tS;
+    *W = tW;
+    return ORC_OK;
+}
+
 int orc_action(int64_t N, const uint8_t *rel, uint64_t *hist, uint64_t *R, uint64_t *sum_m,
                uint64_t *W, int threads) {
     return orc_action_rows(N, rel, 0, N, hist, R, sum_m, W, threads);

@@ -162,7 +162,11 @@ void worker_main(ServeState *S) {
             std::lock_guard<std::mutex> lk(S->mu);
             S->reserved -= bytes;
         }
-        if (rc == CSG_OK) rc = run_pipeline(sets.data(), n, seeds.data(), seqs.data(), CSG_POPC,
+        // the tensor form is the faster one wherever its operands fit (N <= 2^17)
+        int method = CSG_TC;
+        for (csg_set *x : sets)
+            if (x->N > (1 << 17)) method = CSG_POPC;
+        if (rc == CSG_OK) rc = run_pipeline(sets.data(), n, seeds.data(), seqs.data(), method,
                                             res.data(), st);
         for (csg_set *x : sets) free_set(x);
         {

@@ -294,6 +294,16 @@ def test_rows_partition():
     assert a["R"] + b["R"] == full["R"] and a["W"] + b["W"] == full["W"]
 
 
+@pytest.mark.parametrize("d,N,rows", [(2, 300, (0, 300)), (4, 500, (7, 60)), (2, 257, (250, 257))])
+def test_rows_from_coords_match_matrix(d, N, rows):
+    # the matrix-free row count agrees with the graph-library-pinned matrix count
+    c = oracle.sprinkle_sorted(d, N, 21)
+    a = oracle.action(oracle.link(d, c), rows=rows)
+    b = oracle.action_rows_coords(d, c, *rows)
+    assert np.array_equal(a["hist"], b["hist"])
+    assert (a["R"], a["sum_m"], a["W"]) == (b["R"], b["sum_m"], b["W"])
+
+
 def test_pack_layout():
     rel = inputs.random_upper_rel(130, 0.3, 1)
     w = oracle.pack(rel)
