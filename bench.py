@@ -22,6 +22,8 @@ from __future__ import annotations
 import argparse
 import json
 import math
+
+import numpy as np
 import os
 import statistics
 import subprocess
@@ -204,6 +206,143 @@ def profile_action(args):
     return 0
 
 
+def bench_batch(args):
+    """Plain (one set at a time, each call synchronised) vs batched (one call for all
+    sets, every step batched) on the mixed-size workload: 4096 diamonds, d alternating
+    2/4, N log-uniform in [256, 8192], seed 3."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1709_03013_gb300 import csg, inputs
+    method = csg.POPC if args.method == "popc" else csg.TC
+    specs = [(s.d, s.N, s.seed, s.seq) for s in inputs.batch_workload(n_sets=args.n_sets)]
+    ctx = csg.Context(0)
+    stream = torch.cuda.current_stream()
+
+    def plain():
+        out = []
+        for d, N, seed, seq in specs:
+            st = ctx.sprinkle(d, N, seed, seq)
+            st.link()
+            out.append(st.action(method))
+            st.free()
+        return out
+
+    def batched():
+        return ctx.run_batch(specs, method)
+
+    res_b = batched()
+    res_p = plain()
+    assert [(r.R, r.Nk, r.W) for r in res_b] == [(r.R, r.Nk, r.W) for r in res_p]
+    for _ in range(max(0, args.warmup - 1)):
+        batched()
+    times = {}
+    for name, fn in (("batched", batched), ("plain", plain)):
+        reps = args.steps if name == "batched" else max(1, args.steps // 2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1) / reps
+    R = sum(r.R for r in res_b)
+    W = sum(r.W for r in res_b)
+    line = {"metric": METRIC, "value": R / (times["batched"] / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": times["batched"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp8" if method == csg.TC else "u64", "data": "synthetic",
+            "config": {"workload": f"batch: {len(specs)} flat diamonds, d alternating 2/4, N log-uniform "
+                                   f"in [256, 8192], seed 3 (sprinkle+sort+link+action per set)",
+                       "method": args.method, "sets": len(specs), "sum_R": R, "sum_W": W},
+            "plain": {"value": R / (times["plain"] / 1e3), "ms": times["plain"]},
+            "batched_over_plain": times["plain"] / times["batched"]}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def bench_serve(args):
+    """Requests arrive as a Poisson stream (d in {2,4} 50/50, N log-uniform in
+    [1024, 65536], seed 4) and go through the continuous-batching service; latency is
+    arrival -> result ready.  The rate is swept as fractions of the batched capacity
+    measured on the same requests."""
+    import threading as th
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1709_03013_gb300 import csg, inputs
+    reqs = inputs.serve_workload(n_req=args.n_req)
+    specs = [(r.spec.d, r.spec.N, r.spec.seed, r.spec.seq) for r in reqs]
+    ctx = csg.Context(0, budget_bytes=160 * 10 ** 9)
+    ctx.run_batch(specs[:32], csg.TC)                   # warm up
+    t0 = time.perf_counter()
+    res_b = ctx.run_batch(specs, csg.TC)                 # capacity: all requests as one batch
+    cap_s = time.perf_counter() - t0
+    capacity = len(specs) / cap_s
+    # plain: one request at a time through the single-set calls
+    nplain = min(len(specs), 200)
+    t0 = time.perf_counter()
+    for d, N, seed, seq in specs[:nplain]:
+        st = ctx.sprinkle(d, N, seed, seq)
+        st.link()
+        st.action(csg.TC)
+        st.free()
+    plain_rate = nplain / (time.perf_counter() - t0)
+    sweeps = []
+    for frac in [float(x) for x in args.rates.split(",")]:
+        rate = frac * capacity
+        gaps = np.random.default_rng(4).exponential(1.0 / rate, size=len(specs))
+        arrive = np.cumsum(gaps) - gaps[0]
+        done = [0.0] * len(specs)
+        results = [None] * len(specs)
+        tickets = [None] * len(specs)
+        start = time.perf_counter()
+
+        def collect():
+            # scan the outstanding tickets without blocking so that out-of-order
+            # completions are timed when they happen
+            pending = set(range(len(specs)))
+            while pending:
+                for k in list(pending):
+                    if tickets[k] is None:
+                        continue
+                    r = ctx.serve_poll(tickets[k], timeout_ms=0)
+                    if r is not None:
+                        results[k] = r
+                        done[k] = time.perf_counter() - start
+                        pending.discard(k)
+                time.sleep(0.0002)
+
+        poller = th.Thread(target=collect)
+        poller.start()
+        for k, (d, N, seed, seq) in enumerate(specs):
+            delay = arrive[k] - (time.perf_counter() - start)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[k] = ctx.serve_submit(d, N, seed, seq)
+        poller.join()
+        lat = np.array(done) - arrive
+        span = max(done)
+        ok = all(r is not None and (r.R, r.Nk, r.W) == (b.R, b.Nk, b.W) for r, b in zip(results, res_b))
+        sweeps.append({"rate_frac": frac, "rate_req_s": rate, "throughput_req_s": len(specs) / span,
+                       "pairs_per_s": sum(r.R for r in results) / span,
+                       "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                       "results_equal_batch": ok})
+    R = sum(r.R for r in res_b)
+    line = {"metric": METRIC, "value": R / cap_s, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": cap_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp8", "data": "synthetic",
+            "config": {"workload": f"serve: {len(specs)} requests, d in {{2,4}} 50/50, N log-uniform in "
+                                   f"[1024, 65536], Poisson arrivals, seed 4, 160 GB admission budget",
+                       "method": "tc"},
+            "capacity_req_s": capacity, "plain_req_s": plain_rate,
+            "served_capacity_over_plain": capacity / plain_rate, "sweep": sweeps}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -217,9 +356,20 @@ def main():
     ap.add_argument("--d", type=int, default=4)
     ap.add_argument("--n", type=int, default=40000)
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
+                    help="single: the d=4 N=65536 set; batch: 4096 mixed diamonds, plain vs batched; "
+                         "serve: Poisson request stream through the service, p50/p99 latency")
+    ap.add_argument("--n-sets", type=int, default=4096)
+    ap.add_argument("--n-req", type=int, default=2000)
+    ap.add_argument("--rates", default="0.25,0.5,0.75,0.9,1.1",
+                    help="serve: arrival rates as fractions of the measured batched capacity")
     args = ap.parse_args()
     if args.profile_action:
         return profile_action(args)
+    if args.workload == "batch":
+        return bench_batch(args)
+    if args.workload == "serve":
+        return bench_serve(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -25,6 +25,7 @@
 
 #include <algorithm>
 
+#include "arena.h"
 #include "csg_internal.cuh"
 #include "ptx.cuh"
 
@@ -196,9 +197,8 @@ action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict_
 }
 
 template <int G>
-int launch_g(const SetDesc *d_sets, const WorkItem *d_items, int n_items, int pitch,
-             unsigned int *queue, unsigned long long *hist, int64_t nbins, cudaStream_t st) {
-    const size_t smem = 128 + (size_t)G * pitch * sizeof(uint64_t);
+int launch_g(const PopcPlan &p, const Arena &a, cudaStream_t st) {
+    const size_t smem = 128 + (size_t)G * p.pitch * sizeof(uint64_t);
     auto kern = action_popc_kernel<G>;
     CSG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0, per_sm = 0;
@@ -210,10 +210,12 @@ int launch_g(const SetDesc *d_sets, const WorkItem *d_items, int n_items, int pi
         return CSG_E_INVAL;
     }
     int grid = sms * per_sm;
-    if (grid > n_items) grid = n_items;
+    if (grid > p.n_items) grid = p.n_items;
+    unsigned int *queue = a.scr<unsigned int>(p.s_queue);
+    CSG_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned int), st));
     stage_begin(CSG_STAGE_ACTION, st);
-    kern<<<grid, kThreads, smem, st>>>(d_sets, d_items, n_items, pitch, queue, hist,
-                                       (long long)nbins);
+    kern<<<grid, kThreads, smem, st>>>(a.tab<SetDesc>(p.t_sets), a.tab<WorkItem>(p.t_items), p.n_items,
+                                       p.pitch, queue, p.hist, (long long)p.nbins);
     stage_end(CSG_STAGE_ACTION, st);
     CSG_CUDA_TRY(cudaGetLastError());
     return CSG_OK;
@@ -224,60 +226,63 @@ int launch_g(const SetDesc *d_sets, const WorkItem *d_items, int n_items, int pi
 // Shared-memory budget for the staged rows of one CTA.
 static constexpr size_t kRowBudget = 200 * 1024;
 
-int action_popc(const SetDesc *sets, int n_sets, cudaStream_t st, unsigned long long *dev_hist,
-                int64_t nbins) {
-    if (n_sets <= 0) return CSG_OK;
+PopcPlan popc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned long long *hist,
+                   int64_t nbins, int *rc) {
+    PopcPlan p;
+    *rc = CSG_OK;
+    p.n_sets = n;
+    p.s_counters = s_counters;
+    p.hist = hist;
+    p.nbins = nbins;
     int64_t maxw = 0;
-    for (int s = 0; s < n_sets; ++s) {
-        int64_t w = (sets[s].N + 63) / 64 + 2;
-        if (w > maxw) maxw = w;
-    }
-    const int pitch = (int)((maxw + 1) & ~int64_t(1));
+    for (int s = 0; s < n; ++s) maxw = std::max<int64_t>(maxw, (sets[s].N + 63) / 64 + 2);
+    p.pitch = (int)((maxw + 1) & ~int64_t(1));
     int G = 16;
-    while (G > 1 && (size_t)G * pitch * 8 > kRowBudget) G >>= 1;
-    if ((size_t)G * pitch * 8 > kRowBudget) {
+    while (G > 1 && (size_t)G * p.pitch * 8 > kRowBudget) G >>= 1;
+    if ((size_t)G * p.pitch * 8 > kRowBudget) {
         set_error("action_popc: rows of %lld words do not fit shared memory", (long long)maxw);
-        return CSG_E_INVAL;
+        *rc = CSG_E_INVAL;
+        return p;
     }
-    // work items: groups of G rows over each set's row range, sets in order
+    p.G = G;
+    // work items: groups of G rows over each set's row range
     std::vector<WorkItem> items;
-    for (int s = 0; s < n_sets; ++s) {
-        int64_t lo = sets[s].row_lo, hi = sets[s].row_hi;
-        if (hi > sets[s].N) hi = sets[s].N;
-        if (lo < 0) lo = 0;
+    for (int s = 0; s < n; ++s) {
+        int64_t lo = std::max<int64_t>(0, sets[s].row_lo), hi = std::min<int64_t>(sets[s].N, sets[s].row_hi);
         for (int64_t i0 = lo / G * G; i0 < hi; i0 += G) items.push_back(WorkItem{s, 0, i0});
     }
-    if (items.empty()) return CSG_OK;
     if (items.size() > 0x7fffffff) {
         set_error("action_popc: too many work items");
-        return CSG_E_INVAL;
+        *rc = CSG_E_INVAL;
+        return p;
     }
-    const int n_items = (int)items.size();
     // longest first: an item's work grows with the number of later rows
-    std::stable_sort(items.begin(), items.end(), [&](const WorkItem &a, const WorkItem &b) {
-        const int64_t ra = sets[a.set].N - a.i0, rb = sets[b.set].N - b.i0;
-        return ra * (sets[a.set].N) > rb * (sets[b.set].N);
+    std::stable_sort(items.begin(), items.end(), [&](const WorkItem &x, const WorkItem &y) {
+        const int64_t rx = sets[x.set].N - x.i0, ry = sets[y.set].N - y.i0;
+        return rx * sets[x.set].N > ry * sets[y.set].N;
     });
-    char *scratch = nullptr;
-    const size_t bytes = 256 + n_sets * sizeof(SetDesc) + items.size() * sizeof(WorkItem);
-    CSG_CUDA_TRY(cudaMallocAsync((void **)&scratch, bytes, st));
-    unsigned int *queue = reinterpret_cast<unsigned int *>(scratch);
-    SetDesc *d_sets = reinterpret_cast<SetDesc *>(scratch + 256);
-    WorkItem *d_items = reinterpret_cast<WorkItem *>(scratch + 256 + n_sets * sizeof(SetDesc));
-    cudaMemsetAsync(queue, 0, 256, st);
-    cudaMemcpyAsync(d_sets, sets, n_sets * sizeof(SetDesc), cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
-                    st);
-    int rc;
-    switch (G) {
-        case 16: rc = launch_g<16>(d_sets, d_items, n_items, pitch, queue, dev_hist, nbins, st); break;
-        case 8: rc = launch_g<8>(d_sets, d_items, n_items, pitch, queue, dev_hist, nbins, st); break;
-        case 4: rc = launch_g<4>(d_sets, d_items, n_items, pitch, queue, dev_hist, nbins, st); break;
-        case 2: rc = launch_g<2>(d_sets, d_items, n_items, pitch, queue, dev_hist, nbins, st); break;
-        default: rc = launch_g<1>(d_sets, d_items, n_items, pitch, queue, dev_hist, nbins, st); break;
+    p.n_items = (int)items.size();
+    p.t_sets = a.put(sets, n * sizeof(SetDesc));
+    p.t_items = a.put(items.data(), items.size() * sizeof(WorkItem));
+    p.s_queue = a.reserve(sizeof(unsigned int));
+    return p;
+}
+
+void popc_patch(const PopcPlan &p, Arena &a) {
+    SetDesc *d = a.host<SetDesc>(p.t_sets);
+    for (int s = 0; s < p.n_sets; ++s)
+        d[s].counters = a.scr<unsigned long long>(p.s_counters) + (size_t)s * CNT_WORDS;
+}
+
+int popc_launch(const PopcPlan &p, const Arena &a, cudaStream_t st) {
+    if (p.n_items == 0) return CSG_OK;
+    switch (p.G) {
+        case 16: return launch_g<16>(p, a, st);
+        case 8: return launch_g<8>(p, a, st);
+        case 4: return launch_g<4>(p, a, st);
+        case 2: return launch_g<2>(p, a, st);
+        default: return launch_g<1>(p, a, st);
     }
-    cudaFreeAsync(scratch, st);
-    return rc;
 }
 
 }  // namespace csg

@@ -40,6 +40,7 @@
 #include <tuple>
 #include <vector>
 
+#include "arena.h"
 #include "csg_internal.cuh"
 #include "ptx.cuh"
 
@@ -61,67 +62,78 @@ constexpr uint8_t kOne = 0x38;   // 1.0 in fp8 e4m3
 constexpr int SUPER = 2048;      // rasterisation block (elements per side)
 
 struct TcTile {
+    int32_t set;     // index into the launch's set table
     int32_t ti, tj;  // rows [BM ti, BM ti + BM), columns [BN tj, BN tj + BN)
+    int32_t pad;
 };
 
 struct TcArgs {
-    const uint64_t *rows;  // packed symmetric bitmap
-    int64_t N, stride;
-    int64_t row_lo, row_hi;
-    unsigned long long *counters;
-    unsigned long long *hist;
-    long long nbins;
+    const TcSetDesc *sets;
+    const CUtensorMap *maps;  // 2 per set: U, P (global memory, 128-byte aligned)
     const TcTile *tiles;
     int n_tiles;
+    unsigned long long *hist;  // optional full histogram (single-set launches)
+    long long nbins;
 };
 
 // ------------------------------------------------------------------ expand
 
-__global__ void expand_kernel(const uint64_t *__restrict__ rows, int64_t N, int64_t stride,
-                              int64_t kp, uint8_t *__restrict__ U, uint8_t *__restrict__ P) {
-    const int64_t wpr = kp / 64;  // words per expanded row
-    const int64_t total = N * wpr;
+__device__ __forceinline__ int find_set(const int64_t *__restrict__ starts, int n, int64_t g) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (starts[mid] <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void put64(uint8_t *dst, uint64_t m) {
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t v[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const uint32_t nib = (uint32_t)(m >> (16 * q + 4 * h)) & 0xFu;
+            v[h] = ((nib & 1u) ? (uint32_t)kOne : 0u) | ((nib & 2u) ? (uint32_t)kOne << 8 : 0u) |
+                   ((nib & 4u) ? (uint32_t)kOne << 16 : 0u) | ((nib & 8u) ? (uint32_t)kOne << 24 : 0u);
+        }
+        d4[q] = make_uint4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+// One thread per packed word of the sets [set_lo, set_lo + nset): writes the 64 fp8
+// bytes of U and of P the word covers, where the product reads them.
+__global__ void expand_kernel(const TcSetDesc *__restrict__ sets, const int64_t *__restrict__ wstarts,
+                              int set_lo, int nset, int64_t total) {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
          g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = g / wpr, w = g - i * wpr;
+        const int ls = find_set(wstarts, nset, g);
+        const TcSetDesc S = sets[set_lo + ls];
+        const int64_t wpr = S.kp / 64;
+        const int64_t gl = g - wstarts[ls];
+        const int64_t i = gl / wpr, w = gl - i * wpr;
         const int64_t k0 = w * 64;
-        const uint64_t word = rows[i * stride + w];
+        const uint64_t word = S.rows[i * S.stride + w];
         // U row i is read from column BM*floor(i/BM); P row i up to column BN*(floor(i/BN)+1)
-        const bool needU = k0 + 64 > (i / BM) * BM;
-        const bool needP = k0 < (i / BN + 1) * BN;
-        if (needU) {
+        if (k0 + 64 > (i / BM) * BM) {
             uint64_t m = word;
-            if (k0 + 63 <= i) m = 0;
-            else if (k0 <= i) m &= ~((2ull << (i - k0)) - 1ull);  // keep k > i
-            uint4 *dst = reinterpret_cast<uint4 *>(U + i * kp + k0);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                uint32_t v[4];
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const uint32_t nib = (uint32_t)(m >> (16 * q + 4 * h)) & 0xFu;
-                    v[h] = ((nib & 1u) ? (uint32_t)kOne : 0u) | ((nib & 2u) ? (uint32_t)kOne << 8 : 0u) |
-                           ((nib & 4u) ? (uint32_t)kOne << 16 : 0u) | ((nib & 8u) ? (uint32_t)kOne << 24 : 0u);
-                }
-                dst[q] = make_uint4(v[0], v[1], v[2], v[3]);
-            }
+            if (k0 + 63 <= i)
+                m = 0;
+            else if (k0 <= i)
+                m &= ~((2ull << (i - k0)) - 1ull);  // keep k > i
+            put64(S.U + i * S.kp + k0, m);
         }
-        if (needP) {
+        if (k0 < (i / BN + 1) * BN) {
             uint64_t m = word;
-            if (k0 >= i) m = 0;
-            else if (k0 + 63 >= i) m &= (1ull << (i - k0)) - 1ull;  // keep k < i
-            uint4 *dst = reinterpret_cast<uint4 *>(P + i * kp + k0);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                uint32_t v[4];
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const uint32_t nib = (uint32_t)(m >> (16 * q + 4 * h)) & 0xFu;
-                    v[h] = ((nib & 1u) ? (uint32_t)kOne : 0u) | ((nib & 2u) ? (uint32_t)kOne << 8 : 0u) |
-                           ((nib & 4u) ? (uint32_t)kOne << 16 : 0u) | ((nib & 8u) ? (uint32_t)kOne << 24 : 0u);
-                }
-                dst[q] = make_uint4(v[0], v[1], v[2], v[3]);
-            }
+            if (k0 >= i)
+                m = 0;
+            else if (k0 + 63 >= i)
+                m &= (1ull << (i - k0)) - 1ull;  // keep k < i
+            put64(S.P + i * S.kp + k0, m);
         }
     }
 }
@@ -188,6 +200,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
         : "r"(addr))
 
 __device__ __forceinline__ void k_range(const TcTile &t, int64_t N, int &kt0, int &kt1) {
+    // K runs from the tile's first row to its last column (or N)
     const int64_t I0 = (int64_t)t.ti * BM;
     const int64_t J1 = min((int64_t)(t.tj + 1) * BN, N);
     kt0 = (int)(I0 / BK);
@@ -195,8 +208,7 @@ __device__ __forceinline__ void k_range(const TcTile &t, int64_t N, int &kt0, in
 }
 
 __global__ void __launch_bounds__(THREADS, 1)
-action_tc_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmP,
-                 const TcArgs args) {
+action_tc_kernel(const TcArgs args) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -229,7 +241,6 @@ action_tc_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int64_t N = args.N;
     bool bad = false;
 
     if (warp == 0) {
@@ -239,7 +250,8 @@ action_tc_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant_
             for (int t = blockIdx.x; t < args.n_tiles && !bad; t += gridDim.x) {
                 const TcTile tile = args.tiles[t];
                 int kt0, kt1;
-                k_range(tile, N, kt0, kt1);
+                k_range(tile, args.sets[tile.set].N, kt0, kt1);
+                const CUtensorMap *mU = args.maps + 2 * tile.set, *mP = mU + 1;
                 for (int kt = kt0; kt < kt1; ++kt) {
                     if (!ptx::mbar_wait_bounded(&empty[s], ph ^ 1u, kWaitNs)) {
                         bad = true;
@@ -247,8 +259,8 @@ action_tc_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant_
                     }
                     ptx::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
                     unsigned char *st = base + s * STAGE_BYTES;
-                    tma_load_2d(st, &tmU, kt * BK, tile.ti * BM, &full[s]);
-                    tma_load_2d(st + A_BYTES, &tmP, kt * BK, tile.tj * BN, &full[s]);
+                    tma_load_2d(st, mU, kt * BK, tile.ti * BM, &full[s]);
+                    tma_load_2d(st + A_BYTES, mP, kt * BK, tile.tj * BN, &full[s]);
                     if (++s == STAGES) {
                         s = 0;
                         ph ^= 1u;
@@ -263,7 +275,7 @@ action_tc_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant_
             for (int t = blockIdx.x; t < args.n_tiles && !bad; t += gridDim.x) {
                 const TcTile tile = args.tiles[t];
                 int kt0, kt1;
-                k_range(tile, N, kt0, kt1);
+                k_range(tile, args.sets[tile.set].N, kt0, kt1);
                 if (!ptx::mbar_wait_bounded(&tempty[b], bph ^ 1u, kWaitNs)) {
                     bad = true;
                     break;
@@ -300,9 +312,39 @@ action_tc_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant_
         const int q = warp & 3;
         const int r = q * 32 + lane;
         unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, cR = 0, cM = 0, cW = 0;
+        int cur = -1;  // set whose counters are being accumulated
+        auto flush = [&](int set) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+                c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+                c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+                c3 += __shfl_xor_sync(0xffffffffu, c3, o);
+                cR += __shfl_xor_sync(0xffffffffu, cR, o);
+                cM += __shfl_xor_sync(0xffffffffu, cM, o);
+                cW += __shfl_xor_sync(0xffffffffu, cW, o);
+            }
+            if (lane == 0 && cR) {
+                unsigned long long *cnt = args.sets[set].counters;
+                atomicAdd(&cnt[CNT_N0], c0);
+                atomicAdd(&cnt[CNT_N1], c1);
+                atomicAdd(&cnt[CNT_N2], c2);
+                atomicAdd(&cnt[CNT_N3], c3);
+                atomicAdd(&cnt[CNT_R], cR);
+                atomicAdd(&cnt[CNT_SUM_M], cM);
+                atomicAdd(&cnt[CNT_W], cW);
+            }
+            c0 = c1 = c2 = c3 = cR = cM = cW = 0;
+        };
         uint32_t b = 0, bph = 0;
         for (int t = blockIdx.x; t < args.n_tiles; t += gridDim.x) {
             const TcTile tile = args.tiles[t];
+            if (tile.set != cur) {
+                if (cur >= 0) flush(cur);
+                cur = tile.set;
+            }
+            const TcSetDesc S = args.sets[tile.set];
+            const int64_t N = S.N;
             const bool ok = ptx::mbar_wait_bounded(&tfull[b], bph, kWaitNs);
             if (!__all_sync(0xffffffffu, ok)) {
                 bad = true;
@@ -311,10 +353,10 @@ action_tc_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant_
             tc_fence_after();
             const int64_t i = (int64_t)tile.ti * BM + r;
             const int64_t J0 = (int64_t)tile.tj * BN;
-            const bool row_ok = i < N && i >= args.row_lo && i < args.row_hi;
+            const bool row_ok = i < N && i >= S.row_lo && i < S.row_hi;
             uint64_t w4[4] = {0, 0, 0, 0};
             if (row_ok) {
-                const uint64_t *src = args.rows + i * args.stride + J0 / 64;
+                const uint64_t *src = S.rows + i * S.stride + J0 / 64;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) w4[u] = (J0 + 64 * u < N) ? __ldg(src + u) : 0ull;
             }
@@ -326,7 +368,7 @@ action_tc_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant_
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 uint32_t bits = (uint32_t)(w4[c >> 6] >> (c & 32));
                 // only columns j > i
-                const int64_t rel = i - (J0 + c);  // bits q with q > rel survive
+                const int64_t rel = i - (J0 + c);  // bits u with u > rel survive
                 if (rel >= 31)
                     bits = 0;
                 else if (rel >= 0)
@@ -354,32 +396,14 @@ action_tc_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant_
             b ^= 1u;
             if (b == 0) bph ^= 1u;
         }
-        // warp-reduce the counters and flush
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            c0 += __shfl_xor_sync(0xffffffffu, c0, o);
-            c1 += __shfl_xor_sync(0xffffffffu, c1, o);
-            c2 += __shfl_xor_sync(0xffffffffu, c2, o);
-            c3 += __shfl_xor_sync(0xffffffffu, c3, o);
-            cR += __shfl_xor_sync(0xffffffffu, cR, o);
-            cM += __shfl_xor_sync(0xffffffffu, cM, o);
-            cW += __shfl_xor_sync(0xffffffffu, cW, o);
-        }
-        if (lane == 0 && cR) {
-            unsigned long long *cnt = args.counters;
-            atomicAdd(&cnt[CNT_N0], c0);
-            atomicAdd(&cnt[CNT_N1], c1);
-            atomicAdd(&cnt[CNT_N2], c2);
-            atomicAdd(&cnt[CNT_N3], c3);
-            atomicAdd(&cnt[CNT_R], cR);
-            atomicAdd(&cnt[CNT_SUM_M], cM);
-            atomicAdd(&cnt[CNT_W], cW);
-        }
+        if (cur >= 0) flush(cur);
     }
     if (bad) atomicExch(bad_flag, 1);
     tc_fence_before();
     __syncthreads();
-    if (*bad_flag && threadIdx.x == 0) atomicExch(&args.counters[CNT_ERR], 1ull);
+    if (*bad_flag && threadIdx.x == 0 && args.n_tiles > 0)
+        atomicExch(&args.sets[args.tiles[blockIdx.x < args.n_tiles ? blockIdx.x : 0].set].counters[CNT_ERR],
+                   CNT_ERR_TIMEOUT);
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
@@ -400,7 +424,63 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
     return fn;
 }
 
-int make_map(CUtensorMap *m, void *base, int64_t rows, int64_t kp, int box_rows) {
+
+struct TileKey {
+    int64_t ext;
+    int bi, bj;
+    TcTile t;
+};
+
+// Output tiles of the upper triangle of one set, with their sort keys: longest K
+// first at the granularity of SUPER x SUPER blocks, column-major inside a block (tiles
+// sharing a P panel run together).
+void set_tiles(int set, int64_t N, int64_t row_lo, int64_t row_hi, std::vector<TileKey> &keys) {
+    const int NI = (int)((N + BM - 1) / BM), NJ = (int)((N + BN - 1) / BN);
+    for (int ti = 0; ti < NI; ++ti) {
+        const int64_t I0 = (int64_t)ti * BM, I1 = I0 + BM;
+        if (I1 <= row_lo || I0 >= row_hi) continue;
+        for (int tj = ti / 2; tj < NJ; ++tj) {
+            const int64_t J1 = std::min<int64_t>((int64_t)(tj + 1) * BN, N);
+            if (J1 <= I0 + 1) continue;  // no pair i < j in the tile
+            const int bi = (int)(I0 / SUPER), bj = (int)(((int64_t)tj * BN) / SUPER);
+            const int64_t ext = (int64_t)(bj + 1) * SUPER - (int64_t)bi * SUPER;
+            keys.push_back(TileKey{ext, bi, bj, TcTile{set, ti, tj, 0}});
+        }
+    }
+}
+
+bool key_before(const TileKey &a, const TileKey &b) {
+    if (a.ext != b.ext) return a.ext > b.ext;
+    if (a.t.set != b.t.set) return a.t.set < b.t.set;
+    if (a.bi != b.bi) return a.bi < b.bi;
+    if (a.bj != b.bj) return a.bj < b.bj;
+    if (a.t.tj != b.t.tj) return a.t.tj < b.t.tj;
+    return a.t.ti < b.t.ti;
+}
+
+// Sorted tile lists of single sets, kept per (N, row range): a set of N = 65536 has
+// ~65k tiles whose construction would otherwise stall every call.
+struct TileCache {
+    std::mutex mu;
+    std::map<std::tuple<int64_t, int64_t, int64_t>, std::vector<TcTile>> lists;
+};
+TileCache g_tiles;
+
+std::vector<TcTile> single_set_tiles(int64_t N, int64_t lo, int64_t hi) {
+    std::lock_guard<std::mutex> g(g_tiles.mu);
+    auto key = std::make_tuple(N, lo, hi);
+    auto it = g_tiles.lists.find(key);
+    if (it != g_tiles.lists.end()) return it->second;
+    if (g_tiles.lists.size() >= 256) g_tiles.lists.clear();
+    std::vector<TileKey> keys;
+    set_tiles(0, N, lo, hi, keys);
+    std::sort(keys.begin(), keys.end(), key_before);
+    std::vector<TcTile> tiles(keys.size());
+    for (size_t k = 0; k < keys.size(); ++k) tiles[k] = keys[k].t;
+    return g_tiles.lists[key] = std::move(tiles);
+}
+
+int encode_map(CUtensorMap *m, void *base, int64_t rows, int64_t kp, int box_rows) {
     auto enc = get_encoder();
     if (!enc) {
         set_error("action_tc: cuTensorMapEncodeTiled is unavailable");
@@ -420,143 +500,139 @@ int make_map(CUtensorMap *m, void *base, int64_t rows, int64_t kp, int box_rows)
     return CSG_OK;
 }
 
-// Output tiles of the upper triangle, longest K first at the granularity of
-// SUPER x SUPER blocks, column-major inside a block (tiles sharing a P panel run
-// together).
-std::vector<TcTile> make_tiles(int64_t N, int64_t row_lo, int64_t row_hi) {
-    const int NI = (int)((N + BM - 1) / BM), NJ = (int)((N + BN - 1) / BN);
-    struct Key {
-        int64_t ext;
-        int bi, bj, tj, ti;
-    };
-    std::vector<Key> keys;
-    for (int ti = 0; ti < NI; ++ti) {
-        const int64_t I0 = (int64_t)ti * BM, I1 = I0 + BM;
-        if (I1 <= row_lo || I0 >= row_hi) continue;
-        for (int tj = ti / 2; tj < NJ; ++tj) {
-            const int64_t J1 = std::min<int64_t>((int64_t)(tj + 1) * BN, N);
-            if (J1 <= I0 + 1) continue;  // no pair i < j in the tile
-            const int bi = (int)(I0 / SUPER), bj = (int)(((int64_t)tj * BN) / SUPER);
-            const int64_t ext = (int64_t)(bj + 1) * SUPER - (int64_t)bi * SUPER;
-            keys.push_back(Key{ext, bi, bj, tj, ti});
-        }
-    }
-    std::sort(keys.begin(), keys.end(), [](const Key &a, const Key &b) {
-        if (a.ext != b.ext) return a.ext > b.ext;
-        if (a.bi != b.bi) return a.bi < b.bi;
-        if (a.bj != b.bj) return a.bj < b.bj;
-        if (a.tj != b.tj) return a.tj < b.tj;
-        return a.ti < b.ti;
-    });
-    std::vector<TcTile> tiles(keys.size());
-    for (size_t k = 0; k < keys.size(); ++k) tiles[k] = TcTile{keys[k].ti, keys[k].tj};
-    return tiles;
-}
-
-// Device copies of tile lists, kept per (device, N, row range): building and
-// sorting a list of ~10^5 tiles on the host would otherwise stall every call.
-struct TileCache {
-    std::mutex mu;
-    std::map<std::tuple<int, int64_t, int64_t, int64_t>, std::pair<TcTile *, int>> lists;
-};
-TileCache g_tiles;
-
-int cached_tiles(int64_t N, int64_t lo, int64_t hi, const TcTile **out, int *n, cudaStream_t st) {
-    int dev = 0;
-    CSG_CUDA_TRY(cudaGetDevice(&dev));
-    auto key = std::make_tuple(dev, N, lo, hi);
-    std::lock_guard<std::mutex> g(g_tiles.mu);
-    auto it = g_tiles.lists.find(key);
-    if (it != g_tiles.lists.end()) {
-        *out = it->second.first;
-        *n = it->second.second;
-        return CSG_OK;
-    }
-    if (g_tiles.lists.size() >= 64) {
-        // drop every cached list (rare: more than 64 distinct shapes in one process)
-        CSG_CUDA_TRY(cudaStreamSynchronize(st));
-        for (auto &kv : g_tiles.lists) cudaFree(kv.second.first);
-        g_tiles.lists.clear();
-    }
-    std::vector<TcTile> tiles = make_tiles(N, lo, hi);
-    TcTile *d = nullptr;
-    if (!tiles.empty()) {
-        CSG_CUDA_TRY(cudaMalloc((void **)&d, tiles.size() * sizeof(TcTile)));
-        CSG_CUDA_TRY(cudaMemcpy(d, tiles.data(), tiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice));
-    }
-    g_tiles.lists[key] = std::make_pair(d, (int)tiles.size());
-    *out = d;
-    *n = (int)tiles.size();
-    return CSG_OK;
-}
-
 }  // namespace
 
 // Largest N the tensor form accepts: its fp8 operands take 2 N^2 bytes of scratch.
 static constexpr int64_t kTcMaxN = 1 << 17;
+// Operand scratch shared by the sets of one chunk (a larger single set gets its own).
+static constexpr int64_t kChunkBytes = 16ll << 30;
 
-int action_tc(const SetDesc *sets, int n_sets, cudaStream_t st, unsigned long long *dev_hist,
-              int64_t nbins) {
-    for (int s = 0; s < n_sets; ++s) {
+TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned long long *hist,
+               int64_t nbins, int *rc) {
+    TcPlan p;
+    *rc = CSG_OK;
+    p.n_sets = n;
+    p.s_counters = s_counters;
+    p.hist = hist;
+    p.nbins = nbins;
+    std::vector<TcSetDesc> desc(n);
+    int64_t chunk_bytes = 0, max_chunk = 0;
+    TcPlan::Chunk cur;
+    cur.set_lo = 0;
+    for (int s = 0; s < n; ++s) {
         const SetDesc &S = sets[s];
-        const int64_t N = S.N;
-        if (N > kTcMaxN) {
-            set_error("action_tc: N=%lld exceeds the tensor form's limit %lld", (long long)N,
+        if (S.N > kTcMaxN) {
+            set_error("action_tc: N=%lld exceeds the tensor form's limit %lld", (long long)S.N,
                       (long long)kTcMaxN);
-            return CSG_E_INVAL;
+            *rc = CSG_E_INVAL;
+            return p;
         }
-        const int64_t lo = std::max<int64_t>(0, S.row_lo), hi = std::min<int64_t>(N, S.row_hi);
-        if (hi <= lo) continue;
-        const int64_t kp = (N + BK - 1) / BK * BK;  // expanded row pitch in bytes
-        const TcTile *d_tiles = nullptr;
-        int n_tiles = 0;
-        int trc = cached_tiles(N, lo, hi, &d_tiles, &n_tiles, st);
-        if (trc != CSG_OK) return trc;
-        if (n_tiles == 0) continue;
-        uint8_t *ops = nullptr;
-        const size_t op_bytes = 2 * (size_t)N * kp;
-        CSG_CUDA_TRY(cudaMallocAsync((void **)&ops, op_bytes, st));
-        uint8_t *U = ops, *P = ops + (size_t)N * kp;
-        const int64_t words = N * (kp / 64);
-        int blocks = (int)std::min<int64_t>((words + 255) / 256, 152 * 32);
-        stage_begin(CSG_STAGE_EXPAND, st);
-        expand_kernel<<<blocks, 256, 0, st>>>(S.rows, N, S.stride, kp, U, P);
-        stage_end(CSG_STAGE_EXPAND, st);
-        CUtensorMap mU, mP;
-        int rc = make_map(&mU, U, N, kp, BM);
-        if (rc == CSG_OK) rc = make_map(&mP, P, N, kp, BN);
-        if (rc == CSG_OK) {
-            TcArgs a;
-            a.rows = S.rows;
-            a.N = N;
-            a.stride = S.stride;
-            a.row_lo = lo;
-            a.row_hi = hi;
-            a.counters = S.counters;
-            a.hist = dev_hist;
-            a.nbins = nbins;
-            a.tiles = d_tiles;
-            a.n_tiles = n_tiles;
-            const size_t smem = 1024 + STAGES * STAGE_BYTES + 256;
-            cudaError_t ae =
-                cudaFuncSetAttribute(action_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            int dev = 0, sms = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const int grid = std::min(sms, n_tiles);
-            if (ae == cudaSuccess) {
-                stage_begin(CSG_STAGE_ACTION, st);
-                action_tc_kernel<<<grid, THREADS, smem, st>>>(mU, mP, a);
-                stage_end(CSG_STAGE_ACTION, st);
-                ae = cudaGetLastError();
-            }
-            if (ae != cudaSuccess) {
-                set_error("action_tc launch: %s", cudaGetErrorString(ae));
-                rc = CSG_E_CUDA;
-            }
+        TcSetDesc &D = desc[s];
+        D.rows = S.rows;
+        D.N = S.N;
+        D.stride = S.stride;
+        D.row_lo = std::max<int64_t>(0, S.row_lo);
+        D.row_hi = std::min<int64_t>(S.N, S.row_hi);
+        D.counters = nullptr;
+        D.kp = (S.N + BK - 1) / BK * BK;
+        const int64_t ob = 2 * S.N * D.kp;
+        if (s > cur.set_lo && chunk_bytes + ob > kChunkBytes) {
+            cur.set_hi = s;
+            p.chunks.push_back(cur);
+            max_chunk = std::max(max_chunk, chunk_bytes);
+            cur = TcPlan::Chunk();
+            cur.set_lo = s;
+            chunk_bytes = 0;
         }
-        cudaFreeAsync(ops, st);
+        D.U = reinterpret_cast<uint8_t *>(chunk_bytes);           // offsets, patched later
+        D.P = reinterpret_cast<uint8_t *>(chunk_bytes + S.N * D.kp);
+        chunk_bytes += ob;
+    }
+    cur.set_hi = n;
+    p.chunks.push_back(cur);
+    max_chunk = std::max(max_chunk, chunk_bytes);
+    p.t_sets = a.put(desc.data(), n * sizeof(TcSetDesc));
+    p.t_maps = a.put(nullptr, 2 * (size_t)n * sizeof(CUtensorMap));
+    p.s_ops = a.reserve((size_t)max_chunk);
+    for (TcPlan::Chunk &c : p.chunks) {
+        std::vector<int64_t> wstarts;
+        int64_t total = 0;
+        std::vector<TileKey> keys;
+        std::vector<TcTile> tiles;
+        for (int s = c.set_lo; s < c.set_hi; ++s) {
+            wstarts.push_back(total);
+            total += desc[s].N * (desc[s].kp / 64);
+        }
+        if (c.set_hi - c.set_lo == 1) {
+            const TcSetDesc &D = desc[c.set_lo];
+            if (D.row_hi > D.row_lo) {
+                tiles = single_set_tiles(D.N, D.row_lo, D.row_hi);
+                for (TcTile &t : tiles) t.set = c.set_lo;
+            }
+        } else {
+            for (int s = c.set_lo; s < c.set_hi; ++s)
+                if (desc[s].row_hi > desc[s].row_lo) set_tiles(s, desc[s].N, desc[s].row_lo, desc[s].row_hi, keys);
+            std::sort(keys.begin(), keys.end(), key_before);
+            tiles.resize(keys.size());
+            for (size_t k = 0; k < keys.size(); ++k) tiles[k] = keys[k].t;
+        }
+        if (tiles.size() > 0x7fffffff) {
+            set_error("action_tc: too many tiles");
+            *rc = CSG_E_INVAL;
+            return p;
+        }
+        c.words = total;
+        c.t_wstarts = a.put(wstarts.data(), wstarts.size() * sizeof(int64_t));
+        c.n_tiles = (int)tiles.size();
+        c.t_tiles = a.put(tiles.data(), tiles.size() * sizeof(TcTile));
+    }
+    return p;
+}
+
+int tc_patch(const TcPlan &p, Arena &a) {
+    TcSetDesc *desc = a.host<TcSetDesc>(p.t_sets);
+    CUtensorMap *maps = a.host<CUtensorMap>(p.t_maps);
+    uint8_t *ops = a.scr<uint8_t>(p.s_ops);
+    for (int s = 0; s < p.n_sets; ++s) {
+        TcSetDesc &D = desc[s];
+        D.counters = a.scr<unsigned long long>(p.s_counters) + (size_t)s * CNT_WORDS;
+        D.U = ops + reinterpret_cast<uintptr_t>(D.U);
+        D.P = ops + reinterpret_cast<uintptr_t>(D.P);
+        int rc = encode_map(&maps[2 * s], D.U, D.N, D.kp, BM);
+        if (rc == CSG_OK) rc = encode_map(&maps[2 * s + 1], D.P, D.N, D.kp, BN);
         if (rc != CSG_OK) return rc;
+    }
+    return CSG_OK;
+}
+
+int tc_launch(const TcPlan &p, const Arena &a, cudaStream_t st) {
+    const size_t smem = 1024 + STAGES * STAGE_BYTES + 256;
+    CSG_CUDA_TRY(cudaFuncSetAttribute(action_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0;
+    CSG_CUDA_TRY(cudaGetDevice(&dev));
+    CSG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const TcSetDesc *d_sets = a.tab<TcSetDesc>(p.t_sets);
+    for (const TcPlan::Chunk &c : p.chunks) {
+        if (c.words > 0) {
+            const int blocks = (int)std::min<int64_t>((c.words + 255) / 256, (int64_t)sms * 32);
+            stage_begin(CSG_STAGE_EXPAND, st);
+            expand_kernel<<<blocks, 256, 0, st>>>(d_sets, a.tab<int64_t>(c.t_wstarts), c.set_lo,
+                                                  c.set_hi - c.set_lo, c.words);
+            stage_end(CSG_STAGE_EXPAND, st);
+        }
+        if (c.n_tiles > 0) {
+            TcArgs args;
+            args.sets = d_sets;
+            args.maps = a.tab<CUtensorMap>(p.t_maps);
+            args.tiles = a.tab<TcTile>(c.t_tiles);
+            args.n_tiles = c.n_tiles;
+            args.hist = p.hist;
+            args.nbins = (long long)p.nbins;
+            stage_begin(CSG_STAGE_ACTION, st);
+            action_tc_kernel<<<std::min(sms, c.n_tiles), THREADS, smem, st>>>(args);
+            stage_end(CSG_STAGE_ACTION, st);
+        }
+        CSG_CUDA_TRY(cudaGetLastError());
     }
     return CSG_OK;
 }

@@ -22,104 +22,6 @@ void set_error(const char *fmt, ...) {
     va_end(ap);
 }
 
-namespace {
-
-// Forms the action from the counters (a6 of the path): the integer combination in
-// int64, then one double multiply (Eq. s_local for d=2; (4/sqrt6) for d=4).
-struct FinRow {
-    int32_t d;
-    int32_t pad;
-    int64_t N;
-    const unsigned long long *counters;
-};
-
-__global__ void finalize_kernel(const FinRow *__restrict__ rows, int n, csg_result *__restrict__ out) {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        const FinRow F = rows[s];
-        const unsigned long long *c = F.counters;
-        csg_result r;
-        r.d = F.d;
-        r.status = c[CNT_ERR] ? CSG_E_TIMEOUT : CSG_OK;
-        r.N = F.N;
-        r.R = c[CNT_R];
-        for (int k = 0; k < 4; ++k) r.Nk[k] = c[CNT_N0 + k];
-        r.sum_m = c[CNT_SUM_M];
-        r.W = c[CNT_W];
-        const long long n0 = (long long)c[CNT_N0], n1 = (long long)c[CNT_N1],
-                        n2 = (long long)c[CNT_N2], n3 = (long long)c[CNT_N3];
-        if (F.d == 2) {
-            r.combo = F.N - 2 * n0 + 4 * n1 - 2 * n2;
-            r.S = __dmul_rn(2.0, __ll2double_rn(r.combo));
-        } else {
-            r.combo = F.N - n0 + 9 * n1 - 16 * n2 + 8 * n3;
-            r.S = __dmul_rn(__ddiv_rn(4.0, __dsqrt_rn(6.0)), __ll2double_rn(r.combo));
-        }
-        out[s] = r;
-    }
-}
-
-}  // namespace
-
-// Runs the action for n sets (already linked) and writes n results to host `out`.
-int run_actions(csg_set *const *sets, int n, int method, int64_t row_lo, int64_t row_hi,
-                unsigned long long *dev_hist, int64_t nbins, csg_result *out, cudaStream_t st) {
-    if (n <= 0) return CSG_OK;
-    std::vector<SetDesc> desc(n);
-    std::vector<FinRow> fin(n);
-    char *scratch = nullptr;
-    const size_t cnt_bytes = (size_t)n * CNT_WORDS * sizeof(unsigned long long);
-    const size_t bytes = cnt_bytes + n * sizeof(FinRow) + n * sizeof(csg_result) + 64;
-    CSG_CUDA_TRY(cudaMallocAsync((void **)&scratch, bytes, st));
-    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(scratch);
-    FinRow *d_fin = reinterpret_cast<FinRow *>(scratch + cnt_bytes);
-    csg_result *d_out = reinterpret_cast<csg_result *>(scratch + cnt_bytes + n * sizeof(FinRow));
-    for (int s = 0; s < n; ++s) {
-        desc[s].rows = sets[s]->rows;
-        desc[s].N = sets[s]->N;
-        desc[s].stride = sets[s]->stride;
-        desc[s].counters = cnt + (size_t)s * CNT_WORDS;
-        desc[s].row_lo = row_lo < 0 ? 0 : row_lo;
-        desc[s].row_hi = row_hi < 0 ? sets[s]->N : std::min<int64_t>(row_hi, sets[s]->N);
-        fin[s].d = sets[s]->d;
-        fin[s].pad = 0;
-        fin[s].N = sets[s]->N;
-        fin[s].counters = desc[s].counters;
-    }
-    cudaMemsetAsync(cnt, 0, cnt_bytes, st);
-    cudaMemcpyAsync(d_fin, fin.data(), n * sizeof(FinRow), cudaMemcpyHostToDevice, st);
-    int rc;
-    if (method == CSG_POPC)
-        rc = action_popc(desc.data(), n, st, dev_hist, nbins);
-    else
-        rc = action_tc(desc.data(), n, st, dev_hist, nbins);
-    if (rc == CSG_OK) {
-        stage_begin(CSG_STAGE_FINALIZE, st);
-        finalize_kernel<<<(n + 127) / 128, 128, 0, st>>>(d_fin, n, d_out);
-        stage_end(CSG_STAGE_FINALIZE, st);
-        cudaError_t le = cudaGetLastError();
-        if (le != cudaSuccess) {
-            set_error("finalize launch: %s", cudaGetErrorString(le));
-            rc = CSG_E_CUDA;
-        } else {
-            cudaMemcpyAsync(out, d_out, n * sizeof(csg_result), cudaMemcpyDeviceToHost, st);
-        }
-    }
-    cudaFreeAsync(scratch, st);
-    cudaError_t se = cudaStreamSynchronize(st);
-    if (rc == CSG_OK && se != cudaSuccess) {
-        set_error("action: %s", cudaGetErrorString(se));
-        rc = CSG_E_CUDA;
-    }
-    if (rc == CSG_OK) {
-        for (int s = 0; s < n; ++s)
-            if (out[s].status != CSG_OK) {
-                set_error("action: a bounded device wait expired (set %d)", s);
-                rc = out[s].status;
-            }
-    }
-    return rc;
-}
-
 // ------------------------------------------------------------------ sets
 
 int alloc_set(csg_ctx *ctx, int d, int64_t N, csg_set **out) {
@@ -233,6 +135,7 @@ void csg_finalize(csg_ctx *ctx) {
     serve_shutdown(ctx);
     cudaSetDevice(ctx->device);
     destroy_timer(ctx);
+    free_batch_graph(ctx);
     std::vector<csg_set *> all;
     {
         std::lock_guard<std::mutex> g(ctx->mu);
@@ -250,7 +153,7 @@ int csg_sprinkle(csg_ctx *ctx, int d, int64_t N, uint64_t seed, uint64_t seq, vo
     csg_set *s = nullptr;
     int rc = alloc_set(ctx, d, N, &s);
     if (rc != CSG_OK) return rc;
-    SprinkleSpec sp{d, 0, N, seed, seq, s->coords, 0};
+    SprinkleSpec sp{d, 0, N, seed, seq, s->coords, nullptr};
     rc = sprinkle_sort_batch(&sp, 1, (cudaStream_t)stream, nullptr);
     if (rc != CSG_OK) {
         free_set(s);
@@ -282,7 +185,7 @@ int csg_set_from_coords(csg_ctx *ctx, int d, int64_t N, const double *host_coord
     csg_set *s = nullptr;
     int rc = alloc_set(ctx, d, N, &s);
     if (rc != CSG_OK) return rc;
-    SprinkleSpec sp{d, 0, N, 0, 0, s->coords, 0};
+    SprinkleSpec sp{d, 0, N, 0, 0, s->coords, nullptr};
     const double *hc[1] = {host_coords};
     rc = sprinkle_sort_batch(&sp, 1, (cudaStream_t)stream, hc);
     if (rc != CSG_OK) {
@@ -406,22 +309,18 @@ int csg_run_batch(csg_ctx *ctx, int n, const int32_t *d, const int64_t *N, const
         set_error("csg_run_batch: bad arguments");
         return CSG_E_INVAL;
     }
-    CSG_CUDA_TRY(cudaSetDevice(ctx->device));
-    TimerScope ts(ctx);
-    cudaStream_t st = (cudaStream_t)stream;
-    std::vector<csg_set *> sets;
-    int rc = CSG_OK;
-    for (int s = 0; s < n && rc == CSG_OK; ++s) {
-        csg_set *x = nullptr;
-        rc = alloc_set(ctx, d[s], N[s], &x);
-        if (rc == CSG_OK) {
-            x->coord_scale = 1.0;
-            sets.push_back(x);
+    for (int s = 0; s < n; ++s)
+        if ((d[s] != 2 && d[s] != 4) || N[s] < 1 || N[s] > CSG_MAX_N) {
+            set_error("csg_run_batch: bad spec %d (d=%d, N=%lld)", s, d[s], (long long)N[s]);
+            return CSG_E_INVAL;
         }
+    if (method != CSG_POPC && method != CSG_TC) {
+        set_error("csg_run_batch: bad method");
+        return CSG_E_INVAL;
     }
-    if (rc == CSG_OK) rc = run_pipeline(sets.data(), n, seed, seq, method, out, st);
-    for (csg_set *x : sets) free_set(x);
-    return rc;
+    CSG_CUDA_TRY(cudaSetDevice(ctx->device));
+    if (n == 0) return CSG_OK;
+    return run_batch_graph(ctx, n, d, N, seed, seq, method, out, (cudaStream_t)stream);
 }
 
 int csg_export_coords(csg_set *set, double *host, size_t cap) {

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/csg.h"
+#include "arena.h"
 
 namespace csg {
 
@@ -36,9 +37,10 @@ enum : int {
     CNT_R,
     CNT_SUM_M,
     CNT_W,
-    CNT_ERR,  // nonzero: a bounded device wait expired or an invariant failed
+    CNT_ERR,  // nonzero: CNT_ERR_TIMEOUT (a bounded device wait expired) or CNT_ERR_REJECT
     CNT_WORDS = 8
 };
+constexpr unsigned long long CNT_ERR_TIMEOUT = 1, CNT_ERR_REJECT = 2;
 
 // One set as the kernels see it.
 struct SetDesc {
@@ -58,16 +60,28 @@ struct WorkItem {
 
 // ---------------------------------------------------------------- kernels
 
-// Sprinkle + sort for a batch of sets sharing one launch sequence.  coords[s] is
-// [4][N_s] doubles (sorted output); seeds per set.  Returns CSG_OK or an error.
+// Sprinkle + sort for a batch of sets sharing one launch sequence.
 struct SprinkleSpec {
     int32_t d;
     int32_t pad;
     int64_t N;
     uint64_t seed, seq;
-    double *coords;     // [4][N] sorted output
-    int64_t key_off;    // offset of this set in the batch's sort arrays
+    double *coords;            // [4][N] sorted output
+    unsigned long long *err;   // per-set error word (the set's CNT_ERR), or null
 };
+struct SprinklePlan {
+    int n = 0;
+    int64_t E = 0, C = 0, maxN = 0;
+    bool from_coords = false;
+    size_t t_rows = 0, t_starts = 0, t_cstarts = 0;
+    size_t s_tmp = 0, s_keys = 0, s_idx = 0, s_err = (size_t)-1;
+    size_t s_counters = (size_t)-1;  // when set: set s reports into its counters' CNT_ERR
+};
+SprinklePlan sprinkle_plan(const SprinkleSpec *specs, int n, Arena &a, bool from_coords,
+                           size_t s_counters = (size_t)-1);
+void sprinkle_patch(const SprinklePlan &p, Arena &a);  // after allocation, before upload
+void sprinkle_launch(const SprinklePlan &p, const Arena &a, cudaStream_t st);
+// standalone: allocate, run, synchronise; host_coords (optional) replaces the sprinkle
 int sprinkle_sort_batch(const SprinkleSpec *specs_host, int n, cudaStream_t st,
                         const double *const *host_coords /*null: sprinkle*/);
 
@@ -79,20 +93,60 @@ struct LinkSpec {
     int64_t stride;
     const double *coords;
     uint64_t *rows;
-    int64_t tile_off;  // first tile index of this set in the batch's tile space
+    int64_t tile_off;    // unused by callers (filled by the plan)
     double coord_scale;  // max(1, max |coordinate|): scales the d=4 float-screen margin
 };
+struct LinkPlan {
+    int n = 0;
+    int64_t T = 0;
+    size_t t_rows = 0, t_starts = 0;
+};
+LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc);
+void link_launch(const LinkPlan &p, const Arena &a, cudaStream_t st);
 int link_batch(const LinkSpec *specs_host, int n, cudaStream_t st);
 
-// Popcount action over a list of sets.  counters must be zeroed by the caller.
-// items == nullptr: one set, items implicit over its row range.
-int action_popc(const SetDesc *sets_host, int n_sets, cudaStream_t st,
-                unsigned long long *dev_hist, int64_t nbins);
+// Arena helpers (stream-ordered allocation; upload of the table image)
+int arena_alloc(Arena &a, cudaStream_t st);
+void arena_upload(Arena &a, cudaStream_t st);
+void arena_free(Arena &a, cudaStream_t st);
 
-// Tensor-core action (masked 0/1 product on tcgen05).  counters must be zeroed by
-// the caller; dev_hist (optional) receives the full interval-size histogram.
-int action_tc(const SetDesc *sets_host, int n_sets, cudaStream_t st, unsigned long long *dev_hist,
-              int64_t nbins);
+// Popcount action over a list of sets.  Per-set counters live in the arena's scratch
+// at s_counters (CNT_WORDS per set) and must be zeroed before the launch.
+struct PopcPlan {
+    int n_sets = 0, n_items = 0, G = 16, pitch = 0;
+    size_t t_sets = 0, t_items = 0, s_queue = 0, s_counters = 0;
+    unsigned long long *hist = nullptr;
+    int64_t nbins = 0;
+};
+PopcPlan popc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned long long *hist,
+                   int64_t nbins, int *rc);
+void popc_patch(const PopcPlan &p, Arena &a);
+int popc_launch(const PopcPlan &p, const Arena &a, cudaStream_t st);
+
+// Tensor-core action (masked 0/1 product on tcgen05), many sets per launch.
+struct TcSetDesc {
+    const uint64_t *rows;
+    int64_t N, stride, row_lo, row_hi;
+    unsigned long long *counters;
+    uint8_t *U, *P;  // fp8 operands (strict future rows, strict past rows), N x kp bytes
+    int64_t kp;      // operand row pitch (N rounded up to 128)
+};
+struct TcPlan {
+    struct Chunk {
+        int set_lo = 0, set_hi = 0, n_tiles = 0;
+        int64_t words = 0;
+        size_t t_wstarts = 0, t_tiles = 0;
+    };
+    int n_sets = 0;
+    size_t t_sets = 0, t_maps = 0, s_ops = 0, s_counters = 0;
+    unsigned long long *hist = nullptr;
+    int64_t nbins = 0;
+    std::vector<Chunk> chunks;
+};
+TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned long long *hist,
+               int64_t nbins, int *rc);
+int tc_patch(const TcPlan &p, Arena &a);
+int tc_launch(const TcPlan &p, const Arena &a, cudaStream_t st);
 
 // ---------------------------------------------------------------- errors
 

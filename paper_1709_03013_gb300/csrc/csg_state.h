@@ -25,6 +25,7 @@ struct csg_set {
 namespace csg {
 struct ServeState;
 struct StageTimer;
+struct BatchGraph;
 }
 
 struct csg_ctx {
@@ -36,6 +37,7 @@ struct csg_ctx {
     std::mutex serve_mu;
     csg::ServeState *serve = nullptr;
     csg::StageTimer *timer = nullptr;  // per-stage CUDA events when timing is on
+    csg::BatchGraph *batch = nullptr;  // the last batch's captured graph and memory
 };
 
 namespace csg {
@@ -53,6 +55,9 @@ int run_pipeline(csg_set *const *sets, int n, const uint64_t *seed, const uint64
                  csg_result *out, cudaStream_t st);
 
 void serve_shutdown(csg_ctx *ctx);
+void free_batch_graph(csg_ctx *ctx);
+int run_batch_graph(csg_ctx *ctx, int n, const int32_t *d, const int64_t *N, const uint64_t *seed,
+                    const uint64_t *seq, int method, csg_result *out, cudaStream_t st);
 void destroy_timer(csg_ctx *ctx);
 
 // Makes the context's stage timer (if any) current for the calling thread.

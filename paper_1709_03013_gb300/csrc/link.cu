@@ -225,11 +225,12 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
 
 }  // namespace
 
-int link_batch(const LinkSpec *specs, int n, cudaStream_t st) {
-    if (n <= 0) return CSG_OK;
+LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
+    LinkPlan p;
+    p.n = n;
+    *rc = CSG_OK;
     std::vector<LinkRow> rows(n);
     std::vector<int64_t> starts(n);
-    int64_t T = 0;
     for (int s = 0; s < n; ++s) {
         LinkRow &L = rows[s];
         L.d = specs[s].d;
@@ -240,33 +241,46 @@ int link_batch(const LinkSpec *specs, int n, cudaStream_t st) {
         L.rows = specs[s].rows;
         L.nb = (L.N + kTile - 1) / kTile;
         L.nbc = L.stride / kTileWords;
-        L.tile_off = T;
+        L.tile_off = p.T;
         L.screen = 1e-5f * (float)(specs[s].coord_scale * specs[s].coord_scale);
         L.pad2 = 0.f;
-        starts[s] = T;
+        starts[s] = p.T;
         if (L.stride % 16 != 0 || L.nbc < L.nb) {
-            set_error("link: stride %lld does not cover N=%lld", (long long)L.stride,
-                      (long long)L.N);
-            return CSG_E_INVAL;
+            set_error("link: stride %lld does not cover N=%lld", (long long)L.stride, (long long)L.N);
+            *rc = CSG_E_INVAL;
+            return p;
         }
-        T += L.nb * L.nbc - L.nb * (L.nb - 1) / 2;
+        p.T += L.nb * L.nbc - L.nb * (L.nb - 1) / 2;
     }
-    if (T == 0) return CSG_OK;
-    if (T > 0x7fffffffLL) {
-        set_error("link: %lld tiles exceed one launch", (long long)T);
-        return CSG_E_INVAL;
+    if (p.T > 0x7fffffffLL) {
+        set_error("link: %lld tiles exceed one launch", (long long)p.T);
+        *rc = CSG_E_INVAL;
+        return p;
     }
-    char *tab = nullptr;
-    CSG_CUDA_TRY(cudaMallocAsync((void **)&tab, n * (sizeof(LinkRow) + sizeof(int64_t)), st));
-    LinkRow *d_rows = (LinkRow *)tab;
-    int64_t *d_starts = (int64_t *)(tab + n * sizeof(LinkRow));
-    cudaMemcpyAsync(d_rows, rows.data(), n * sizeof(LinkRow), cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(d_starts, starts.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    p.t_rows = a.put(rows.data(), n * sizeof(LinkRow));
+    p.t_starts = a.put(starts.data(), n * sizeof(int64_t));
+    return p;
+}
+
+void link_launch(const LinkPlan &p, const Arena &a, cudaStream_t st) {
+    if (p.T == 0) return;
     stage_begin(CSG_STAGE_LINK, st);
-    link_kernel<<<(unsigned)T, kTile, 0, st>>>(d_rows, d_starts, n);
+    link_kernel<<<(unsigned)p.T, kTile, 0, st>>>(a.tab<LinkRow>(p.t_rows), a.tab<int64_t>(p.t_starts), p.n);
     stage_end(CSG_STAGE_LINK, st);
+}
+
+int link_batch(const LinkSpec *specs, int n, cudaStream_t st) {
+    if (n <= 0) return CSG_OK;
+    Arena a;
+    int rc;
+    LinkPlan p = link_plan(specs, n, a, &rc);
+    if (rc != CSG_OK || p.T == 0) return rc;
+    rc = arena_alloc(a, st);
+    if (rc != CSG_OK) return rc;
+    arena_upload(a, st);
+    link_launch(p, a, st);
     cudaError_t le = cudaGetLastError();
-    cudaFreeAsync(tab, st);
+    arena_free(a, st);
     if (le != cudaSuccess) {
         set_error("link launch: %s", cudaGetErrorString(le));
         return CSG_E_CUDA;

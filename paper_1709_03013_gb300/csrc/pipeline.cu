@@ -1,0 +1,310 @@
+// Launch sequences of the whole path over many sets, built on one Arena:
+//   run_actions  -- interval counts + action for linked sets
+//   run_pipeline -- sprinkle, time order, link, counts, action, all batched
+//   batch graphs -- run_pipeline captured once into a CUDA graph and replayed
+// The finalize step (integer combination, one double multiply) runs on the GPU.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "arena.h"
+#include "csg_internal.cuh"
+#include "csg_state.h"
+
+namespace csg {
+
+int arena_alloc(Arena &a, cudaStream_t st) {
+    if (cudaMallocAsync((void **)&a.dev, a.bytes(), st) != cudaSuccess) {
+        cudaGetLastError();
+        a.dev = nullptr;
+        set_error("scratch allocation of %zu bytes failed", a.bytes());
+        return CSG_E_NOMEM;
+    }
+    return CSG_OK;
+}
+
+void arena_upload(Arena &a, cudaStream_t st) {
+    // pageable source: the copy is staged before the call returns
+    if (!a.img.empty()) cudaMemcpyAsync(a.dev, a.img.data(), a.img.size(), cudaMemcpyHostToDevice, st);
+}
+
+void arena_free(Arena &a, cudaStream_t st) {
+    if (a.dev) cudaFreeAsync(a.dev, st);
+    a.dev = nullptr;
+}
+
+namespace {
+
+struct FinRow {
+    int32_t d;
+    int32_t pad;
+    int64_t N;
+    const unsigned long long *counters;
+};
+
+__global__ void finalize_kernel(const FinRow *__restrict__ rows, int n, csg_result *__restrict__ out) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const FinRow F = rows[s];
+        const unsigned long long *c = F.counters;
+        csg_result r;
+        r.d = F.d;
+        r.status = c[CNT_ERR] == 0 ? CSG_OK : (c[CNT_ERR] == CNT_ERR_REJECT ? CSG_E_REJECT : CSG_E_TIMEOUT);
+        r.N = F.N;
+        r.R = c[CNT_R];
+        for (int k = 0; k < 4; ++k) r.Nk[k] = c[CNT_N0 + k];
+        r.sum_m = c[CNT_SUM_M];
+        r.W = c[CNT_W];
+        const long long n0 = (long long)c[CNT_N0], n1 = (long long)c[CNT_N1], n2 = (long long)c[CNT_N2],
+                        n3 = (long long)c[CNT_N3];
+        if (F.d == 2) {
+            r.combo = F.N - 2 * n0 + 4 * n1 - 2 * n2;          // Eq. s_local
+            r.S = __dmul_rn(2.0, __ll2double_rn(r.combo));
+        } else {
+            r.combo = F.N - n0 + 9 * n1 - 16 * n2 + 8 * n3;    // 3+1 BD action
+            r.S = __dmul_rn(__ddiv_rn(4.0, __dsqrt_rn(6.0)), __ll2double_rn(r.combo));
+        }
+        out[s] = r;
+    }
+}
+
+// A launch sequence over n sets: counters, optional sprinkle/link, the count, finalize.
+struct Seq {
+    Arena a;
+    int n = 0, method = CSG_POPC;
+    size_t s_counters = 0, t_fin = 0, s_out = 0;
+    bool with_front = false;  // sprinkle + link before the count
+    SprinklePlan sp;
+    LinkPlan lp;
+    PopcPlan pp;
+    TcPlan tp;
+};
+
+int build_seq(Seq &q, csg_set *const *sets, int n, int method, int64_t row_lo, int64_t row_hi,
+              unsigned long long *hist, int64_t nbins, const uint64_t *seed, const uint64_t *seq) {
+    q.n = n;
+    q.method = method;
+    q.s_counters = q.a.reserve((size_t)n * CNT_WORDS * sizeof(unsigned long long));
+    q.s_out = q.a.reserve((size_t)n * sizeof(csg_result));
+    int rc = CSG_OK;
+    if (seed) {
+        q.with_front = true;
+        std::vector<SprinkleSpec> sp(n);
+        std::vector<LinkSpec> lk(n);
+        for (int s = 0; s < n; ++s) {
+            sp[s] = SprinkleSpec{sets[s]->d, 0, sets[s]->N, seed[s], seq[s], sets[s]->coords, nullptr};
+            lk[s] = LinkSpec{sets[s]->d, 0, sets[s]->N, sets[s]->stride, sets[s]->coords, sets[s]->rows, 0, 1.0};
+        }
+        q.sp = sprinkle_plan(sp.data(), n, q.a, false, q.s_counters);
+        q.lp = link_plan(lk.data(), n, q.a, &rc);
+        if (rc != CSG_OK) return rc;
+    }
+    std::vector<SetDesc> desc(n);
+    std::vector<FinRow> fin(n);
+    for (int s = 0; s < n; ++s) {
+        desc[s].rows = sets[s]->rows;
+        desc[s].N = sets[s]->N;
+        desc[s].stride = sets[s]->stride;
+        desc[s].counters = nullptr;
+        desc[s].row_lo = row_lo < 0 ? 0 : row_lo;
+        desc[s].row_hi = row_hi < 0 ? sets[s]->N : std::min<int64_t>(row_hi, sets[s]->N);
+        fin[s] = FinRow{sets[s]->d, 0, sets[s]->N, nullptr};
+    }
+    if (method == CSG_POPC)
+        q.pp = popc_plan(desc.data(), n, q.a, q.s_counters, hist, nbins, &rc);
+    else
+        q.tp = tc_plan(desc.data(), n, q.a, q.s_counters, hist, nbins, &rc);
+    if (rc != CSG_OK) return rc;
+    q.t_fin = q.a.put(fin.data(), n * sizeof(FinRow));
+    return CSG_OK;
+}
+
+int patch_seq(Seq &q) {
+    if (q.with_front) sprinkle_patch(q.sp, q.a);
+    FinRow *fin = q.a.host<FinRow>(q.t_fin);
+    for (int s = 0; s < q.n; ++s) fin[s].counters = q.a.scr<unsigned long long>(q.s_counters) + (size_t)s * CNT_WORDS;
+    if (q.method == CSG_POPC) {
+        popc_patch(q.pp, q.a);
+        return CSG_OK;
+    }
+    return tc_patch(q.tp, q.a);
+}
+
+// Enqueues the whole sequence; no allocation, no synchronisation.
+int launch_seq(const Seq &q, cudaStream_t st) {
+    CSG_CUDA_TRY(cudaMemsetAsync(q.a.scr<unsigned long long>(q.s_counters), 0,
+                                 (size_t)q.n * CNT_WORDS * sizeof(unsigned long long), st));
+    if (q.with_front) {
+        sprinkle_launch(q.sp, q.a, st);
+        link_launch(q.lp, q.a, st);
+    }
+    int rc = q.method == CSG_POPC ? popc_launch(q.pp, q.a, st) : tc_launch(q.tp, q.a, st);
+    if (rc != CSG_OK) return rc;
+    stage_begin(CSG_STAGE_FINALIZE, st);
+    finalize_kernel<<<(q.n + 127) / 128, 128, 0, st>>>(q.a.tab<FinRow>(q.t_fin), q.n,
+                                                       q.a.scr<csg_result>(q.s_out));
+    stage_end(CSG_STAGE_FINALIZE, st);
+    CSG_CUDA_TRY(cudaGetLastError());
+    return CSG_OK;
+}
+
+int collect(const csg_result *out, int n) {
+    for (int s = 0; s < n; ++s)
+        if (out[s].status != CSG_OK) {
+            set_error(out[s].status == CSG_E_REJECT ? "sprinkle: set %d hit the rejection cap"
+                                                    : "a bounded device wait expired (set %d)",
+                      s);
+            return out[s].status;
+        }
+    return CSG_OK;
+}
+
+int run_seq(csg_set *const *sets, int n, int method, int64_t lo, int64_t hi, unsigned long long *hist,
+            int64_t nbins, const uint64_t *seed, const uint64_t *seq, csg_result *out, cudaStream_t st) {
+    if (n <= 0) return CSG_OK;
+    Seq q;
+    int rc = build_seq(q, sets, n, method, lo, hi, hist, nbins, seed, seq);
+    if (rc != CSG_OK) return rc;
+    rc = arena_alloc(q.a, st);
+    if (rc != CSG_OK) return rc;
+    rc = patch_seq(q);
+    if (rc == CSG_OK) {
+        arena_upload(q.a, st);
+        rc = launch_seq(q, st);
+    }
+    if (rc == CSG_OK) cudaMemcpyAsync(out, q.a.scr<csg_result>(q.s_out), n * sizeof(csg_result),
+                                      cudaMemcpyDeviceToHost, st);
+    arena_free(q.a, st);
+    cudaError_t se = cudaStreamSynchronize(st);
+    if (rc == CSG_OK && se != cudaSuccess) {
+        set_error("action: %s", cudaGetErrorString(se));
+        rc = CSG_E_CUDA;
+    }
+    if (rc == CSG_OK && seed)
+        for (int s = 0; s < n; ++s) sets[s]->linked = true;
+    return rc == CSG_OK ? collect(out, n) : rc;
+}
+
+}  // namespace
+
+int run_actions(csg_set *const *sets, int n, int method, int64_t row_lo, int64_t row_hi,
+                unsigned long long *dev_hist, int64_t nbins, csg_result *out, cudaStream_t st) {
+    return run_seq(sets, n, method, row_lo, row_hi, dev_hist, nbins, nullptr, nullptr, out, st);
+}
+
+int run_pipeline(csg_set *const *sets, int n, const uint64_t *seed, const uint64_t *seq, int method,
+                 csg_result *out, cudaStream_t st) {
+    return run_seq(sets, n, method, -1, -1, nullptr, 0, seed, seq, out, st);
+}
+
+// ------------------------------------------------------------------ batch graphs
+
+struct BatchGraph {
+    std::vector<int32_t> d;
+    std::vector<int64_t> N;
+    std::vector<uint64_t> seed, seq;
+    int method = 0;
+    std::vector<csg_set *> sets;
+    Seq q;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    csg_result *pinned = nullptr;
+};
+
+void free_batch_graph(csg_ctx *ctx) {
+    BatchGraph *g = ctx->batch;
+    if (!g) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->pinned) cudaFreeHost(g->pinned);
+    if (g->q.a.dev) cudaFree(g->q.a.dev);
+    for (csg_set *s : g->sets) free_set(s);
+    delete g;
+    ctx->batch = nullptr;
+}
+
+static int build_batch_graph(csg_ctx *ctx, int n, const int32_t *d, const int64_t *N, const uint64_t *seed,
+                             const uint64_t *seq, int method, BatchGraph **out) {
+    BatchGraph *g = new BatchGraph();
+    g->d.assign(d, d + n);
+    g->N.assign(N, N + n);
+    g->seed.assign(seed, seed + n);
+    g->seq.assign(seq, seq + n);
+    g->method = method;
+    int rc = CSG_OK;
+    for (int s = 0; s < n && rc == CSG_OK; ++s) {
+        csg_set *x = nullptr;
+        rc = alloc_set(ctx, d[s], N[s], &x);
+        if (rc == CSG_OK) g->sets.push_back(x);
+    }
+    if (rc == CSG_OK) rc = build_seq(g->q, g->sets.data(), n, method, -1, -1, nullptr, 0, seed, seq);
+    if (rc == CSG_OK && cudaMalloc((void **)&g->q.a.dev, g->q.a.bytes()) != cudaSuccess) {
+        cudaGetLastError();
+        g->q.a.dev = nullptr;
+        set_error("batch: scratch allocation of %zu bytes failed", g->q.a.bytes());
+        rc = CSG_E_NOMEM;
+    }
+    if (rc == CSG_OK) rc = patch_seq(g->q);
+    if (rc == CSG_OK && cudaMallocHost((void **)&g->pinned, n * sizeof(csg_result)) != cudaSuccess) {
+        cudaGetLastError();
+        g->pinned = nullptr;
+        set_error("batch: pinned result buffer allocation failed");
+        rc = CSG_E_NOMEM;
+    }
+    cudaStream_t cap = nullptr;
+    if (rc == CSG_OK && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+        set_error("batch: stream creation failed");
+        rc = CSG_E_CUDA;
+    }
+    if (rc == CSG_OK) {
+        cudaMemcpy(g->q.a.dev, g->q.a.img.data(), g->q.a.img.size(), cudaMemcpyHostToDevice);
+        TimerScope no_timing(nullptr);
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            set_error("batch: stream capture could not begin");
+            rc = CSG_E_CUDA;
+        } else {
+            int lrc = launch_seq(g->q, cap);
+            cudaMemcpyAsync(g->pinned, g->q.a.scr<csg_result>(g->q.s_out), n * sizeof(csg_result),
+                            cudaMemcpyDeviceToHost, cap);
+            cudaError_t ce = cudaStreamEndCapture(cap, &g->graph);
+            if (lrc != CSG_OK) {
+                rc = lrc;
+            } else if (ce != cudaSuccess ||
+                       cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) {
+                set_error("batch: graph capture failed: %s", cudaGetErrorString(ce));
+                rc = CSG_E_CUDA;
+            }
+        }
+        cudaStreamDestroy(cap);
+    }
+    *out = g;
+    return rc;
+}
+
+// Runs the batch through a cached CUDA graph (built on the first call with these specs).
+int run_batch_graph(csg_ctx *ctx, int n, const int32_t *d, const int64_t *N, const uint64_t *seed,
+                    const uint64_t *seq, int method, csg_result *out, cudaStream_t st) {
+    BatchGraph *g = ctx->batch;
+    const bool same = g && g->method == method && (int)g->d.size() == n &&
+                      std::equal(d, d + n, g->d.begin()) && std::equal(N, N + n, g->N.begin()) &&
+                      std::equal(seed, seed + n, g->seed.begin()) && std::equal(seq, seq + n, g->seq.begin());
+    if (!same) {
+        free_batch_graph(ctx);
+        BatchGraph *ng = nullptr;
+        int rc = build_batch_graph(ctx, n, d, N, seed, seq, method, &ng);
+        ctx->batch = ng;
+        if (rc != CSG_OK) {
+            free_batch_graph(ctx);
+            return rc;
+        }
+        g = ng;
+    }
+    CSG_CUDA_TRY(cudaGraphLaunch(g->exec, st));
+    CSG_CUDA_TRY(cudaStreamSynchronize(st));
+    std::copy(g->pinned, g->pinned + n, out);
+    return collect(out, n);
+}
+
+}  // namespace csg

@@ -24,24 +24,6 @@
 
 namespace csg {
 
-int run_pipeline(csg_set *const *sets, int n, const uint64_t *seed, const uint64_t *seq, int method,
-                 csg_result *out, cudaStream_t st) {
-    if (n <= 0) return CSG_OK;
-    std::vector<SprinkleSpec> sp(n);
-    std::vector<LinkSpec> lk(n);
-    for (int s = 0; s < n; ++s) {
-        sp[s] = SprinkleSpec{sets[s]->d, 0, sets[s]->N, seed[s], seq[s], sets[s]->coords, 0};
-        lk[s] = LinkSpec{sets[s]->d, 0, sets[s]->N, sets[s]->stride, sets[s]->coords, sets[s]->rows,
-                         0, 1.0};
-    }
-    int rc = sprinkle_sort_batch(sp.data(), n, st, nullptr);
-    if (rc != CSG_OK) return rc;
-    rc = link_batch(lk.data(), n, st);
-    if (rc != CSG_OK) return rc;
-    for (int s = 0; s < n; ++s) sets[s]->linked = true;
-    return run_actions(sets, n, method, -1, -1, nullptr, 0, out, st);
-}
-
 // ------------------------------------------------------------------ service
 
 namespace {

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "arena.h"
 #include "csg_internal.cuh"
 
 namespace csg {
@@ -72,6 +73,7 @@ struct SetRow {
     double *coords;      // sorted output [4][N]
     int64_t off;         // element offset in the flattened batch
     int64_t chunk_off;   // first chunk index of the set
+    unsigned long long *err;  // set to CNT_ERR_REJECT when an element hits the attempt cap
 };
 
 __device__ __forceinline__ int find_set(const int64_t *__restrict__ starts, int n, int64_t g) {
@@ -96,7 +98,7 @@ struct Keys {
 // tmp is [4][E] (row r of set s at tmp + r*E + off).
 __global__ void sprinkle_keys_kernel(const SetRow *__restrict__ sets, const int64_t *__restrict__ starts,
                                      int n, int64_t E, double *__restrict__ tmp, Keys keys,
-                                     int from_coords, int *__restrict__ err) {
+                                     int from_coords) {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < E;
          g += (int64_t)gridDim.x * blockDim.x) {
         const int s = find_set(starts, n, g);
@@ -134,7 +136,7 @@ __global__ void sprinkle_keys_kernel(const SetRow *__restrict__ sets, const int6
                     found = true;
                 }
             }
-            if (!found) atomicExch(err, CSG_E_REJECT);
+            if (!found) atomicExch(S.err, (unsigned long long)CNT_ERR_REJECT);
         }
         if (!from_coords) {
             tmp[g] = c0;
@@ -244,12 +246,15 @@ int grid_for(int64_t E, int threads) {
 
 }  // namespace
 
-int sprinkle_sort_batch(const SprinkleSpec *specs, int n, cudaStream_t st,
-                        const double *const *host_coords) {
-    if (n <= 0) return CSG_OK;
+SprinklePlan sprinkle_plan(const SprinkleSpec *specs, int n, Arena &a, bool from_coords,
+                           size_t s_counters) {
+    SprinklePlan p;
+    p.n = n;
+    p.from_coords = from_coords;
+    p.s_counters = s_counters;
     std::vector<SetRow> rows(n);
-    std::vector<int64_t> starts(n), chunk_starts(n);
-    int64_t E = 0, C = 0, maxN = 0;
+    std::vector<int64_t> starts(n), cstarts(n);
+    bool shared_err = false;
     for (int s = 0; s < n; ++s) {
         rows[s].d = specs[s].d;
         rows[s].pad = 0;
@@ -257,77 +262,95 @@ int sprinkle_sort_batch(const SprinkleSpec *specs, int n, cudaStream_t st,
         rows[s].seed = specs[s].seed;
         rows[s].seq = specs[s].seq;
         rows[s].coords = specs[s].coords;
-        rows[s].off = E;
-        rows[s].chunk_off = C;
-        starts[s] = E;
-        chunk_starts[s] = C;
-        E += specs[s].N;
-        C += (specs[s].N + kChunk - 1) / kChunk;
-        if (specs[s].N > maxN) maxN = specs[s].N;
+        rows[s].off = p.E;
+        rows[s].chunk_off = p.C;
+        rows[s].err = specs[s].err;
+        if (!specs[s].err && s_counters == (size_t)-1) shared_err = true;
+        starts[s] = p.E;
+        cstarts[s] = p.C;
+        p.E += specs[s].N;
+        p.C += (specs[s].N + kChunk - 1) / kChunk;
+        if (specs[s].N > p.maxN) p.maxN = specs[s].N;
     }
-    if (E == 0) return CSG_OK;
-    // one device block: set table, starts, chunk starts, error word
-    size_t tab_bytes = n * sizeof(SetRow) + 2 * n * sizeof(int64_t) + 16;
-    char *tab = nullptr;
-    double *tmp = nullptr;
-    uint64_t *kb = nullptr;
-    uint32_t *ib = nullptr;
-    CSG_CUDA_TRY(cudaMallocAsync((void **)&tab, tab_bytes, st));
-    cudaError_t e1 = cudaMallocAsync((void **)&tmp, 4 * E * sizeof(double), st);
-    cudaError_t e2 = cudaMallocAsync((void **)&kb, 4 * E * sizeof(uint64_t), st);
-    cudaError_t e3 = cudaMallocAsync((void **)&ib, 2 * E * sizeof(uint32_t), st);
-    int rc = CSG_OK;
-    int err_host = 0;
-    SetRow *d_rows = (SetRow *)tab;
-    int64_t *d_starts = (int64_t *)(tab + n * sizeof(SetRow));
-    int64_t *d_cstarts = d_starts + n;
-    int *d_err = (int *)(d_cstarts + n);
-    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
-        set_error("sprinkle: scratch allocation of %lld elements failed", (long long)E);
-        rc = CSG_E_NOMEM;
-        goto done;
+    p.t_rows = a.put(rows.data(), n * sizeof(SetRow));
+    p.t_starts = a.put(starts.data(), n * sizeof(int64_t));
+    p.t_cstarts = a.put(cstarts.data(), n * sizeof(int64_t));
+    p.s_tmp = a.reserve(4 * p.E * sizeof(double));
+    p.s_keys = a.reserve(4 * p.E * sizeof(uint64_t));
+    p.s_idx = a.reserve(2 * p.E * sizeof(uint32_t));
+    p.s_err = shared_err ? a.reserve(sizeof(unsigned long long)) : (size_t)-1;
+    return p;
+}
+
+void sprinkle_patch(const SprinklePlan &p, Arena &a) {
+    SetRow *rows = a.host<SetRow>(p.t_rows);
+    for (int s = 0; s < p.n; ++s) {
+        if (rows[s].err) continue;
+        if (p.s_counters != (size_t)-1)
+            rows[s].err = a.scr<unsigned long long>(p.s_counters) + (size_t)s * CNT_WORDS + CNT_ERR;
+        else
+            rows[s].err = a.scr<unsigned long long>(p.s_err);
     }
-    {
-        // the host tables are pageable; cudaMemcpyAsync stages them before returning
-        cudaMemcpyAsync(d_rows, rows.data(), n * sizeof(SetRow), cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(d_starts, starts.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(d_cstarts, chunk_starts.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice,
-                        st);
-        cudaMemsetAsync(d_err, 0, sizeof(int), st);
-        if (host_coords) {
-            for (int s = 0; s < n; ++s)
-                for (int r = 0; r < 4; ++r)
-                    cudaMemcpyAsync(tmp + r * E + rows[s].off, host_coords[s] + r * rows[s].N,
-                                    rows[s].N * sizeof(double), cudaMemcpyHostToDevice, st);
-        }
-        Keys a{kb, kb + E, ib}, b{kb + 2 * E, kb + 3 * E, ib + E};
-        const int T = 256;
-        stage_begin(CSG_STAGE_SPRINKLE, st);
-        sprinkle_keys_kernel<<<grid_for(E, T), T, 0, st>>>(d_rows, d_starts, n, E, tmp, a,
-                                                           host_coords ? 1 : 0, d_err);
-        chunk_sort_kernel<<<(unsigned)C, kSortThreads, 0, st>>>(d_rows, d_cstarts, n, a, b);
-        Keys cur = b, nxt = a;
-        for (int64_t w = kChunk; w < maxN; w *= 2) {
-            merge_pass_kernel<<<grid_for(E, T), T, 0, st>>>(d_rows, d_starts, n, E, w, cur, nxt);
-            Keys t = cur;
-            cur = nxt;
-            nxt = t;
-        }
-        gather_kernel<<<grid_for(E, T), T, 0, st>>>(d_rows, d_starts, n, E, tmp, cur.idx);
-        stage_end(CSG_STAGE_SPRINKLE, st);
-        cudaError_t le = cudaGetLastError();
-        if (le != cudaSuccess) {
-            set_error("sprinkle/sort launch: %s", cudaGetErrorString(le));
-            rc = CSG_E_CUDA;
-            goto done;
-        }
-        cudaMemcpyAsync(&err_host, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+}
+
+void sprinkle_launch(const SprinklePlan &p, const Arena &a, cudaStream_t st) {
+    if (p.E == 0) return;
+    const int64_t E = p.E;
+    SetRow *d_rows = a.tab<SetRow>(p.t_rows);
+    int64_t *d_starts = a.tab<int64_t>(p.t_starts);
+    int64_t *d_cstarts = a.tab<int64_t>(p.t_cstarts);
+    double *tmp = a.scr<double>(p.s_tmp);
+    uint64_t *kb = a.scr<uint64_t>(p.s_keys);
+    uint32_t *ib = a.scr<uint32_t>(p.s_idx);
+    if (p.s_err != (size_t)-1) cudaMemsetAsync(a.scr<unsigned long long>(p.s_err), 0, sizeof(unsigned long long), st);
+    Keys ka{kb, kb + E, ib}, kb2{kb + 2 * E, kb + 3 * E, ib + E};
+    const int T = 256;
+    stage_begin(CSG_STAGE_SPRINKLE, st);
+    sprinkle_keys_kernel<<<grid_for(E, T), T, 0, st>>>(d_rows, d_starts, p.n, E, tmp, ka,
+                                                       p.from_coords ? 1 : 0);
+    chunk_sort_kernel<<<(unsigned)p.C, kSortThreads, 0, st>>>(d_rows, d_cstarts, p.n, ka, kb2);
+    Keys cur = kb2, nxt = ka;
+    for (int64_t w = kChunk; w < p.maxN; w *= 2) {
+        merge_pass_kernel<<<grid_for(E, T), T, 0, st>>>(d_rows, d_starts, p.n, E, w, cur, nxt);
+        Keys t = cur;
+        cur = nxt;
+        nxt = t;
     }
-done:
-    if (tmp) cudaFreeAsync(tmp, st);
-    if (kb) cudaFreeAsync(kb, st);
-    if (ib) cudaFreeAsync(ib, st);
-    cudaFreeAsync(tab, st);
+    gather_kernel<<<grid_for(E, T), T, 0, st>>>(d_rows, d_starts, p.n, E, tmp, cur.idx);
+    stage_end(CSG_STAGE_SPRINKLE, st);
+}
+
+int sprinkle_sort_batch(const SprinkleSpec *specs, int n, cudaStream_t st,
+                        const double *const *host_coords) {
+    if (n <= 0) return CSG_OK;
+    Arena a;
+    SprinklePlan p = sprinkle_plan(specs, n, a, host_coords != nullptr);
+    if (p.E == 0) return CSG_OK;
+    int rc = arena_alloc(a, st);
+    if (rc != CSG_OK) return rc;
+    sprinkle_patch(p, a);
+    arena_upload(a, st);
+    if (host_coords) {
+        const SetRow *rows = a.host<SetRow>(p.t_rows);
+        double *tmp = a.scr<double>(p.s_tmp);
+        for (int s = 0; s < n; ++s)
+            for (int r = 0; r < 4; ++r)
+                cudaMemcpyAsync(tmp + r * p.E + rows[s].off, host_coords[s] + r * rows[s].N,
+                                rows[s].N * sizeof(double), cudaMemcpyHostToDevice, st);
+    }
+    sprinkle_launch(p, a, st);
+    rc = CSG_OK;
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) {
+        set_error("sprinkle/sort launch: %s", cudaGetErrorString(le));
+        rc = CSG_E_CUDA;
+    }
+    // collect the rejection flags of sets that had no error slot of their own
+    unsigned long long err_host = 0;
+    if (rc == CSG_OK && p.s_err != (size_t)-1)
+        cudaMemcpyAsync(&err_host, a.scr<unsigned long long>(p.s_err), sizeof err_host,
+                        cudaMemcpyDeviceToHost, st);
+    arena_free(a, st);
     cudaError_t se = cudaStreamSynchronize(st);
     if (rc == CSG_OK && se != cudaSuccess) {
         set_error("sprinkle/sort: %s", cudaGetErrorString(se));
@@ -335,7 +358,7 @@ done:
     }
     if (rc == CSG_OK && err_host != 0) {
         set_error("sprinkle: an element hit the 256-attempt rejection cap");
-        rc = err_host;
+        rc = CSG_E_REJECT;
     }
     return rc;
 }
