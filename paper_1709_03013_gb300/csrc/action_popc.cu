@@ -227,9 +227,10 @@ int launch_g(const PopcPlan &p, const Arena &a, cudaStream_t st) {
 static constexpr size_t kRowBudget = 200 * 1024;
 
 PopcPlan popc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned long long *hist,
-                   int64_t nbins, int *rc) {
+                   int64_t nbins, int *rc, const int *slots) {
     PopcPlan p;
     *rc = CSG_OK;
+    if (slots) p.slot.assign(slots, slots + n);
     p.n_sets = n;
     p.s_counters = s_counters;
     p.hist = hist;
@@ -271,7 +272,8 @@ PopcPlan popc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsi
 void popc_patch(const PopcPlan &p, Arena &a) {
     SetDesc *d = a.host<SetDesc>(p.t_sets);
     for (int s = 0; s < p.n_sets; ++s)
-        d[s].counters = a.scr<unsigned long long>(p.s_counters) + (size_t)s * CNT_WORDS;
+        d[s].counters = a.scr<unsigned long long>(p.s_counters) +
+                        (size_t)(p.slot.empty() ? s : p.slot[s]) * CNT_WORDS;
 }
 
 int popc_launch(const PopcPlan &p, const Arena &a, cudaStream_t st) {

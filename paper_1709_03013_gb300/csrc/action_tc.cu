@@ -14,12 +14,15 @@
 //
 // Pass 1 (expand): one thread per packed word writes the 64 fp8 bytes of U and of P
 // it covers; only the column ranges the product reads are written.
-// Pass 2 (product): persistent CTAs, one per SM, walk a list of output tiles
-// (128 rows i x 256 columns j, upper triangle only, K from the first row of the
-// tile to the last column) in a longest-first, 2048 x 2048 block-rasterised order.
+// Pass 2 (product): persistent CTAs, one per SM, take output tiles (128 rows i x 256
+// columns j, upper triangle only, K from the first row of the tile to the last
+// column) from a global work queue (an atomic counter over a tile list ordered set by
+// set, longest first, block-rasterised); claiming tiles in list order keeps the CTAs
+// on the same set's operands, which then stay in L2.
 // Warp roles per CTA:
-//   warp 0     TMA producer: 128-byte-swizzled K tiles of U (128 x 128) and P
-//              (256 x 128) into a 4-stage shared-memory ring (mbarrier complete_tx)
+//   warp 0     claims tiles and passes their indices to warps 1-5 through a 4-slot
+//              shared-memory ring; TMA producer: 128-byte-swizzled K tiles of U
+//              (128 x 128) and P (256 x 128) into a 4-stage ring (mbarrier complete_tx)
 //   warp 1     allocates 512 TMEM columns; one lane issues tcgen05.mma
 //              (kind::f8f6f4, M=128, N=256, K=32, fp32 accumulate) and commits
 //              each stage back to the producer and each finished tile to the epilogue
@@ -59,7 +62,6 @@ constexpr int THREADS = (2 + EPI_WARPS) * 32;
 constexpr uint32_t TMEM_COLS = 2 * BN;
 constexpr uint64_t kWaitNs = 4000000000ull;
 constexpr uint8_t kOne = 0x38;   // 1.0 in fp8 e4m3
-constexpr int SUPER = 2048;      // rasterisation block (elements per side)
 
 struct TcTile {
     int32_t set;     // index into the launch's set table
@@ -72,9 +74,12 @@ struct TcArgs {
     const CUtensorMap *maps;  // 2 per set: U, P (global memory, 128-byte aligned)
     const TcTile *tiles;
     int n_tiles;
+    unsigned int *queue;       // tile counter (zeroed before the launch)
     unsigned long long *hist;  // optional full histogram (single-set launches)
     long long nbins;
 };
+
+constexpr int RING = 4;  // tile indices handed from the producer to the MMA and epilogue warps
 
 // ------------------------------------------------------------------ expand
 
@@ -188,6 +193,14 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_addr(bar)) : "memory");
 }
 
+#define TMEM_LD16(addr, v)                                                                          \
+    asm volatile(                                                                                   \
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),       \
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), \
+          "=r"(v[14]), "=r"(v[15])                                                                  \
+        : "r"(addr))
+
 #define TMEM_LD32(addr, v)                                                                          \
     asm volatile(                                                                                   \
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17," \
@@ -215,7 +228,9 @@ action_tc_kernel(const TcArgs args) {
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + STAGES * STAGE_BYTES);
     uint64_t *full = bars, *empty = bars + STAGES, *tfull = bars + 2 * STAGES,
              *tempty = bars + 2 * STAGES + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 4);
+    uint64_t *rfull = bars + 2 * STAGES + 4, *rempty = rfull + RING;
+    int *ring = reinterpret_cast<int *>(rempty + RING);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ring + RING);
     int *bad_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -227,6 +242,10 @@ action_tc_kernel(const TcArgs args) {
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&tfull[b], 1);
             ptx::mbar_init(&tempty[b], EPI_WARPS * 32);
+        }
+        for (int q = 0; q < RING; ++q) {
+            ptx::mbar_init(&rfull[q], 1);
+            ptx::mbar_init(&rempty[q], 1 + EPI_WARPS * 32);  // the MMA lane and every epilogue thread
         }
         *bad_flag = 0;
         ptx::fence_mbar_init();
@@ -247,7 +266,18 @@ action_tc_kernel(const TcArgs args) {
         if (lane == 0) {
             int s = 0;
             uint32_t ph = 0;
-            for (int t = blockIdx.x; t < args.n_tiles && !bad; t += gridDim.x) {
+            for (int n = 0; !bad; ++n) {
+                // claim the next tile and hand its index to the MMA and epilogue warps
+                const int slot = n % RING;
+                const uint32_t rph = (uint32_t)(n / RING) & 1u;
+                if (!ptx::mbar_wait_bounded(&rempty[slot], rph ^ 1u, kWaitNs)) {
+                    bad = true;
+                    break;
+                }
+                const int t = (int)atomicAdd(args.queue, 1u);
+                ring[slot] = t < args.n_tiles ? t : -1;
+                mbar_arrive(&rfull[slot]);
+                if (t >= args.n_tiles) break;
                 const TcTile tile = args.tiles[t];
                 int kt0, kt1;
                 k_range(tile, args.sets[tile.set].N, kt0, kt1);
@@ -272,7 +302,15 @@ action_tc_kernel(const TcArgs args) {
         if (lane == 0) {
             int s = 0;
             uint32_t ph = 0, b = 0, bph = 0;
-            for (int t = blockIdx.x; t < args.n_tiles && !bad; t += gridDim.x) {
+            for (int n = 0; !bad; ++n) {
+                const int slot = n % RING;
+                if (!ptx::mbar_wait_bounded(&rfull[slot], (uint32_t)(n / RING) & 1u, kWaitNs)) {
+                    bad = true;
+                    break;
+                }
+                const int t = ring[slot];
+                mbar_arrive(&rempty[slot]);
+                if (t < 0) break;
                 const TcTile tile = args.tiles[t];
                 int kt0, kt1;
                 k_range(tile, args.sets[tile.set].N, kt0, kt1);
@@ -311,6 +349,8 @@ action_tc_kernel(const TcArgs args) {
         // epilogue: TMEM lane quarter of this warp
         const int q = warp & 3;
         const int r = q * 32 + lane;
+        // per-thread counters; N0..N3 are packed 16 bits each and spilled into the
+        // 64-bit totals after every tile (a tile holds at most 256 pairs per row)
         unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, cR = 0, cM = 0, cW = 0;
         int cur = -1;  // set whose counters are being accumulated
         auto flush = [&](int set) {
@@ -337,7 +377,16 @@ action_tc_kernel(const TcArgs args) {
             c0 = c1 = c2 = c3 = cR = cM = cW = 0;
         };
         uint32_t b = 0, bph = 0;
-        for (int t = blockIdx.x; t < args.n_tiles; t += gridDim.x) {
+        for (int n = 0;; ++n) {
+            const int slot = n % RING;
+            const bool got = ptx::mbar_wait_bounded(&rfull[slot], (uint32_t)(n / RING) & 1u, kWaitNs);
+            if (!__all_sync(0xffffffffu, got)) {
+                bad = true;
+                break;
+            }
+            const int t = ring[slot];
+            mbar_arrive(&rempty[slot]);
+            if (t < 0) break;
             const TcTile tile = args.tiles[t];
             if (tile.set != cur) {
                 if (cur >= 0) flush(cur);
@@ -345,52 +394,63 @@ action_tc_kernel(const TcArgs args) {
             }
             const TcSetDesc S = args.sets[tile.set];
             const int64_t N = S.N;
+            const int64_t i = (int64_t)tile.ti * BM + r;
+            const int64_t J0 = (int64_t)tile.tj * BN;
+            // the row's relation bits for columns J0..J0+255, fetched before the wait
+            uint64_t w4[4] = {0, 0, 0, 0};
+            if (i < N && i >= S.row_lo && i < S.row_hi) {
+                const uint64_t *src = S.rows + i * S.stride + J0 / 64;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) w4[u] = (J0 + 64 * u < N) ? __ldg(src + u) : 0ull;
+                // only columns j > i
+                const int64_t rel = i - J0;  // bit positions k > rel survive
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t lo = rel - 64 * u;
+                    if (lo >= 63)
+                        w4[u] = 0;
+                    else if (lo >= 0)
+                        w4[u] &= ~((2ull << lo) - 1ull);
+                }
+            }
             const bool ok = ptx::mbar_wait_bounded(&tfull[b], bph, kWaitNs);
             if (!__all_sync(0xffffffffu, ok)) {
                 bad = true;
                 break;
             }
             tc_fence_after();
-            const int64_t i = (int64_t)tile.ti * BM + r;
-            const int64_t J0 = (int64_t)tile.tj * BN;
-            const bool row_ok = i < N && i >= S.row_lo && i < S.row_hi;
-            uint64_t w4[4] = {0, 0, 0, 0};
-            if (row_ok) {
-                const uint64_t *src = S.rows + i * S.stride + J0 / 64;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) w4[u] = (J0 + 64 * u < N) ? __ldg(src + u) : 0ull;
-            }
-#pragma unroll
-            for (int c = 0; c < BN; c += 32) {
-                uint32_t v[32];
+            unsigned long long packed = 0;  // N0..N3 of this tile, 16 bits each
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 16) {
+                uint32_t v[16];
                 const uint32_t addr = tmem + b * BN + (uint32_t)c + ((uint32_t)(q * 32) << 16);
-                TMEM_LD32(addr, v);
+                TMEM_LD16(addr, v);
+                const uint64_t wsel = c < 64 ? w4[0] : (c < 128 ? w4[1] : (c < 192 ? w4[2] : w4[3]));
+                const uint32_t bits = (uint32_t)(wsel >> (c & 63)) & 0xFFFFu;
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                uint32_t bits = (uint32_t)(w4[c >> 6] >> (c & 32));
-                // only columns j > i
-                const int64_t rel = i - (J0 + c);  // bits u with u > rel survive
-                if (rel >= 31)
-                    bits = 0;
-                else if (rel >= 0)
-                    bits &= ~((2u << rel) - 1u);
                 if (bits) {
+                    // R and W of the chunk from bit counts: sum over set bits u of (J0+c+u - i - 1)
+                    const unsigned pc = __popc(bits);
+                    const unsigned su = __popc(bits & 0xAAAAu) + 2u * __popc(bits & 0xCCCCu) +
+                                        4u * __popc(bits & 0xF0F0u) + 8u * __popc(bits & 0xFF00u);
+                    cR += pc;
+                    cW += (unsigned long long)pc * (unsigned long long)(J0 + c - i - 1) + su;
 #pragma unroll
-                    for (int u = 0; u < 32; ++u) {
+                    for (int u = 0; u < 16; ++u) {
                         if (bits >> u & 1u) {
                             const uint32_t m = __float2uint_rn(__uint_as_float(v[u]));
-                            c0 += (m == 0);
-                            c1 += (m == 1);
-                            c2 += (m == 2);
-                            c3 += (m == 3);
-                            cR += 1;
                             cM += m;
-                            cW += (unsigned long long)(J0 + c + u - i - 1);
+                            if (m < 4u) packed += 1ull << (16u * m);
                             if (args.hist != nullptr && (long long)m < args.nbins)
                                 atomicAdd(&args.hist[m], 1ull);
                         }
                     }
                 }
             }
+            c0 += packed & 0xFFFFull;
+            c1 += (packed >> 16) & 0xFFFFull;
+            c2 += (packed >> 32) & 0xFFFFull;
+            c3 += packed >> 48;
             tc_fence_before();
             mbar_arrive(&tempty[b]);
             b ^= 1u;
@@ -402,8 +462,7 @@ action_tc_kernel(const TcArgs args) {
     tc_fence_before();
     __syncthreads();
     if (*bad_flag && threadIdx.x == 0 && args.n_tiles > 0)
-        atomicExch(&args.sets[args.tiles[blockIdx.x < args.n_tiles ? blockIdx.x : 0].set].counters[CNT_ERR],
-                   CNT_ERR_TIMEOUT);
+        atomicExch(&args.sets[args.tiles[0].set].counters[CNT_ERR], CNT_ERR_TIMEOUT);
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
@@ -434,7 +493,7 @@ struct TileKey {
 // Output tiles of the upper triangle of one set, with their sort keys: longest K
 // first at the granularity of SUPER x SUPER blocks, column-major inside a block (tiles
 // sharing a P panel run together).
-void set_tiles(int set, int64_t N, int64_t row_lo, int64_t row_hi, std::vector<TileKey> &keys) {
+void set_tiles(int set, int64_t N, int64_t row_lo, int64_t row_hi, int super, std::vector<TileKey> &keys) {
     const int NI = (int)((N + BM - 1) / BM), NJ = (int)((N + BN - 1) / BN);
     for (int ti = 0; ti < NI; ++ti) {
         const int64_t I0 = (int64_t)ti * BM, I1 = I0 + BM;
@@ -442,8 +501,8 @@ void set_tiles(int set, int64_t N, int64_t row_lo, int64_t row_hi, std::vector<T
         for (int tj = ti / 2; tj < NJ; ++tj) {
             const int64_t J1 = std::min<int64_t>((int64_t)(tj + 1) * BN, N);
             if (J1 <= I0 + 1) continue;  // no pair i < j in the tile
-            const int bi = (int)(I0 / SUPER), bj = (int)(((int64_t)tj * BN) / SUPER);
-            const int64_t ext = (int64_t)(bj + 1) * SUPER - (int64_t)bi * SUPER;
+            const int bi = (int)(I0 / super), bj = (int)(((int64_t)tj * BN) / super);
+            const int64_t ext = (int64_t)(bj + 1) * super - (int64_t)bi * super;
             keys.push_back(TileKey{ext, bi, bj, TcTile{set, ti, tj, 0}});
         }
     }
@@ -462,18 +521,18 @@ bool key_before(const TileKey &a, const TileKey &b) {
 // ~65k tiles whose construction would otherwise stall every call.
 struct TileCache {
     std::mutex mu;
-    std::map<std::tuple<int64_t, int64_t, int64_t>, std::vector<TcTile>> lists;
+    std::map<std::tuple<int64_t, int64_t, int64_t, int>, std::vector<TcTile>> lists;
 };
 TileCache g_tiles;
 
-std::vector<TcTile> single_set_tiles(int64_t N, int64_t lo, int64_t hi) {
+std::vector<TcTile> single_set_tiles(int64_t N, int64_t lo, int64_t hi, int super) {
     std::lock_guard<std::mutex> g(g_tiles.mu);
-    auto key = std::make_tuple(N, lo, hi);
+    auto key = std::make_tuple(N, lo, hi, super);
     auto it = g_tiles.lists.find(key);
     if (it != g_tiles.lists.end()) return it->second;
     if (g_tiles.lists.size() >= 256) g_tiles.lists.clear();
     std::vector<TileKey> keys;
-    set_tiles(0, N, lo, hi, keys);
+    set_tiles(0, N, lo, hi, super, keys);
     std::sort(keys.begin(), keys.end(), key_before);
     std::vector<TcTile> tiles(keys.size());
     for (size_t k = 0; k < keys.size(); ++k) tiles[k] = keys[k].t;
@@ -508,9 +567,11 @@ static constexpr int64_t kTcMaxN = 1 << 17;
 static constexpr int64_t kChunkBytes = 16ll << 30;
 
 TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned long long *hist,
-               int64_t nbins, int *rc) {
+               int64_t nbins, int *rc, const int *slots, int super) {
     TcPlan p;
     *rc = CSG_OK;
+    if (slots) p.slot.assign(slots, slots + n);
+    if (super < BN) super = BN;
     p.n_sets = n;
     p.s_counters = s_counters;
     p.hist = hist;
@@ -554,6 +615,7 @@ TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned
     p.t_sets = a.put(desc.data(), n * sizeof(TcSetDesc));
     p.t_maps = a.put(nullptr, 2 * (size_t)n * sizeof(CUtensorMap));
     p.s_ops = a.reserve((size_t)max_chunk);
+    p.s_queues = a.reserve(p.chunks.size() * sizeof(unsigned int));
     for (TcPlan::Chunk &c : p.chunks) {
         std::vector<int64_t> wstarts;
         int64_t total = 0;
@@ -566,15 +628,21 @@ TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned
         if (c.set_hi - c.set_lo == 1) {
             const TcSetDesc &D = desc[c.set_lo];
             if (D.row_hi > D.row_lo) {
-                tiles = single_set_tiles(D.N, D.row_lo, D.row_hi);
+                tiles = single_set_tiles(D.N, D.row_lo, D.row_hi, super);
                 for (TcTile &t : tiles) t.set = c.set_lo;
             }
         } else {
+            // set by set, largest first: the CTAs running at any moment then work on one or
+            // two sets whose operands stay in L2, and the small sets fill the tail
+            std::vector<int> order;
             for (int s = c.set_lo; s < c.set_hi; ++s)
-                if (desc[s].row_hi > desc[s].row_lo) set_tiles(s, desc[s].N, desc[s].row_lo, desc[s].row_hi, keys);
-            std::sort(keys.begin(), keys.end(), key_before);
-            tiles.resize(keys.size());
-            for (size_t k = 0; k < keys.size(); ++k) tiles[k] = keys[k].t;
+                if (desc[s].row_hi > desc[s].row_lo) order.push_back(s);
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return desc[x].N > desc[y].N; });
+            for (int s : order) {
+                std::vector<TcTile> ts = single_set_tiles(desc[s].N, desc[s].row_lo, desc[s].row_hi, super);
+                for (TcTile &t : ts) t.set = s;
+                tiles.insert(tiles.end(), ts.begin(), ts.end());
+            }
         }
         if (tiles.size() > 0x7fffffff) {
             set_error("action_tc: too many tiles");
@@ -595,7 +663,7 @@ int tc_patch(const TcPlan &p, Arena &a) {
     uint8_t *ops = a.scr<uint8_t>(p.s_ops);
     for (int s = 0; s < p.n_sets; ++s) {
         TcSetDesc &D = desc[s];
-        D.counters = a.scr<unsigned long long>(p.s_counters) + (size_t)s * CNT_WORDS;
+        D.counters = a.scr<unsigned long long>(p.s_counters) + (size_t)(p.slot.empty() ? s : p.slot[s]) * CNT_WORDS;
         D.U = ops + reinterpret_cast<uintptr_t>(D.U);
         D.P = ops + reinterpret_cast<uintptr_t>(D.P);
         int rc = encode_map(&maps[2 * s], D.U, D.N, D.kp, BM);
@@ -606,13 +674,16 @@ int tc_patch(const TcPlan &p, Arena &a) {
 }
 
 int tc_launch(const TcPlan &p, const Arena &a, cudaStream_t st) {
-    const size_t smem = 1024 + STAGES * STAGE_BYTES + 256;
+    const size_t smem = 1024 + STAGES * STAGE_BYTES + 512;
     CSG_CUDA_TRY(cudaFuncSetAttribute(action_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    unsigned int *queues = a.scr<unsigned int>(p.s_queues);
+    CSG_CUDA_TRY(cudaMemsetAsync(queues, 0, p.chunks.size() * sizeof(unsigned int), st));
     int dev = 0, sms = 0;
     CSG_CUDA_TRY(cudaGetDevice(&dev));
     CSG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const TcSetDesc *d_sets = a.tab<TcSetDesc>(p.t_sets);
-    for (const TcPlan::Chunk &c : p.chunks) {
+    for (size_t ci = 0; ci < p.chunks.size(); ++ci) {
+        const TcPlan::Chunk &c = p.chunks[ci];
         if (c.words > 0) {
             const int blocks = (int)std::min<int64_t>((c.words + 255) / 256, (int64_t)sms * 32);
             stage_begin(CSG_STAGE_EXPAND, st);
@@ -626,6 +697,7 @@ int tc_launch(const TcPlan &p, const Arena &a, cudaStream_t st) {
             args.maps = a.tab<CUtensorMap>(p.t_maps);
             args.tiles = a.tab<TcTile>(c.t_tiles);
             args.n_tiles = c.n_tiles;
+            args.queue = queues + ci;
             args.hist = p.hist;
             args.nbins = (long long)p.nbins;
             stage_begin(CSG_STAGE_ACTION, st);

@@ -113,13 +113,14 @@ void arena_free(Arena &a, cudaStream_t st);
 // Popcount action over a list of sets.  Per-set counters live in the arena's scratch
 // at s_counters (CNT_WORDS per set) and must be zeroed before the launch.
 struct PopcPlan {
+    std::vector<int> slot;  // counter slot of each set (empty: identity)
     int n_sets = 0, n_items = 0, G = 16, pitch = 0;
     size_t t_sets = 0, t_items = 0, s_queue = 0, s_counters = 0;
     unsigned long long *hist = nullptr;
     int64_t nbins = 0;
 };
 PopcPlan popc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned long long *hist,
-                   int64_t nbins, int *rc);
+                   int64_t nbins, int *rc, const int *slots = nullptr);
 void popc_patch(const PopcPlan &p, Arena &a);
 int popc_launch(const PopcPlan &p, const Arena &a, cudaStream_t st);
 
@@ -137,14 +138,16 @@ struct TcPlan {
         int64_t words = 0;
         size_t t_wstarts = 0, t_tiles = 0;
     };
+    std::vector<int> slot;  // counter slot of each set (empty: identity)
     int n_sets = 0;
-    size_t t_sets = 0, t_maps = 0, s_ops = 0, s_counters = 0;
+    size_t t_sets = 0, t_maps = 0, s_ops = 0, s_counters = 0, s_queues = 0;
     unsigned long long *hist = nullptr;
     int64_t nbins = 0;
     std::vector<Chunk> chunks;
 };
+// super: side of the square blocks (in elements) in which output tiles are rasterised
 TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned long long *hist,
-               int64_t nbins, int *rc);
+               int64_t nbins, int *rc, const int *slots = nullptr, int super = 2048);
 int tc_patch(const TcPlan &p, Arena &a);
 int tc_launch(const TcPlan &p, const Arena &a, cudaStream_t st);
 

@@ -13,9 +13,12 @@
 //
 // d=4 decisions are the exact IEEE double ones (t_k > t_i and dt*dt > (dx*dx +
 // dy*dy) + dz*dz, separately rounded).  A float screen settles almost every pair
-// first: with coordinates in [-1, 1] the float value of dt^2 - |dx|^2 is within
-// 100 * 2^-24 (< 6e-6) of the real value, and the double expression within
-// 40 * 2^-53 of it, so a float difference beyond +-1e-5 fixes the double decision.
+// first: with coordinates in [-1, 1], rounding them to float moves each difference
+// by at most 4.0001 * 2^-24 and each square by at most 16.004 * 2^-24; the four
+// fused multiply-adds that form dt^2 - ((dx^2 + dy^2) + dz^2) add at most
+// 4 * 4.01 * 2^-24, so the float value is within 80.1 * 2^-24 (< 4.8e-6) of the real
+// one, and the double expression within 40 * 2^-53 of it.  A float difference
+// beyond +-1e-5 therefore fixes the double decision.
 // Pairs inside the margin are decided in double.  Every error term scales with the
 // square of the coordinate range, so sets whose coordinates exceed 1 in magnitude
 // use the margin 1e-5 * max|coordinate|^2 (coordinates are limited to 1e15, far
@@ -81,7 +84,7 @@ __global__ void __launch_bounds__(kTile)
 link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts, int n) {
     __shared__ double cd[4][kTile];       // column coordinates (d=4: t,x,y,z)
     __shared__ uint64_t ck[2][kTile];     // column order keys of u and v (d=2)
-    __shared__ float cf[4][kTile];        // column coordinates in float (d=4)
+    __shared__ float4 cf4[kTile];         // column coordinates in float (d=4): t, x, y, z
     __shared__ uint32_t tb[kTile][9];     // mirrored bits: tb[c][w] = rows 32w..32w+31 of column c
 
     const int s = find_set(starts, n, blockIdx.x);
@@ -114,12 +117,14 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
         }
     } else {
         if (kc < N) {
+            double v[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                double v = S.coords[q * N + kc];
-                cd[q][r] = v;
-                cf[q][r] = __double2float_rn(v);
+                v[q] = S.coords[q * N + kc];
+                cd[q][r] = v[q];
             }
+            cf4[r] = make_float4(__double2float_rn(v[0]), __double2float_rn(v[1]), __double2float_rn(v[2]),
+                                 __double2float_rn(v[3]));
         }
     }
     __syncthreads();
@@ -159,20 +164,15 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
                 for (int b = 0; b < 64; ++b) {
                     const int c = q * 64 + b;
                     if (c >= c0 && c < ncol) {
-                        float dt = __fsub_rn(cf[0][c], tf);
-                        float dx = __fsub_rn(cf[1][c], xf);
-                        float dy = __fsub_rn(cf[2][c], yf);
-                        float dz = __fsub_rn(cf[3][c], zf);
-                        float a = __fmul_rn(dt, dt);
-                        float bsum = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)),
-                                               __fmul_rn(dz, dz));
-                        float diff = __fsub_rn(a, bsum);
-                        bool rel;
-                        if (diff > screen)
-                            rel = true;
-                        else if (diff < -screen)
-                            rel = false;
-                        else
+                        const float4 k4 = cf4[c];
+                        const float dt = __fsub_rn(k4.x, tf);
+                        const float dx = __fsub_rn(k4.y, xf);
+                        const float dy = __fsub_rn(k4.z, yf);
+                        const float dz = __fsub_rn(k4.w, zf);
+                        const float sp = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+                        const float diff = __fmaf_rn(dt, dt, -sp);
+                        bool rel = diff > screen;
+                        if (fabsf(diff) <= screen)
                             rel = exact4(ti, xi, yi, zi, cd[0][c], cd[1][c], cd[2][c], cd[3][c]);
                         if (rel) acc |= 1ull << b;
                     }

@@ -5,7 +5,12 @@
 // The finalize step (integer combination, one double multiply) runs on the GPU.
 #include <cuda_runtime.h>
 
+#include <stdio.h>
+#include <stdlib.h>
+#include <sys/stat.h>
+
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "arena.h"
@@ -68,12 +73,23 @@ __global__ void finalize_kernel(const FinRow *__restrict__ rows, int n, csg_resu
     }
 }
 
+}  // namespace
+
+// Tunable choices of a launch sequence.
+struct Tune {
+    int64_t popc_below = 0;  // with the tensor method, sets with N below this use the popcount kernel
+    int super = 2048;        // rasterisation block of the tensor kernel's output tiles
+};
+
+namespace {
+
 // A launch sequence over n sets: counters, optional sprinkle/link, the count, finalize.
 struct Seq {
     Arena a;
     int n = 0, method = CSG_POPC;
     size_t s_counters = 0, t_fin = 0, s_out = 0;
     bool with_front = false;  // sprinkle + link before the count
+    bool has_popc = false, has_tc = false;
     SprinklePlan sp;
     LinkPlan lp;
     PopcPlan pp;
@@ -81,7 +97,8 @@ struct Seq {
 };
 
 int build_seq(Seq &q, csg_set *const *sets, int n, int method, int64_t row_lo, int64_t row_hi,
-              unsigned long long *hist, int64_t nbins, const uint64_t *seed, const uint64_t *seq) {
+              unsigned long long *hist, int64_t nbins, const uint64_t *seed, const uint64_t *seq,
+              const Tune &tune = Tune()) {
     q.n = n;
     q.method = method;
     q.s_counters = q.a.reserve((size_t)n * CNT_WORDS * sizeof(unsigned long long));
@@ -110,11 +127,26 @@ int build_seq(Seq &q, csg_set *const *sets, int n, int method, int64_t row_lo, i
         desc[s].row_hi = row_hi < 0 ? sets[s]->N : std::min<int64_t>(row_hi, sets[s]->N);
         fin[s] = FinRow{sets[s]->d, 0, sets[s]->N, nullptr};
     }
-    if (method == CSG_POPC)
-        q.pp = popc_plan(desc.data(), n, q.a, q.s_counters, hist, nbins, &rc);
-    else
-        q.tp = tc_plan(desc.data(), n, q.a, q.s_counters, hist, nbins, &rc);
-    if (rc != CSG_OK) return rc;
+    // split the sets between the two kernels (the tensor method sends small sets to the
+    // popcount kernel when tuned to)
+    std::vector<SetDesc> dp, dt;
+    std::vector<int> sp_slot, st_slot;
+    for (int s = 0; s < n; ++s) {
+        const bool pop = method == CSG_POPC || sets[s]->N < tune.popc_below;
+        (pop ? dp : dt).push_back(desc[s]);
+        (pop ? sp_slot : st_slot).push_back(s);
+    }
+    if (!dp.empty()) {
+        q.has_popc = true;
+        q.pp = popc_plan(dp.data(), (int)dp.size(), q.a, q.s_counters, hist, nbins, &rc, sp_slot.data());
+        if (rc != CSG_OK) return rc;
+    }
+    if (!dt.empty()) {
+        q.has_tc = true;
+        q.tp = tc_plan(dt.data(), (int)dt.size(), q.a, q.s_counters, hist, nbins, &rc, st_slot.data(),
+                       tune.super);
+        if (rc != CSG_OK) return rc;
+    }
     q.t_fin = q.a.put(fin.data(), n * sizeof(FinRow));
     return CSG_OK;
 }
@@ -123,11 +155,8 @@ int patch_seq(Seq &q) {
     if (q.with_front) sprinkle_patch(q.sp, q.a);
     FinRow *fin = q.a.host<FinRow>(q.t_fin);
     for (int s = 0; s < q.n; ++s) fin[s].counters = q.a.scr<unsigned long long>(q.s_counters) + (size_t)s * CNT_WORDS;
-    if (q.method == CSG_POPC) {
-        popc_patch(q.pp, q.a);
-        return CSG_OK;
-    }
-    return tc_patch(q.tp, q.a);
+    if (q.has_popc) popc_patch(q.pp, q.a);
+    return q.has_tc ? tc_patch(q.tp, q.a) : CSG_OK;
 }
 
 // Enqueues the whole sequence; no allocation, no synchronisation.
@@ -138,7 +167,8 @@ int launch_seq(const Seq &q, cudaStream_t st) {
         sprinkle_launch(q.sp, q.a, st);
         link_launch(q.lp, q.a, st);
     }
-    int rc = q.method == CSG_POPC ? popc_launch(q.pp, q.a, st) : tc_launch(q.tp, q.a, st);
+    int rc = q.has_popc ? popc_launch(q.pp, q.a, st) : CSG_OK;
+    if (rc == CSG_OK && q.has_tc) rc = tc_launch(q.tp, q.a, st);
     if (rc != CSG_OK) return rc;
     stage_begin(CSG_STAGE_FINALIZE, st);
     finalize_kernel<<<(q.n + 127) / 128, 128, 0, st>>>(q.a.tab<FinRow>(q.t_fin), q.n,
@@ -225,6 +255,126 @@ void free_batch_graph(csg_ctx *ctx) {
     ctx->batch = nullptr;
 }
 
+// ------------------------------------------------------------------ autotuner
+//
+// The first batch of a given shape times a few candidate tunings (which sets go to
+// the popcount kernel, the tensor kernel's rasterisation block) with CUDA events, one
+// untimed and one timed run each, and keeps the fastest.  Choices are remembered per
+// GPU and batch shape in a JSON-lines file ($CSG_AUTOTUNE_CACHE, default
+// ~/.cache/csg/autotune.jsonl); CSG_AUTOTUNE=0 skips tuning.
+
+static std::string tune_key(int n, const int32_t *d, const int64_t *N) {
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    long long sumN = 0, maxN = 0, d2 = 0;
+    for (int s = 0; s < n; ++s) {
+        sumN += N[s];
+        maxN = std::max<long long>(maxN, N[s]);
+        d2 += d[s] == 2;
+    }
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|tc|n=%d|sumN=%lld|maxN=%lld|d2=%lld", prop.name, n, sumN, maxN, d2);
+    return buf;
+}
+
+static std::string tune_path() {
+    const char *p = getenv("CSG_AUTOTUNE_CACHE");
+    if (p && *p) return p;
+    const char *home = getenv("HOME");
+    return std::string(home && *home ? home : "/tmp") + "/.cache/csg/autotune.jsonl";
+}
+
+static bool tune_lookup(const std::string &key, Tune *t) {
+    FILE *f = fopen(tune_path().c_str(), "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (fgets(line, sizeof line, f)) {
+        char k[300];
+        long long pb = 0;
+        int sup = 0;
+        if (sscanf(line, "{\"key\": \"%299[^\"]\", \"popc_below\": %lld, \"super\": %d", k, &pb, &sup) == 3 &&
+            key == k) {
+            t->popc_below = pb;
+            t->super = sup;
+            found = true;  // the last entry wins
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+static void tune_store(const std::string &key, const Tune &t, double ms) {
+    const std::string path = tune_path();
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos) {
+        std::string dir = path.substr(0, slash);
+        for (size_t q = 1; q <= dir.size(); ++q)
+            if (q == dir.size() || dir[q] == '/') mkdir(dir.substr(0, q).c_str(), 0755);
+    }
+    FILE *f = fopen(path.c_str(), "a");
+    if (!f) return;
+    fprintf(f, "{\"key\": \"%s\", \"popc_below\": %lld, \"super\": %d, \"ms\": %.3f}\n", key.c_str(),
+            (long long)t.popc_below, t.super, ms);
+    fclose(f);
+}
+
+static int autotune(csg_ctx *ctx, csg_set *const *sets, int n, const int32_t *d, const int64_t *N,
+                    const uint64_t *seed, const uint64_t *seq, Tune *best) {
+    (void)ctx;
+    const char *env = getenv("CSG_AUTOTUNE");
+    if (env && env[0] == '0') return CSG_OK;
+    const std::string key = tune_key(n, d, N);
+    if (tune_lookup(key, best)) return CSG_OK;
+    const Tune cands[] = {{0, 2048}, {1024, 2048}, {2048, 2048}, {0, 1024}};
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        set_error("autotune: stream/event creation failed");
+        return CSG_E_CUDA;
+    }
+    TimerScope no_timing(nullptr);
+    float best_ms = -1.f;
+    int rc = CSG_OK;
+    for (const Tune &t : cands) {
+        Seq q;
+        rc = build_seq(q, sets, n, CSG_TC, -1, -1, nullptr, 0, seed, seq, t);
+        if (rc != CSG_OK) break;
+        rc = arena_alloc(q.a, st);
+        if (rc != CSG_OK) break;
+        rc = patch_seq(q);
+        float ms = 0.f;
+        if (rc == CSG_OK) {
+            arena_upload(q.a, st);
+            rc = launch_seq(q, st);  // untimed: first touch of memory and caches
+            if (rc == CSG_OK) {
+                cudaEventRecord(e0, st);
+                rc = launch_seq(q, st);
+                cudaEventRecord(e1, st);
+            }
+        }
+        arena_free(q.a, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess && rc == CSG_OK) {
+            set_error("autotune: a candidate run failed");
+            rc = CSG_E_CUDA;
+        }
+        if (rc != CSG_OK) break;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best_ms < 0.f || ms < best_ms) {
+            best_ms = ms;
+            *best = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    if (rc == CSG_OK && best_ms >= 0.f) tune_store(key, *best, best_ms);
+    return rc;
+}
+
 static int build_batch_graph(csg_ctx *ctx, int n, const int32_t *d, const int64_t *N, const uint64_t *seed,
                              const uint64_t *seq, int method, BatchGraph **out) {
     BatchGraph *g = new BatchGraph();
@@ -239,7 +389,9 @@ static int build_batch_graph(csg_ctx *ctx, int n, const int32_t *d, const int64_
         rc = alloc_set(ctx, d[s], N[s], &x);
         if (rc == CSG_OK) g->sets.push_back(x);
     }
-    if (rc == CSG_OK) rc = build_seq(g->q, g->sets.data(), n, method, -1, -1, nullptr, 0, seed, seq);
+    Tune tune;
+    if (rc == CSG_OK && method == CSG_TC) rc = autotune(ctx, g->sets.data(), n, d, N, seed, seq, &tune);
+    if (rc == CSG_OK) rc = build_seq(g->q, g->sets.data(), n, method, -1, -1, nullptr, 0, seed, seq, tune);
     if (rc == CSG_OK && cudaMalloc((void **)&g->q.a.dev, g->q.a.bytes()) != cudaSuccess) {
         cudaGetLastError();
         g->q.a.dev = nullptr;

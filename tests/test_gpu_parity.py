@@ -212,3 +212,20 @@ def test_cancel_and_unknown_ticket(ctx, csg):
         assert ctx.serve_poll(t, 60000) is not None
     for b in big:
         assert ctx.serve_poll(b, 120000) is not None
+
+
+def test_batch_autotune_records_choice(csg, tmp_path, monkeypatch):
+    # the first batch of a shape times candidate tunings and records the winner; every
+    # candidate gives the same counts, so the results stay exact whichever wins
+    cache = tmp_path / "autotune.jsonl"
+    monkeypatch.setenv("CSG_AUTOTUNE_CACHE", str(cache))
+    specs = inputs.batch_workload(n_sets=30, seed=5, lo=300, hi=2600)
+    tup = [(sp.d, sp.N, sp.seed, sp.seq) for sp in specs]
+    with csg.Context(0) as c:
+        got = c.run_batch(tup, csg.TC)
+        again = c.run_batch(tup, csg.TC)          # replay of the captured graph
+    assert got == again
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == 1 and '"popc_below"' in lines[0] and '"super"' in lines[0]
+    for sp, r in list(zip(specs, got))[:5]:
+        _check_result(r, oracle.run(sp.d, sp.N, sp.seed, sp.seq), sp.d, sp.N)
