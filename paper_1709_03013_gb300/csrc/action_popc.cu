@@ -42,6 +42,95 @@ struct Smem {
     int stop;
 };
 
+struct Counters {
+    unsigned long long n0 = 0, n1 = 0, n2 = 0, n3 = 0, R = 0, M = 0, W = 0;
+};
+
+// The K group rows related to j (the set bits of mask) against row j: each lane takes
+// word pairs (2 lane, 2 lane + 1) + 64 t, so every load is 16 bytes, and the K staged
+// rows are compile-time slots (no per-row branches in the loop).  Lane 0 books the
+// pairs' interval sizes after a warp reduction.
+template <int K>
+__device__ __forceinline__ void sweep_rows(uint32_t mask, const uint64_t *__restrict__ A, int pitch,
+                                           const uint64_t *__restrict__ bj, int wj, uint64_t lastmask,
+                                           int lane, int64_t j, int64_t i0, Counters &c,
+                                           unsigned long long *__restrict__ hist, long long nbins) {
+    int off[K];
+    uint32_t m = mask;
+    int rsum = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int r = __ffs(m) - 1;
+        m &= m - 1;
+        off[k] = r * pitch;
+        rsum += r;
+    }
+    uint32_t acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0;
+#pragma unroll 2
+    for (int w = 2 * lane; w <= wj; w += 64) {
+        ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2 *>(bj + w));
+        if (w + 1 >= wj) {
+            if (w == wj) {
+                b.x &= lastmask;
+                b.y = 0;
+            } else {
+                b.y &= lastmask;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(A + off[k] + w);
+            acc[k] += __popcll(a.x & b.x) + __popcll(a.y & b.y);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        uint32_t v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+            c.n0 += v == 0u;
+            c.n1 += v == 1u;
+            c.n2 += v == 2u;
+            c.n3 += v == 3u;
+            c.M += v;
+            if (hist != nullptr && (long long)v < nbins) atomicAdd(&hist[v], 1ull);
+        }
+    }
+    if (lane == 0) {
+        c.R += K;
+        // sum over the K rows r of (j - (i0 + r) - 1)
+        c.W += (unsigned long long)K * (unsigned long long)(j - i0 - 1) - (unsigned long long)rsum;
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void dispatch_rows(int cnt, uint32_t mask, const uint64_t *__restrict__ A,
+                                              int pitch, const uint64_t *__restrict__ bj, int wj,
+                                              uint64_t lastmask, int lane, int64_t j, int64_t i0,
+                                              Counters &c, unsigned long long *__restrict__ hist,
+                                              long long nbins) {
+#define CSG_ROWS_CASE(K)                                                                       \
+    case K:                                                                                    \
+        if constexpr (K <= G && K <= 8) sweep_rows<K>(mask, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins); \
+        break;
+    switch (cnt) {
+        CSG_ROWS_CASE(1)
+        CSG_ROWS_CASE(2)
+        CSG_ROWS_CASE(3)
+        CSG_ROWS_CASE(4)
+        CSG_ROWS_CASE(5)
+        CSG_ROWS_CASE(6)
+        CSG_ROWS_CASE(7)
+        CSG_ROWS_CASE(8)
+        default:
+            break;
+    }
+#undef CSG_ROWS_CASE
+}
+
 template <int G>
 __global__ void __launch_bounds__(kThreads, 1)
 action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict__ items,
@@ -118,7 +207,7 @@ action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict_
         __syncthreads();
 
         // ---- sweep later elements j in runs of 32 per warp
-        unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, cR = 0, cM = 0, cW = 0;
+        Counters cnt;
         const int gshift = (int)(i0 & 63);
         const uint32_t Gbits = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
         for (int64_t jb = i0 + 1 + 32 * (int64_t)warp; jb < N; jb += 32 * kWarps) {
@@ -136,61 +225,33 @@ action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict_
                 todo &= todo - 1;
                 const uint32_t mask = __shfl_sync(0xffffffffu, my, src);
                 const int64_t j = jb + src;
-                const int wj = (int)((j >> 6) - w0a);     // last word, relative
+                const int wj = (int)((j >> 6) - w0a);                 // last word, relative
                 const uint64_t lastmask = (1ull << (j & 63)) - 1ull;  // bits k < j
                 const uint64_t *__restrict__ bj = rows + j * stride + w0a;
-                uint32_t acc[G];
+                // at most 8 rows per pass keeps the row slots and sums in registers
+                uint32_t rest = mask;
+                while (rest) {
+                    uint32_t part = rest;
+                    if (__popc(rest) > 8) {
+                        uint32_t t = rest;
 #pragma unroll
-                for (int r = 0; r < G; ++r) acc[r] = 0;
-                int w = lane;
-                for (; w + 32 <= wj; w += 64) {
-                    const uint64_t b0 = __ldg(bj + w);
-                    const uint64_t b1 = __ldg(bj + w + 32);  // may be the last word
-                    const uint64_t b1m = (w + 32 == wj) ? (b1 & lastmask) : b1;
-#pragma unroll
-                    for (int r = 0; r < G; ++r) {
-                        if (mask >> r & 1u) {
-                            const uint64_t *a = A + (size_t)r * pitch;
-                            acc[r] += __popcll(a[w] & b0) + __popcll(a[w + 32] & b1m);
-                        }
+                        for (int k = 0; k < 8; ++k) t &= t - 1;
+                        part = rest & ~t;  // the lowest 8 rows
                     }
-                }
-                if (w <= wj) {
-                    uint64_t b0 = __ldg(bj + w);
-                    if (w == wj) b0 &= lastmask;
-#pragma unroll
-                    for (int r = 0; r < G; ++r)
-                        if (mask >> r & 1u) acc[r] += __popcll(A[(size_t)r * pitch + w] & b0);
-                }
-#pragma unroll
-                for (int r = 0; r < G; ++r) {
-                    if (mask >> r & 1u) {
-                        uint32_t m = acc[r];
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
-                        if (lane == 0) {
-                            c0 += (m == 0);
-                            c1 += (m == 1);
-                            c2 += (m == 2);
-                            c3 += (m == 3);
-                            cR += 1;
-                            cM += m;
-                            cW += (unsigned long long)(j - (i0 + r) - 1);
-                            if (hist != nullptr && (long long)m < nbins) atomicAdd(&hist[m], 1ull);
-                        }
-                    }
+                    rest &= ~part;
+                    dispatch_rows<G>(__popc(part), part, A, pitch, bj, wj, lastmask, lane, j, i0, cnt, hist, nbins);
                 }
             }
         }
-        if (lane == 0 && cR != 0) {
-            unsigned long long *cnt = S.counters;
-            if (c0) atomicAdd(&cnt[CNT_N0], c0);
-            if (c1) atomicAdd(&cnt[CNT_N1], c1);
-            if (c2) atomicAdd(&cnt[CNT_N2], c2);
-            if (c3) atomicAdd(&cnt[CNT_N3], c3);
-            atomicAdd(&cnt[CNT_R], cR);
-            atomicAdd(&cnt[CNT_SUM_M], cM);
-            atomicAdd(&cnt[CNT_W], cW);
+        if (lane == 0 && cnt.R != 0) {
+            unsigned long long *g = S.counters;
+            if (cnt.n0) atomicAdd(&g[CNT_N0], cnt.n0);
+            if (cnt.n1) atomicAdd(&g[CNT_N1], cnt.n1);
+            if (cnt.n2) atomicAdd(&g[CNT_N2], cnt.n2);
+            if (cnt.n3) atomicAdd(&g[CNT_N3], cnt.n3);
+            atomicAdd(&g[CNT_R], cnt.R);
+            atomicAdd(&g[CNT_SUM_M], cnt.M);
+            atomicAdd(&g[CNT_W], cnt.W);
         }
         __syncthreads();  // the staged rows are reused by the next item
     }
