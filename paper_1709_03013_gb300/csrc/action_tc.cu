@@ -470,6 +470,8 @@ action_tc_kernel(const TcArgs args) {
     }
 }
 
+// ------------------------------------------------------------------ host side
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -484,41 +486,10 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
 }
 
 
-struct TileKey {
-    int64_t ext;
-    int bi, bj;
-    TcTile t;
-};
-
-// Output tiles of the upper triangle of one set, with their sort keys: longest K
-// first at the granularity of SUPER x SUPER blocks, column-major inside a block (tiles
-// sharing a P panel run together).
-void set_tiles(int set, int64_t N, int64_t row_lo, int64_t row_hi, int super, std::vector<TileKey> &keys) {
-    const int NI = (int)((N + BM - 1) / BM), NJ = (int)((N + BN - 1) / BN);
-    for (int ti = 0; ti < NI; ++ti) {
-        const int64_t I0 = (int64_t)ti * BM, I1 = I0 + BM;
-        if (I1 <= row_lo || I0 >= row_hi) continue;
-        for (int tj = ti / 2; tj < NJ; ++tj) {
-            const int64_t J1 = std::min<int64_t>((int64_t)(tj + 1) * BN, N);
-            if (J1 <= I0 + 1) continue;  // no pair i < j in the tile
-            const int bi = (int)(I0 / super), bj = (int)(((int64_t)tj * BN) / super);
-            const int64_t ext = (int64_t)(bj + 1) * super - (int64_t)bi * super;
-            keys.push_back(TileKey{ext, bi, bj, TcTile{set, ti, tj, 0}});
-        }
-    }
-}
-
-bool key_before(const TileKey &a, const TileKey &b) {
-    if (a.ext != b.ext) return a.ext > b.ext;
-    if (a.t.set != b.t.set) return a.t.set < b.t.set;
-    if (a.bi != b.bi) return a.bi < b.bi;
-    if (a.bj != b.bj) return a.bj < b.bj;
-    if (a.t.tj != b.t.tj) return a.t.tj < b.t.tj;
-    return a.t.ti < b.t.ti;
-}
-
-// Sorted tile lists of single sets, kept per (N, row range): a set of N = 65536 has
-// ~65k tiles whose construction would otherwise stall every call.
+// Output tiles of the upper triangle of one set, longest K first at the granularity
+// of super x super blocks (block pairs by decreasing extent bj - bi, then bi), and
+// column-major inside a block pair, so tiles sharing a P panel run together.  The
+// list is generated in that order directly and kept per (N, row range, block).
 struct TileCache {
     std::mutex mu;
     std::map<std::tuple<int64_t, int64_t, int64_t, int>, std::vector<TcTile>> lists;
@@ -531,11 +502,25 @@ std::vector<TcTile> single_set_tiles(int64_t N, int64_t lo, int64_t hi, int supe
     auto it = g_tiles.lists.find(key);
     if (it != g_tiles.lists.end()) return it->second;
     if (g_tiles.lists.size() >= 256) g_tiles.lists.clear();
-    std::vector<TileKey> keys;
-    set_tiles(0, N, lo, hi, super, keys);
-    std::sort(keys.begin(), keys.end(), key_before);
-    std::vector<TcTile> tiles(keys.size());
-    for (size_t k = 0; k < keys.size(); ++k) tiles[k] = keys[k].t;
+    std::vector<TcTile> tiles;
+    const int NI = (int)((N + BM - 1) / BM), NJ = (int)((N + BN - 1) / BN);
+    const int rows_per_block = super / BM, cols_per_block = super / BN;
+    const int NB = (int)((N + super - 1) / super);
+    for (int L = NB; L >= 1; --L) {              // extent level: bj - bi + 1
+        for (int bi = 0; bi + L - 1 < NB; ++bi) {
+            const int bj = bi + L - 1;
+            for (int tj = bj * cols_per_block; tj < std::min(NJ, (bj + 1) * cols_per_block); ++tj) {
+                for (int ti = bi * rows_per_block; ti < std::min(NI, (bi + 1) * rows_per_block); ++ti) {
+                    if (tj < ti / 2) continue;
+                    const int64_t I0 = (int64_t)ti * BM, I1 = I0 + BM;
+                    if (I1 <= lo || I0 >= hi) continue;
+                    const int64_t J1 = std::min<int64_t>((int64_t)(tj + 1) * BN, N);
+                    if (J1 <= I0 + 1) continue;
+                    tiles.push_back(TcTile{0, ti, tj, 0});
+                }
+            }
+        }
+    }
     return g_tiles.lists[key] = std::move(tiles);
 }
 
@@ -619,7 +604,6 @@ TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned
     for (TcPlan::Chunk &c : p.chunks) {
         std::vector<int64_t> wstarts;
         int64_t total = 0;
-        std::vector<TileKey> keys;
         std::vector<TcTile> tiles;
         for (int s = c.set_lo; s < c.set_hi; ++s) {
             wstarts.push_back(total);

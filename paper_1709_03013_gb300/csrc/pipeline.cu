@@ -261,7 +261,8 @@ void free_batch_graph(csg_ctx *ctx) {
 // the popcount kernel, the tensor kernel's rasterisation block) with CUDA events, one
 // untimed and one timed run each, and keeps the fastest.  Choices are remembered per
 // GPU and batch shape in a JSON-lines file ($CSG_AUTOTUNE_CACHE, default
-// ~/.cache/csg/autotune.jsonl); CSG_AUTOTUNE=0 skips tuning.
+// ~/.cache/csg/autotune.jsonl); CSG_AUTOTUNE=0 skips tuning, and batches of fewer
+// than 16 sets keep the defaults.
 
 static std::string tune_key(int n, const int32_t *d, const int64_t *N) {
     cudaDeviceProp prop;
@@ -326,6 +327,7 @@ static int autotune(csg_ctx *ctx, csg_set *const *sets, int n, const int32_t *d,
     (void)ctx;
     const char *env = getenv("CSG_AUTOTUNE");
     if (env && env[0] == '0') return CSG_OK;
+    if (n < 16) return CSG_OK;  // small batches keep the defaults
     const std::string key = tune_key(n, d, N);
     if (tune_lookup(key, best)) return CSG_OK;
     const Tune cands[] = {{0, 2048}, {1024, 2048}, {2048, 2048}, {0, 1024}};

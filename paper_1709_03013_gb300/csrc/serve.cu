@@ -43,10 +43,11 @@ size_t footprint(int64_t N) {
     return (size_t)N * 4 * sizeof(double) + (size_t)N * stride_for(N) * sizeof(uint64_t);
 }
 
-// rough work of a request in bit operations: ~0.12 N^3 (d=2), ~0.035 N^3 (d=4)
+// work of a request for the tensor form: the triangle-restricted contraction, N^3/3 flops
 double work_of(int d, int64_t N) {
-    double n = (double)N;
-    return (d == 2 ? 0.12 : 0.035) * n * n * n;
+    (void)d;
+    const double n = (double)N;
+    return n * n * n / 3.0;
 }
 
 }  // namespace
@@ -63,7 +64,7 @@ struct ServeState {
     size_t reserved = 0;               // bytes admitted by running batches
     std::vector<std::thread> workers;
     size_t max_queue = 1 << 20;
-    double batch_work_cap = 4e12;      // bit operations per batch (about 30-60 ms)
+    double batch_work_cap = 1e14;      // flops per batch (about 30 ms on the tensor form)
     int batch_max_sets = 4096;
 };
 
