@@ -95,18 +95,21 @@ __device__ __forceinline__ int find_set(const int64_t *__restrict__ starts, int 
     return lo;
 }
 
+// Four relation bits -> four fp8 bytes (0x00 or 0x38): multiplying by 1 + 2^7 + 2^14 +
+// 2^21 places bit b of the nibble at bit 8b, the mask keeps exactly those, and the
+// second multiply turns each 0/1 byte into 0x00/0x38 (no carries between bytes).
+__device__ __forceinline__ uint32_t nibble_fp8(uint32_t nib) {
+    return ((nib * 0x00204081u) & 0x01010101u) * (uint32_t)kOne;
+}
+
 __device__ __forceinline__ void put64(uint8_t *dst, uint64_t m) {
     uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    const uint32_t lo = (uint32_t)m, hi = (uint32_t)(m >> 32);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        uint32_t v[4];
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const uint32_t nib = (uint32_t)(m >> (16 * q + 4 * h)) & 0xFu;
-            v[h] = ((nib & 1u) ? (uint32_t)kOne : 0u) | ((nib & 2u) ? (uint32_t)kOne << 8 : 0u) |
-                   ((nib & 4u) ? (uint32_t)kOne << 16 : 0u) | ((nib & 8u) ? (uint32_t)kOne << 24 : 0u);
-        }
-        d4[q] = make_uint4(v[0], v[1], v[2], v[3]);
+        const uint32_t h = q < 2 ? lo >> (16 * q) : hi >> (16 * (q - 2));
+        d4[q] = make_uint4(nibble_fp8(h & 0xFu), nibble_fp8((h >> 4) & 0xFu), nibble_fp8((h >> 8) & 0xFu),
+                           nibble_fp8((h >> 12) & 0xFu));
     }
 }
 

@@ -97,9 +97,12 @@ struct LinkSpec {
     double coord_scale;  // max(1, max |coordinate|): scales the d=4 float-screen margin
 };
 struct LinkPlan {
-    int n = 0;
+    struct Part {  // the sets of one dimension (part 0: d=2, part 1: d=4)
+        int n = 0;
+        int64_t T = 0;
+        size_t t_rows = 0, t_starts = 0;
+    } part[2];
     int64_t T = 0;
-    size_t t_rows = 0, t_starts = 0;
 };
 LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc);
 void link_launch(const LinkPlan &p, const Arena &a, cudaStream_t st);

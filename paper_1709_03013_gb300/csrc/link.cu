@@ -35,7 +35,7 @@ constexpr int kTile = 256;      // rows and columns per tile
 constexpr int kTileWords = 4;   // 64-bit words per tile row
 
 struct LinkRow {
-    int32_t d;
+    int32_t d;  // 2 or 4
     int32_t pad;
     int64_t N, stride;
     const double *coords;
@@ -80,6 +80,61 @@ __device__ __forceinline__ bool exact4(double ti, double xi, double yi, double z
     return __dmul_rn(dt, dt) > s;
 }
 
+// 32x32 bit transpose across a warp: lane r holds row r's bits (bit c = column c) and
+// ends holding column r's bits (bit k = row k).  Five butterfly stages, each swapping
+// the off-diagonal s x s blocks between lanes r and r ^ s.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const uint32_t m = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu : s == 2 ? 0x33333333u : 0x55555555u;
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, s);
+        x = (lane & s) ? ((x & ~m) | ((y & ~m) >> s)) : ((x & m) | ((y & m) << s));
+    }
+    return x;
+}
+
+// One 64-column word of row i: bit b set iff i and column K + q*64 + b are related.
+// FULL: every column of the word is a valid later column (no bounds checks).
+template <int D, bool FULL>
+__device__ __forceinline__ uint64_t link_word(int q, int c0, int ncol, const uint64_t (*ck)[kTile],
+                                              const float4 *cf4, const double (*cd)[kTile], uint64_t ui,
+                                              uint64_t vi, float tf, float xf, float yf, float zf,
+                                              double ti, double xi, double yi, double zi, float screen) {
+    uint64_t acc = 0, amb = 0;
+#pragma unroll
+    for (int b = 0; b < 64; ++b) {
+        const int c = q * 64 + b;
+        if (!FULL && (c < c0 || c >= ncol)) continue;
+        if (D == 2) {
+            if ((ui < ck[0][c]) & (vi < ck[1][c])) acc |= 1ull << b;
+        } else {
+            const float4 k4 = cf4[c];
+            const float dt = __fsub_rn(k4.x, tf);
+            const float dx = __fsub_rn(k4.y, xf);
+            const float dy = __fsub_rn(k4.z, yf);
+            const float dz = __fsub_rn(k4.w, zf);
+            const float sp = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+            const float diff = __fmaf_rn(dt, dt, -sp);
+            if (diff > screen) acc |= 1ull << b;
+            if (fabsf(diff) <= screen) amb |= 1ull << b;
+        }
+    }
+    if (D == 4) {
+        // pairs inside the screen's margin: decide in double (rare)
+        while (amb) {
+            const int b = __ffsll((long long)amb) - 1;
+            amb &= amb - 1;
+            const int c = q * 64 + b;
+            if (exact4(ti, xi, yi, zi, cd[0][c], cd[1][c], cd[2][c], cd[3][c]))
+                acc |= 1ull << b;
+            else
+                acc &= ~(1ull << b);
+        }
+    }
+    return acc;
+}
+
+template <int D>
 __global__ void __launch_bounds__(kTile)
 link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts, int n) {
     __shared__ double cd[4][kTile];       // column coordinates (d=4: t,x,y,z)
@@ -109,14 +164,11 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
     const int64_t i = R + r;
     const int64_t kc = K + r;  // column staged by this thread
 
-    // stage column coordinates
-    if (S.d == 2) {
-        if (kc < N) {
+    if (kc < N) {
+        if (D == 2) {
             ck[0][r] = order_key(S.coords[2 * N + kc]);
             ck[1][r] = order_key(S.coords[3 * N + kc]);
-        }
-    } else {
-        if (kc < N) {
+        } else {
             double v[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -130,67 +182,46 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
     __syncthreads();
 
     uint64_t w[kTileWords] = {0, 0, 0, 0};
-    // columns valid for this tile: [0, ncol)
     const int64_t ncol_l = N - K;
     const int ncol = ncol_l <= 0 ? 0 : (ncol_l >= kTile ? kTile : (int)ncol_l);
     if (i < N) {
-        // first column index strictly after row i within the tile (diagonal tiles)
-        const int c0 = diag ? r + 1 : 0;
-        if (S.d == 2) {
-            const uint64_t ui = order_key(S.coords[2 * N + i]);
-            const uint64_t vi = order_key(S.coords[3 * N + i]);
-            const uint64_t *cu = ck[0];
-            const uint64_t *cv = ck[1];
-#pragma unroll
-            for (int q = 0; q < kTileWords; ++q) {
-                uint64_t acc = 0;
-#pragma unroll 16
-                for (int b = 0; b < 64; ++b) {
-                    const int c = q * 64 + b;
-                    if (c >= c0 && c < ncol && (ui < cu[c]) && (vi < cv[c])) acc |= 1ull << b;
-                }
-                w[q] = acc;
-            }
+        const int c0 = diag ? r + 1 : 0;   // first column strictly after row i
+        uint64_t ui = 0, vi = 0;
+        double ti = 0, xi = 0, yi = 0, zi = 0;
+        float tf = 0, xf = 0, yf = 0, zf = 0;
+        if (D == 2) {
+            ui = order_key(S.coords[2 * N + i]);
+            vi = order_key(S.coords[3 * N + i]);
         } else {
-            const double ti = S.coords[i], xi = S.coords[N + i], yi = S.coords[2 * N + i],
-                         zi = S.coords[3 * N + i];
-            const float screen = S.screen;
-            const float tf = __double2float_rn(ti), xf = __double2float_rn(xi),
-                        yf = __double2float_rn(yi), zf = __double2float_rn(zi);
-#pragma unroll
-            for (int q = 0; q < kTileWords; ++q) {
-                uint64_t acc = 0;
-#pragma unroll 8
-                for (int b = 0; b < 64; ++b) {
-                    const int c = q * 64 + b;
-                    if (c >= c0 && c < ncol) {
-                        const float4 k4 = cf4[c];
-                        const float dt = __fsub_rn(k4.x, tf);
-                        const float dx = __fsub_rn(k4.y, xf);
-                        const float dy = __fsub_rn(k4.z, yf);
-                        const float dz = __fsub_rn(k4.w, zf);
-                        const float sp = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
-                        const float diff = __fmaf_rn(dt, dt, -sp);
-                        bool rel = diff > screen;
-                        if (fabsf(diff) <= screen)
-                            rel = exact4(ti, xi, yi, zi, cd[0][c], cd[1][c], cd[2][c], cd[3][c]);
-                        if (rel) acc |= 1ull << b;
-                    }
-                }
-                w[q] = acc;
-            }
+            ti = S.coords[i];
+            xi = S.coords[N + i];
+            yi = S.coords[2 * N + i];
+            zi = S.coords[3 * N + i];
+            tf = __double2float_rn(ti);
+            xf = __double2float_rn(xi);
+            yf = __double2float_rn(yi);
+            zf = __double2float_rn(zi);
+        }
+        const bool full = !diag && ncol == kTile;
+#pragma unroll 1
+        for (int q = 0; q < kTileWords; ++q) {
+            const uint64_t word =
+                full ? link_word<D, true>(q, c0, ncol, ck, cf4, cd, ui, vi, tf, xf, yf, zf, ti, xi, yi, zi, S.screen)
+                     : link_word<D, false>(q, c0, ncol, ck, cf4, cd, ui, vi, tf, xf, yf, zf, ti, xi, yi, zi, S.screen);
+            if (q == 0) w[0] = word;
+            else if (q == 1) w[1] = word;
+            else if (q == 2) w[2] = word;
+            else w[3] = word;
         }
     }
 
-    // mirrored half: bit r of row (K + c), word R/64 + warp/2, is w_r bit c
-    uint32_t keep[kTile / 32];
+    // mirrored half: transpose each 32 x 32 block of this warp's rows
 #pragma unroll
-    for (int c = 0; c < kTile; ++c) {
-        uint32_t b = __ballot_sync(0xffffffffu, (uint32_t)(w[c >> 6] >> (c & 63)) & 1u);
-        if ((c & 31) == lane) keep[c >> 5] = b;
+    for (int g = 0; g < kTile / 32; ++g) {
+        const uint64_t word = w[g >> 1];
+        const uint32_t x = (uint32_t)(word >> (32 * (g & 1)));
+        tb[32 * g + lane][warp] = warp_transpose32(x, lane);
     }
-#pragma unroll
-    for (int q = 0; q < kTile / 32; ++q) tb[lane + 32 * q][warp] = keep[q];
     __syncthreads();
 
     uint64_t *rows = S.rows;
@@ -227,45 +258,59 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
 
 LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
     LinkPlan p;
-    p.n = n;
     *rc = CSG_OK;
-    std::vector<LinkRow> rows(n);
-    std::vector<int64_t> starts(n);
-    for (int s = 0; s < n; ++s) {
-        LinkRow &L = rows[s];
-        L.d = specs[s].d;
-        L.pad = 0;
-        L.N = specs[s].N;
-        L.stride = specs[s].stride;
-        L.coords = specs[s].coords;
-        L.rows = specs[s].rows;
-        L.nb = (L.N + kTile - 1) / kTile;
-        L.nbc = L.stride / kTileWords;
-        L.tile_off = p.T;
-        L.screen = 1e-5f * (float)(specs[s].coord_scale * specs[s].coord_scale);
-        L.pad2 = 0.f;
-        starts[s] = p.T;
-        if (L.stride % 16 != 0 || L.nbc < L.nb) {
-            set_error("link: stride %lld does not cover N=%lld", (long long)L.stride, (long long)L.N);
+    // one tile space per dimension: each launch runs one instantiation of the kernel
+    for (int part = 0; part < 2; ++part) {
+        const int d = part == 0 ? 2 : 4;
+        std::vector<LinkRow> rows;
+        std::vector<int64_t> starts;
+        int64_t T = 0;
+        for (int s = 0; s < n; ++s) {
+            if (specs[s].d != d) continue;
+            LinkRow L;
+            L.d = d;
+            L.pad = 0;
+            L.N = specs[s].N;
+            L.stride = specs[s].stride;
+            L.coords = specs[s].coords;
+            L.rows = specs[s].rows;
+            L.nb = (L.N + kTile - 1) / kTile;
+            L.nbc = L.stride / kTileWords;
+            L.tile_off = T;
+            L.screen = 1e-5f * (float)(specs[s].coord_scale * specs[s].coord_scale);
+            L.pad2 = 0.f;
+            if (L.stride % 16 != 0 || L.nbc < L.nb) {
+                set_error("link: stride %lld does not cover N=%lld", (long long)L.stride, (long long)L.N);
+                *rc = CSG_E_INVAL;
+                return p;
+            }
+            starts.push_back(T);
+            rows.push_back(L);
+            T += L.nb * L.nbc - L.nb * (L.nb - 1) / 2;
+        }
+        if (T > 0x7fffffffLL) {
+            set_error("link: %lld tiles exceed one launch", (long long)T);
             *rc = CSG_E_INVAL;
             return p;
         }
-        p.T += L.nb * L.nbc - L.nb * (L.nb - 1) / 2;
+        LinkPlan::Part &P = p.part[part];
+        P.n = (int)rows.size();
+        P.T = T;
+        if (P.n) {
+            P.t_rows = a.put(rows.data(), rows.size() * sizeof(LinkRow));
+            P.t_starts = a.put(starts.data(), starts.size() * sizeof(int64_t));
+        }
+        p.T += T;
     }
-    if (p.T > 0x7fffffffLL) {
-        set_error("link: %lld tiles exceed one launch", (long long)p.T);
-        *rc = CSG_E_INVAL;
-        return p;
-    }
-    p.t_rows = a.put(rows.data(), n * sizeof(LinkRow));
-    p.t_starts = a.put(starts.data(), n * sizeof(int64_t));
     return p;
 }
 
 void link_launch(const LinkPlan &p, const Arena &a, cudaStream_t st) {
     if (p.T == 0) return;
     stage_begin(CSG_STAGE_LINK, st);
-    link_kernel<<<(unsigned)p.T, kTile, 0, st>>>(a.tab<LinkRow>(p.t_rows), a.tab<int64_t>(p.t_starts), p.n);
+    const LinkPlan::Part &p2 = p.part[0], &p4 = p.part[1];
+    if (p2.T) link_kernel<2><<<(unsigned)p2.T, kTile, 0, st>>>(a.tab<LinkRow>(p2.t_rows), a.tab<int64_t>(p2.t_starts), p2.n);
+    if (p4.T) link_kernel<4><<<(unsigned)p4.T, kTile, 0, st>>>(a.tab<LinkRow>(p4.t_rows), a.tab<int64_t>(p4.t_starts), p4.n);
     stage_end(CSG_STAGE_LINK, st);
 }
 
