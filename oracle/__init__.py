@@ -68,6 +68,8 @@ def _load():
         lib.orc_action_rows.argtypes = [i64, vp, i64, i64, vp, vp, vp, vp, i32]
         lib.orc_finalize.argtypes = [i32, i64, vp, vp, vp]
         lib.orc_action_rows_coords.argtypes = [i32, i64, vp, i64, i64, vp, vp, vp, vp, i32]
+        lib.orc_smeared.argtypes = [i64, vp, dbl]
+        lib.orc_smeared.restype = dbl
         for f in (lib.orc_sprinkle, lib.orc_sort, lib.orc_link, lib.orc_link_row,
                   lib.orc_related, lib.orc_pack, lib.orc_action_rows, lib.orc_finalize,
                   lib.orc_action_rows_coords):
@@ -214,6 +216,14 @@ def finalize(d: int, N: int, Nk) -> tuple[int, float]:
     if rc != OK:
         raise RuntimeError(f"orc_finalize failed: {rc}")
     return int(combo[0]), float(S[0])
+
+
+def smeared(N: int, hist: np.ndarray, eps: float) -> float:
+    """Smeared action S_eps of Eq. s_smeared from the 0-based histogram (hist[m], m <= N-2)."""
+    h = np.zeros(max(N, 1), dtype=np.uint64)
+    src = np.asarray(hist, dtype=np.uint64)
+    h[:min(len(src), len(h))] = src[:len(h)]
+    return float(_load().orc_smeared(N, _p(h), float(eps)))
 
 
 def run(d: int, N: int, seed: int, seq: int = 0, threads: int = 0) -> dict:

@@ -388,3 +388,22 @@ int orc_finalize(int d, int64_t N, const uint64_t Nk[4], int64_t *combo, double 
     }
     return ORC_EINVAL;
 }
+
+/* Smeared (non-local) action of Eq. s_smeared from the full 0-based histogram
+ * hist[0..N-2] (hist[m] = pairs whose interval holds m elements, so the paper's
+ * 1-based n_i is hist[i-1]):
+ *   S_eps = 2 eps [ N - 2 eps sum_{i=1}^{N-1} n_i f2(i-1, eps) ],
+ *   f2(i, eps) = (1-eps)^i [1 - 2 eps i/(1-eps) + eps^2 i (i-1) / (2 (1-eps)^2)],
+ * for 0 < eps < 1.  The sum runs in increasing i. */
+double orc_smeared(int64_t N, const uint64_t *hist, double eps) {
+    double acc = 0.0;
+    for (int64_t i = 1; i <= N - 1; ++i) {
+        const uint64_t n_i = hist[i - 1];
+        if (n_i == 0) continue;
+        const double a = (double)(i - 1);
+        const double q = 1.0 - eps;
+        const double f2 = pow(q, a) * (1.0 - 2.0 * eps * a / q + eps * eps * a * (a - 1.0) / (2.0 * q * q));
+        acc += (double)n_i * f2;
+    }
+    return 2.0 * eps * ((double)N - 2.0 * eps * acc);
+}

@@ -30,7 +30,7 @@ def read_golden(name):
                 out["rel"].append((i, j))
             elif key in ("Nk",):
                 out[key] = [int(x) for x in val.split()]
-            elif key in ("S2", "S4"):
+            elif key in ("S2", "S4") or key.startswith("Seps"):
                 out[key] = float(val)
             else:
                 out[key] = int(val)

@@ -304,6 +304,44 @@ def test_rows_from_coords_match_matrix(d, N, rows):
     assert (a["R"], a["sum_m"], a["W"]) == (b["R"], b["sum_m"], b["W"])
 
 
+# ------------------------------------------------------------ smeared action
+
+def test_smeared_golden(golden):
+    g = golden("diamond4.txt")
+    h = oracle.action(inputs.rel_from_edges(g["N"], g["rel"]))["hist"]
+    assert abs(oracle.smeared(g["N"], h, 0.5) - g["Seps_half"]) <= 1e-14
+    assert abs(oracle.smeared(g["N"], h, 0.25) - g["Seps_quarter"]) <= 1e-14
+
+
+@pytest.mark.parametrize("eps", [0.01, 2 ** -6, 0.3, 0.7])
+def test_smeared_weights_are_binomial(eps):
+    # f2(m, e) = P(B=0) - 2 P(B=1) + P(B=2) for B ~ Binomial(m, e): the sum in Eq.
+    # s_smeared evaluated with the library binomial pmf
+    from scipy import stats
+    d, N = 2, 400
+    h = oracle.action(oracle.link(d, oracle.sprinkle_sorted(d, N, 33)))["hist"]
+    m = np.arange(N)
+    w = stats.binom.pmf(0, m, eps) - 2 * stats.binom.pmf(1, m, eps) + stats.binom.pmf(2, m, eps)
+    want = 2 * eps * (N - 2 * eps * float((h.astype(np.float64) * w).sum()))
+    got = oracle.smeared(N, h, eps)
+    scale = 2 * eps * (N + 2 * eps * float((h.astype(np.float64) * np.abs(w)).sum()))
+    assert abs(got - want) <= 1e-12 * scale
+
+
+def test_smeared_tends_to_local_action():
+    # as e -> 1 only f2(0)=1, f2(1)=-2, f2(2)=1 survive, giving Eq. s_local
+    for d, N, seed in ((2, 300, 4), (4, 250, 5)):
+        out = oracle.action(oracle.link(d, oracle.sprinkle_sorted(d, N, seed)))
+        _, S2 = oracle.finalize(2, N, out["Nk"])
+        S = oracle.smeared(N, out["hist"], 1 - 1e-9)
+        assert abs(S - S2) <= 1e-5 * max(abs(S2), N)
+
+
+@pytest.mark.parametrize("N", [1, 50])
+def test_smeared_antichain(N):
+    assert oracle.smeared(N, np.zeros(N, np.uint64), 0.2) == 2 * 0.2 * N
+
+
 def test_pack_layout():
     rel = inputs.random_upper_rel(130, 0.3, 1)
     w = oracle.pack(rel)
