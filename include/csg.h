@@ -145,6 +145,17 @@ int csg_action_rows(csg_ctx *ctx, csg_set *set, int method, int64_t row_lo, int6
 int csg_action_hist(csg_ctx *ctx, csg_set *set, int method, uint64_t *dev_hist, int64_t nbins,
                     csg_result *out, void *stream);
 
+/* Smeared (non-local) 1+1 action of Eq. s_smeared:
+ *   S_eps = 2 eps [N - 2 eps sum_{i=1}^{N-1} n_i f2(i-1, eps)],
+ *   f2(i, eps) = (1-eps)^i [1 - 2 eps i/(1-eps) + eps^2 i (i-1) / (2 (1-eps)^2)],
+ * where n_i is the number of related pairs with i-1 elements between them (the full
+ * histogram, Sec. 4.1).  0 < eps < 1; the set must have d = 2 (the paper gives the
+ * smeared form in 1+1 dimensions only).  *S_eps receives the action; *out (optional)
+ * the local counts as from csg_action.  The histogram uses N 64-bit words of
+ * stream-ordered scratch. */
+int csg_action_smeared(csg_ctx *ctx, csg_set *set, int method, double eps, double *S_eps,
+                       csg_result *out, void *stream);
+
 /* Actions of n sets in one pass: all sets' work in one persistent launch over a
  * queue of (set, row group) items, longest first.  out[n] is filled in order. */
 int csg_action_batch(csg_ctx *ctx, csg_set *const *sets, int n, int method, csg_result *out,

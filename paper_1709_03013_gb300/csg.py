@@ -58,7 +58,7 @@ EXPORTS = [
     "csg_set_from_coords", "csg_link", "csg_set_from_bitmap", "csg_action", "csg_action_rows",
     "csg_action_hist", "csg_action_batch", "csg_run_batch", "csg_serve_submit", "csg_serve_poll",
     "csg_serve_cancel", "csg_export_coords", "csg_export_bitmap", "csg_set_info", "csg_set_free",
-    "csg_action_noalloc", "csg_set_timing", "csg_stage_times",
+    "csg_action_noalloc", "csg_set_timing", "csg_stage_times", "csg_action_smeared",
 ]
 
 _lib = None
@@ -99,6 +99,7 @@ def load(path: str = LIB_PATH):
         "csg_set_free": (None, [vp]),
         "csg_action_noalloc": (i32, [i32, i64, vp, i64, vp, vp]),
         "csg_set_timing": (i32, [vp, i32]),
+        "csg_action_smeared": (i32, [vp, vp, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_double), R, vp]),
         "csg_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_double), i32]),
     }
     for name, (res, args) in sig.items():
@@ -193,6 +194,14 @@ class CausalSet:
         _check(load().csg_action_hist(self.ctx.handle, self.handle, method, ctypes.c_void_p(dev_hist_ptr),
                                       nbins, ctypes.byref(r), _stream(stream)), "csg_action_hist")
         return Result.of(r)
+
+    def action_smeared(self, eps: float, method: int = POPC, stream=None):
+        """(S_eps, Result): the smeared 1+1 action of Eq. s_smeared and the local counts."""
+        S = ctypes.c_double()
+        r = _Result()
+        _check(load().csg_action_smeared(self.ctx.handle, self.handle, method, eps, ctypes.byref(S),
+                                         ctypes.byref(r), _stream(stream)), "csg_action_smeared")
+        return S.value, Result.of(r)
 
     def coords(self) -> np.ndarray:
         N = self.N

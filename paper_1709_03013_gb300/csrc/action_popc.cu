@@ -46,12 +46,15 @@ struct Counters {
     unsigned long long n0 = 0, n1 = 0, n2 = 0, n3 = 0, R = 0, M = 0, W = 0;
 };
 
-// The K group rows related to j (the set bits of mask) against row j: each lane takes
-// word pairs (2 lane, 2 lane + 1) + 64 t, so every load is 16 bytes, and the K staged
-// rows are compile-time slots (no per-row branches in the loop).  Lane 0 books the
-// pairs' interval sizes after a warp reduction.
+// The cnt <= K group rows related to j (the set bits of mask) against row j: each lane
+// takes word pairs (2 lane, 2 lane + 1) + 64 t, so every load is 16 bytes, and the K
+// staged rows are compile-time slots (no per-row branches in the loop); slots beyond
+// cnt read the all-zero row at zoff.  K is 1, 2, 4 or 8, which keeps the code small
+// enough for the instruction cache.  Lane 0 books the pairs' interval sizes after a
+// warp reduction.
 template <int K>
-__device__ __forceinline__ void sweep_rows(uint32_t mask, const uint64_t *__restrict__ A, int pitch,
+__device__ __forceinline__ void sweep_rows(uint32_t mask, int cnt, int zoff, const uint64_t *__restrict__ A,
+                                           int pitch,
                                            const uint64_t *__restrict__ bj, int wj, uint64_t lastmask,
                                            int lane, int64_t j, int64_t i0, Counters &c,
                                            unsigned long long *__restrict__ hist, long long nbins) {
@@ -62,8 +65,8 @@ __device__ __forceinline__ void sweep_rows(uint32_t mask, const uint64_t *__rest
     for (int k = 0; k < K; ++k) {
         const int r = __ffs(m) - 1;
         m &= m - 1;
-        off[k] = r * pitch;
-        rsum += r;
+        off[k] = k < cnt ? r * pitch : zoff;
+        rsum += k < cnt ? r : 0;
     }
     uint32_t acc[K];
 #pragma unroll
@@ -87,6 +90,7 @@ __device__ __forceinline__ void sweep_rows(uint32_t mask, const uint64_t *__rest
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
+        if (k >= cnt) break;
         uint32_t v = acc[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -100,9 +104,9 @@ __device__ __forceinline__ void sweep_rows(uint32_t mask, const uint64_t *__rest
         }
     }
     if (lane == 0) {
-        c.R += K;
-        // sum over the K rows r of (j - (i0 + r) - 1)
-        c.W += (unsigned long long)K * (unsigned long long)(j - i0 - 1) - (unsigned long long)rsum;
+        c.R += (unsigned long long)cnt;
+        // sum over the cnt rows r of (j - (i0 + r) - 1)
+        c.W += (unsigned long long)cnt * (unsigned long long)(j - i0 - 1) - (unsigned long long)rsum;
     }
 }
 
@@ -112,23 +116,16 @@ __device__ __forceinline__ void dispatch_rows(int cnt, uint32_t mask, const uint
                                               uint64_t lastmask, int lane, int64_t j, int64_t i0,
                                               Counters &c, unsigned long long *__restrict__ hist,
                                               long long nbins) {
-#define CSG_ROWS_CASE(K)                                                                       \
-    case K:                                                                                    \
-        if constexpr (K <= G && K <= 8) sweep_rows<K>(mask, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins); \
-        break;
-    switch (cnt) {
-        CSG_ROWS_CASE(1)
-        CSG_ROWS_CASE(2)
-        CSG_ROWS_CASE(3)
-        CSG_ROWS_CASE(4)
-        CSG_ROWS_CASE(5)
-        CSG_ROWS_CASE(6)
-        CSG_ROWS_CASE(7)
-        CSG_ROWS_CASE(8)
-        default:
-            break;
+    const int zoff = G * pitch;  // the zero row after the G staged rows
+    if (cnt <= 1)
+        sweep_rows<1>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins);
+    else if (cnt <= 2)
+        sweep_rows<2>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins);
+    else if (cnt <= 4 || G <= 4) {
+        if constexpr (G >= 4) sweep_rows<4>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins);
+    } else {
+        if constexpr (G >= 8) sweep_rows<8>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins);
     }
-#undef CSG_ROWS_CASE
 }
 
 template <int G>
@@ -138,13 +135,14 @@ action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict_
                    unsigned long long *__restrict__ hist, long long nbins) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem *ctl = reinterpret_cast<Smem *>(smem_raw);
-    uint64_t *A = reinterpret_cast<uint64_t *>(smem_raw + 128);  // G rows x pitch words
+    uint64_t *A = reinterpret_cast<uint64_t *>(smem_raw + 128);  // G rows x pitch words, then a zero row
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         ptx::mbar_init(&ctl->bar, 1);
         ptx::fence_mbar_init();
     }
+    for (int w = threadIdx.x; w < pitch; w += blockDim.x) A[(size_t)G * pitch + w] = 0;  // zero row
     __syncthreads();
 
     uint32_t phase = 0;
@@ -259,7 +257,7 @@ action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict_
 
 template <int G>
 int launch_g(const PopcPlan &p, const Arena &a, cudaStream_t st) {
-    const size_t smem = 128 + (size_t)G * p.pitch * sizeof(uint64_t);
+    const size_t smem = 128 + (size_t)(G + 1) * p.pitch * sizeof(uint64_t);
     auto kern = action_popc_kernel<G>;
     CSG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0, per_sm = 0;
@@ -300,8 +298,8 @@ PopcPlan popc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsi
     for (int s = 0; s < n; ++s) maxw = std::max<int64_t>(maxw, (sets[s].N + 63) / 64 + 2);
     p.pitch = (int)((maxw + 1) & ~int64_t(1));
     int G = 16;
-    while (G > 1 && (size_t)G * p.pitch * 8 > kRowBudget) G >>= 1;
-    if ((size_t)G * p.pitch * 8 > kRowBudget) {
+    while (G > 1 && (size_t)(G + 1) * p.pitch * 8 > kRowBudget) G >>= 1;
+    if ((size_t)(G + 1) * p.pitch * 8 > kRowBudget) {
         set_error("action_popc: rows of %lld words do not fit shared memory", (long long)maxw);
         *rc = CSG_E_INVAL;
         return p;

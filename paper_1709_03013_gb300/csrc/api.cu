@@ -287,6 +287,26 @@ int csg_action_hist(csg_ctx *ctx, csg_set *set, int method, uint64_t *dev_hist, 
                          stream);
 }
 
+int csg_action_smeared(csg_ctx *ctx, csg_set *set, int method, double eps, double *S_eps,
+                       csg_result *out, void *stream) {
+    if (!ctx || !set || !S_eps || set->ctx != ctx || (method != CSG_POPC && method != CSG_TC) ||
+        !(eps > 0.0 && eps < 1.0)) {
+        set_error("csg_action_smeared: bad arguments (0 < eps < 1, method POPC or TC)");
+        return CSG_E_INVAL;
+    }
+    if (set->d != 2) {
+        set_error("csg_action_smeared: the smeared action is defined here for d=2 only");
+        return CSG_E_INVAL;
+    }
+    if (!set->linked) {
+        set_error("csg_action_smeared: set has no bitmap (call csg_link)");
+        return CSG_E_INVAL;
+    }
+    CSG_CUDA_TRY(cudaSetDevice(ctx->device));
+    TimerScope ts(ctx);
+    return run_smeared(set, method, eps, S_eps, out, (cudaStream_t)stream);
+}
+
 int csg_action_batch(csg_ctx *ctx, csg_set *const *sets, int n, int method, csg_result *out,
                      void *stream) {
     if (!ctx || (n > 0 && (!sets || !out)) || n < 0 || (method != CSG_POPC && method != CSG_TC)) {

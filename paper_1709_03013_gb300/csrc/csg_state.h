@@ -55,6 +55,7 @@ int run_pipeline(csg_set *const *sets, int n, const uint64_t *seed, const uint64
                  csg_result *out, cudaStream_t st);
 
 void serve_shutdown(csg_ctx *ctx);
+int run_smeared(csg_set *set, int method, double eps, double *S_eps, csg_result *out, cudaStream_t st);
 void free_batch_graph(csg_ctx *ctx);
 int run_batch_graph(csg_ctx *ctx, int n, const int32_t *d, const int64_t *N, const uint64_t *seed,
                     const uint64_t *seq, int method, csg_result *out, cudaStream_t st);

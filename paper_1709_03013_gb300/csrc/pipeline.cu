@@ -227,6 +227,65 @@ int run_pipeline(csg_set *const *sets, int n, const uint64_t *seed, const uint64
     return run_seq(sets, n, method, -1, -1, nullptr, 0, seed, seq, out, st);
 }
 
+// ------------------------------------------------------------------ smeared action
+
+namespace {
+
+// One block: thread t sums hist[m] f2(m, eps) over m = t, t + blockDim, ... in order,
+// then a fixed-shape tree adds the partial sums, so the result is reproducible.
+__global__ void smeared_kernel(const unsigned long long *__restrict__ hist, int64_t N, double eps,
+                               double *__restrict__ out) {
+    __shared__ double part[1024];
+    double acc = 0.0;
+    const double q = 1.0 - eps;
+    for (int64_t m = threadIdx.x; m < N - 1; m += blockDim.x) {
+        const unsigned long long n = hist[m];
+        if (n == 0) continue;
+        const double a = (double)m;
+        const double f2 = pow(q, a) * (1.0 - 2.0 * eps * a / q + eps * eps * a * (a - 1.0) / (2.0 * q * q));
+        acc += (double)n * f2;
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = 2.0 * eps * ((double)N - 2.0 * eps * part[0]);
+}
+
+}  // namespace
+
+int run_smeared(csg_set *set, int method, double eps, double *S_eps, csg_result *out, cudaStream_t st) {
+    const int64_t N = set->N;
+    unsigned long long *hist = nullptr;
+    double *d_S = nullptr;
+    CSG_CUDA_TRY(cudaMallocAsync((void **)&hist, (size_t)N * sizeof(unsigned long long) + 256, st));
+    d_S = reinterpret_cast<double *>(reinterpret_cast<char *>(hist) + (size_t)N * sizeof(unsigned long long));
+    cudaMemsetAsync(hist, 0, (size_t)N * sizeof(unsigned long long), st);
+    csg_result res;
+    csg_set *one[1] = {set};
+    int rc = run_actions(one, 1, method, -1, -1, hist, N, &res, st);  // synchronises st
+    if (rc == CSG_OK) {
+        smeared_kernel<<<1, 1024, 0, st>>>(hist, N, eps, d_S);
+        cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) {
+            set_error("smeared launch: %s", cudaGetErrorString(le));
+            rc = CSG_E_CUDA;
+        } else {
+            cudaMemcpyAsync(S_eps, d_S, sizeof(double), cudaMemcpyDeviceToHost, st);
+        }
+    }
+    cudaFreeAsync(hist, st);
+    cudaError_t se = cudaStreamSynchronize(st);
+    if (rc == CSG_OK && se != cudaSuccess) {
+        set_error("smeared: %s", cudaGetErrorString(se));
+        rc = CSG_E_CUDA;
+    }
+    if (rc == CSG_OK && out) *out = res;
+    return rc;
+}
+
 // ------------------------------------------------------------------ batch graphs
 
 struct BatchGraph {

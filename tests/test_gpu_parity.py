@@ -229,3 +229,32 @@ def test_batch_autotune_records_choice(csg, tmp_path, monkeypatch):
     assert len(lines) == 1 and '"popc_below"' in lines[0] and '"super"' in lines[0]
     for sp, r in list(zip(specs, got))[:5]:
         _check_result(r, oracle.run(sp.d, sp.N, sp.seed, sp.seq), sp.d, sp.N)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 700, 3000])
+@pytest.mark.parametrize("eps", [2 ** -6, 0.3])
+def test_smeared_action(ctx, csg, N, eps):
+    # Eq. s_smeared from the GPU's full histogram against the oracle's; the sum is
+    # reduced in a different order, so the bound is relative to the sum of |terms|
+    s = ctx.sprinkle(2, N, 77, 0).link()
+    want = oracle.action(oracle.link(2, oracle.sprinkle_sorted(2, N, 77, 0)))
+    S_ref = oracle.smeared(N, want["hist"], eps)
+    scale = 2 * eps * N + 8 * eps * eps * want["R"]
+    for method in (csg.POPC, csg.TC):
+        S, res = s.action_smeared(eps, method)
+        assert abs(S - S_ref) <= 1e-12 * max(scale, 1.0), (method, S, S_ref)
+        _check_result(res, want, 2, N)
+    s.free()
+
+
+def test_smeared_rejects_bad_arguments(ctx, csg):
+    s4 = ctx.sprinkle(4, 100, 1, 0).link()
+    with pytest.raises(csg.CsgError) as e:
+        s4.action_smeared(0.1)
+    assert e.value.code == csg.E_INVAL
+    s2 = ctx.sprinkle(2, 100, 1, 0).link()
+    for bad in (0.0, 1.0, -0.5, 2.0):
+        with pytest.raises(csg.CsgError):
+            s2.action_smeared(bad)
+    s4.free()
+    s2.free()
