@@ -13,7 +13,9 @@ through the public API from host coordinates (copied in every step) to the host
 result.  `roofline` is the action kernel of the chosen method (default: the fp8
 tensor-core form, against the fp8 tensor peak; the popcount form against the
 integer-pipe popcount peak is reported beside it); `cpu_baseline` is the CPU oracle
-on a bounded sample of the same workload.
+on a bounded sample of the same workload.  `batch` compares the batched (CUDA-graph)
+path with one-set-at-a-time calls on 4096 mixed diamonds, and `serve` gives p50/p99
+latency of a Poisson request stream through the service (--no-workloads skips both).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -131,6 +133,16 @@ def recorded_traffic(kernel: str, workload: str):
         return None
 
 
+def reduce_over_ranks(dist, ms: float, units: float, device) -> tuple[float, float]:
+    """Replicas: the job's time is the slowest rank's, its work the sum over ranks."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def launches_per_step(N: int, tc: bool) -> int:
     # sprinkle+keys, chunk ranking, merge passes, gather; link; [expand]; action; finalize
     passes, w = 0, 1024
@@ -211,7 +223,7 @@ def profile_action(args):
     return 0
 
 
-def bench_batch(args):
+def bench_batch(args, emit=True):
     """Plain (one set at a time, each call synchronised) vs batched (one call for all
     sets, every step batched) on the mixed-size workload: 4096 diamonds, d alternating
     2/4, N log-uniform in [256, 8192], seed 3."""
@@ -263,12 +275,13 @@ def bench_batch(args):
                        "method": args.method, "sets": len(specs), "sum_R": R, "sum_W": W},
             "plain": {"value": R / (times["plain"] / 1e3), "ms": times["plain"]},
             "batched_over_plain": times["plain"] / times["batched"]}
-    print(json.dumps(line), flush=True)
     ctx.close()
-    return 0
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def bench_serve(args):
+def bench_serve(args, emit=True):
     """Requests arrive as a Poisson stream (d in {2,4} 50/50, N log-uniform in
     [1024, 65536], seed 4) and go through the continuous-batching service; latency is
     arrival -> result ready.  The rate is swept as fractions of the batched capacity
@@ -347,9 +360,10 @@ def bench_serve(args):
                        "method": "tc"},
             "capacity_req_s": capacity, "plain_req_s": plain_rate,
             "served_capacity_over_plain": capacity / plain_rate, "sweep": sweeps}
-    print(json.dumps(line), flush=True)
     ctx.close()
-    return 0
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -360,6 +374,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--method", default="tc", choices=["popc", "tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the batch and serve summaries of the default line")
     ap.add_argument("--profile-action", action="store_true",
                     help="profiling driver: one sprinkled set, then --reps action launches")
     ap.add_argument("--d", type=int, default=4)
@@ -376,9 +392,11 @@ def main():
     if args.profile_action:
         return profile_action(args)
     if args.workload == "batch":
-        return bench_batch(args)
+        bench_batch(args)
+        return 0
     if args.workload == "serve":
-        return bench_serve(args)
+        bench_serve(args)
+        return 0
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -437,12 +455,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     R_total = sum(r.R for r in results)
     if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        rt = torch.tensor([R_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(rt)
-        R_total = float(rt.item())
+        ms, R_total = reduce_over_ranks(dist, ms, R_total, torch.device("cuda", local))
     value = R_total / (ms / 1e3)
     res = results[-1]
     stage_avg = {k: v / args.steps for k, v in stage_ms.items()}
@@ -519,10 +532,29 @@ def main():
     }
     if clocks:
         line["clocks"] = clocks
+    if not args.no_workloads and world == 1:
+        # the metric's other halves: batched vs plain on the 4096-set mixed workload, and
+        # served p50/p99 latency on a Poisson stream (a 300-request sample of it)
+        ctx.close()
+        ctx = None
+        ns = argparse.Namespace(**vars(args))
+        ns.n_sets, ns.steps, ns.warmup = 4096, 2, 1
+        b = bench_batch(ns, emit=False)
+        line["batch"] = {"workload": b["config"]["workload"], "value": b["value"], "unit": UNIT,
+                         "batched_ms": b["ms_per_step"], "plain_ms": b["plain"]["ms"],
+                         "batched_over_plain": b["batched_over_plain"]}
+        ns.n_req, ns.rates = 300, "0.5,0.9"
+        v = bench_serve(ns, emit=False)
+        line["serve"] = {"workload": v["config"]["workload"], "capacity_req_s": v["capacity_req_s"],
+                         "plain_req_s": v["plain_req_s"],
+                         "served_capacity_over_plain": v["served_capacity_over_plain"],
+                         "sweep": [{k: x[k] for k in ("rate_frac", "throughput_req_s", "p50_ms", "p99_ms",
+                                                      "results_equal_batch")} for x in v["sweep"]]}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
