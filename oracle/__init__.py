@@ -29,6 +29,7 @@ _lock = threading.Lock()
 _lib = None
 
 OK, EINVAL, ENOMEM, EREJECT = 0, -1, -2, -3
+DS2 = 3  # geometry code of the 1+1 de Sitter slab (Sec. 5.1); 2 and 4 are the flat diamonds
 
 
 def build(force: bool = False) -> str:
@@ -69,6 +70,8 @@ def _load():
         lib.orc_finalize.argtypes = [i32, i64, vp, vp, vp]
         lib.orc_action_rows_coords.argtypes = [i32, i64, vp, i64, i64, vp, vp, vp, vp, i32]
         lib.orc_smeared.argtypes = [i64, vp, dbl]
+        lib.orc_sprinkle_desitter.argtypes = [i64, dbl, u64, u64, vp]
+        lib.orc_sprinkle_desitter.restype = i32
         lib.orc_smeared.restype = dbl
         for f in (lib.orc_sprinkle, lib.orc_sort, lib.orc_link, lib.orc_link_row,
                   lib.orc_related, lib.orc_pack, lib.orc_action_rows, lib.orc_finalize,
@@ -99,6 +102,15 @@ def sprinkle(d: int, N: int, seed: int, seq: int = 0, with_attempts: bool = Fals
     if rc != OK:
         raise RuntimeError(f"orc_sprinkle failed: {rc}")
     return (coords, att) if with_attempts else coords
+
+
+def sprinkle_desitter(N: int, eta0: float, seed: int, seq: int = 0) -> np.ndarray:
+    """Unsorted sprinkle into the 1+1 de Sitter slab of Sec. 5.1: rows eta, theta, 0, 0."""
+    coords = np.zeros((4, max(N, 0)), dtype=np.float64)
+    rc = _load().orc_sprinkle_desitter(N, eta0, seed, seq, _p(coords))
+    if rc != OK:
+        raise RuntimeError(f"orc_sprinkle_desitter failed: {rc}")
+    return coords
 
 
 def sort(d: int, coords: np.ndarray):

@@ -42,6 +42,11 @@
 #include <omp.h>
 #endif
 
+/* Geometry codes: 2 = flat 1+1 diamond, 4 = flat 3+1 diamond,
+ * ORC_DS2 = 1+1 de Sitter slab of Sec. 5.1 (coordinates eta, theta). */
+#define ORC_DS2 3
+#define ORC_GEOM_OK(d) ((d) == 2 || (d) == 4 || (d) == ORC_DS2)
+
 #define ORC_OK 0
 #define ORC_EINVAL -1
 #define ORC_ENOMEM -2
@@ -125,6 +130,25 @@ int orc_sprinkle(int d, int64_t N, uint64_t seed, uint64_t seq, double *coords,
     return bad ? ORC_EREJECT : ORC_OK;
 }
 
+/* 1+1 de Sitter slab (Sec. 5.1): eta in [-eta0, eta0] with density proportional to
+ * sec^2(eta), theta uniform in [0, 2 pi).  Inverting the distribution function
+ * (tan eta + tan eta0) / (2 tan eta0) gives eta = atan(tan(eta0) (2U - 1)).  Element e
+ * uses words 0 and 1 of the Philox block (e, 0, 0, 0); coords rows are eta, theta, 0, 0. */
+int orc_sprinkle_desitter(int64_t N, double eta0, uint64_t seed, uint64_t seq, double *coords) {
+    if (N < 0 || (N > 0 && !coords) || !(eta0 > 0.0 && eta0 < 1.5707963267948966)) return ORC_EINVAL;
+    const uint64_t key[2] = {seed, seq};
+    const double t0 = tan(eta0);
+    for (int64_t e = 0; e < N; ++e) {
+        uint64_t ctr[4] = {(uint64_t)e, 0, 0, 0}, r[4];
+        orc_philox4x64_10(ctr, key, r);
+        coords[e] = atan(t0 * (2.0 * orc_unit(r[0]) - 1.0));
+        coords[N + e] = 6.283185307179586 * orc_unit(r[1]);
+        coords[2 * N + e] = 0.0;
+        coords[3 * N + e] = 0.0;
+    }
+    return ORC_OK;
+}
+
 /* ---------------------------------------------------------------- sort ---- */
 
 typedef struct {
@@ -144,7 +168,7 @@ static int orc_key_cmp(const void *pa, const void *pb) {
 /* Sorts the elements by time (Sec. 2.2) and permutes coords in place.
  * perm[p] receives the sprinkle index of the element now at position p. */
 int orc_sort(int d, int64_t N, double *coords, int64_t *perm) {
-    if ((d != 2 && d != 4) || N < 0) return ORC_EINVAL;
+    if (!ORC_GEOM_OK(d) || N < 0) return ORC_EINVAL;
     if (N == 0) return ORC_OK;
     orc_key *keys = (orc_key *)malloc((size_t)N * sizeof(orc_key));
     double *tmp = (double *)malloc((size_t)N * 4 * sizeof(double));
@@ -174,6 +198,13 @@ int orc_sort(int d, int64_t N, double *coords, int64_t *perm) {
 
 /* Relation between sorted elements i < j (the later one is j). */
 static int orc_precedes(int d, int64_t N, const double *c, int64_t i, int64_t j) {
+    if (d == ORC_DS2) {
+        /* timelike on the cylinder: the shorter angular separation is below |d eta|
+         * (Eq. ds_metric: d theta^2 < d eta^2) */
+        const double pi = 3.141592653589793;
+        double ang = pi - fabs(pi - fabs(c[N + j] - c[N + i]));
+        return ang < fabs(c[j] - c[i]);
+    }
     if (d == 2) {
         return c[2 * N + i] < c[2 * N + j] && c[3 * N + i] < c[3 * N + j];
     }
@@ -200,7 +231,7 @@ int orc_related(int d, int64_t N, const double *coords, int64_t i, int64_t j) {
 
 /* Dense symmetric adjacency matrix, one byte per entry (Sec. 2.2.2). */
 int orc_link(int d, int64_t N, const double *coords, uint8_t *rel, int threads) {
-    if ((d != 2 && d != 4) || N < 0 || (N > 0 && (!coords || !rel))) return ORC_EINVAL;
+    if (!ORC_GEOM_OK(d) || N < 0 || (N > 0 && (!coords || !rel))) return ORC_EINVAL;
 #ifdef _OPENMP
     if (threads > 0) omp_set_num_threads(threads);
 #endif
@@ -220,7 +251,7 @@ int orc_link(int d, int64_t N, const double *coords, uint8_t *rel, int threads) 
 /* One row of the adjacency matrix, for sampled checks at sizes where the full
  * N*N matrix is not built. */
 int orc_link_row(int d, int64_t N, const double *coords, int64_t i, uint8_t *row) {
-    if ((d != 2 && d != 4) || i < 0 || i >= N) return ORC_EINVAL;
+    if (!ORC_GEOM_OK(d) || i < 0 || i >= N) return ORC_EINVAL;
     for (int64_t j = 0; j < N; ++j) row[j] = (uint8_t)orc_related(d, N, coords, i, j);
     return ORC_OK;
 }
@@ -314,7 +345,7 @@ int orc_action_rows(int64_t N, const uint8_t *rel, int64_t row_lo, int64_t row_h
  * to check sampled rows of sets too large for the matrix. */
 int orc_action_rows_coords(int d, int64_t N, const double *coords, int64_t row_lo, int64_t row_hi,
                            uint64_t *hist, uint64_t *R, uint64_t *sum_m, uint64_t *W, int threads) {
-    if ((d != 2 && d != 4) || N < 0 || row_lo < 0 || row_hi > N || row_lo > row_hi) return ORC_EINVAL;
+    if (!ORC_GEOM_OK(d) || N < 0 || row_lo < 0 || row_hi > N || row_lo > row_hi) return ORC_EINVAL;
     int64_t bins = N > 0 ? N : 1;
     memset(hist, 0, (size_t)bins * sizeof(uint64_t));
     uint64_t tR = 0, tS = 0, tW = 0;

@@ -342,6 +342,33 @@ def test_smeared_antichain(N):
     assert oracle.smeared(N, np.zeros(N, np.uint64), 0.2) == 2 * 0.2 * N
 
 
+# ------------------------------------------------------ 1+1 de Sitter slab
+
+def test_desitter_sampler_distribution():
+    # Sec. 5.1: eta has density sec^2(eta) / (2 tan eta0) on [-eta0, eta0], theta is uniform
+    from scipy import stats
+    eta0 = 0.5
+    c = oracle.sprinkle_desitter(20000, eta0, seed=3)
+    eta, theta = c[0], c[1]
+    assert np.all(np.abs(eta) <= eta0) and np.all((theta >= 0) & (theta < 2 * math.pi))
+    cdf = lambda x: (np.tan(x) + math.tan(eta0)) / (2 * math.tan(eta0))
+    assert stats.kstest(eta, cdf).pvalue > 1e-4
+    assert stats.kstest(theta, "uniform", args=(0, 2 * math.pi)).pvalue > 1e-4
+
+
+def test_desitter_relation_is_cylinder_light_cone():
+    # timelike iff the shorter arc between the angles is below |d eta| (Eq. ds_metric),
+    # decided here in exact rationals with the min(|dth|, 2 pi - |dth|) form of the arc
+    c, _ = oracle.sort(oracle.DS2, oracle.sprinkle_desitter(150, 0.5, seed=4))
+    rel = oracle.link(oracle.DS2, c)
+    pi = Fraction(math.pi)
+    for i, j in itertools.combinations(range(150), 2):
+        dth = abs(Fraction(c[1, j]) - Fraction(c[1, i]))
+        arc = min(dth, 2 * pi - dth)
+        assert rel[i, j] == (arc < abs(Fraction(c[0, j]) - Fraction(c[0, i])))
+    assert np.all(np.diff(c[0]) >= 0)
+
+
 def test_pack_layout():
     rel = inputs.random_upper_rel(130, 0.3, 1)
     w = oracle.pack(rel)
