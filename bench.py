@@ -281,6 +281,38 @@ def bench_batch(args, emit=True):
     return line
 
 
+def bench_desitter(args):
+    """The paper's convergence experiment (Sec. 5.2, Fig. action): smeared action
+    (Eq. s_smeared, eps = 2^-6) of sprinkles into the 1+1 de Sitter slab with eta0 = 0.5,
+    ten sets per size for N = 2^10 .. 2^17; the mean should approach the Einstein-Hilbert
+    value 4 pi tan(eta0) ~ 6.865 from N ~ 2^14 on, with a spread growing like sqrt(N)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1709_03013_gb300 import csg
+    eta0, eps, graphs = 0.5, 2.0 ** -6, 10
+    S_EH = 4 * math.pi * math.tan(eta0)
+    rows = []
+    with csg.Context(0) as ctx:
+        for p in range(10, 18):
+            N = 1 << p
+            vals, t0 = [], time.perf_counter()
+            for g in range(graphs):
+                s = ctx.sprinkle_desitter(N, eta0, seed=5, seq=g)
+                s.link()
+                S, _ = s.action_smeared(eps, csg.TC)
+                s.free()
+                vals.append(S)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3 / graphs
+            v = np.array(vals)
+            rows.append({"N": N, "mean": float(v.mean()), "std": float(v.std(ddof=1)),
+                         "sem": float(v.std(ddof=1) / math.sqrt(graphs)), "ms_per_set": ms})
+    print(json.dumps({"experiment": "smeared action in the 1+1 de Sitter slab (Sec. 5.2)", "eta0": eta0,
+                      "eps": eps, "sets_per_size": graphs, "S_EH": S_EH, "sizes": rows}), flush=True)
+    return 0
+
+
 def bench_serve(args, emit=True):
     """Requests arrive as a Poisson stream (d in {2,4} 50/50, N log-uniform in
     [1024, 65536], seed 4) and go through the continuous-batching service; latency is
@@ -381,7 +413,7 @@ def main():
     ap.add_argument("--d", type=int, default=4)
     ap.add_argument("--n", type=int, default=40000)
     ap.add_argument("--reps", type=int, default=2)
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "desitter"],
                     help="single: the d=4 N=65536 set; batch: 4096 mixed diamonds, plain vs batched; "
                          "serve: Poisson request stream through the service, p50/p99 latency")
     ap.add_argument("--n-sets", type=int, default=4096)
@@ -396,6 +428,9 @@ def main():
         return 0
     if args.workload == "serve":
         bench_serve(args)
+        return 0
+    if args.workload == "desitter":
+        bench_desitter(args)
         return 0
     if args.warmup < 3:
         args.warmup = 3

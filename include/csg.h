@@ -109,6 +109,17 @@ const char *csg_last_error(void);
 int csg_sprinkle(csg_ctx *ctx, int d, int64_t N, uint64_t seed, uint64_t seq, void *stream,
                  csg_set **out);
 
+/* Sprinkle N elements into the 1+1 de Sitter slab of Sec. 5.1 (Eq. ds_metric,
+ * ds^2 = sec^2(eta) (-d eta^2 + d theta^2)), the paper's benchmark manifold: eta in
+ * [-eta0, eta0] with density sec^2(eta) / (2 tan eta0), drawn as
+ * eta = atan(tan(eta0) (2U - 1)) from word 0 of the Philox block (e, 0, 0, 0) with key
+ * (seed, seq), and theta = 2 pi U' from word 1.  Coordinates are stored as rows
+ * (eta, theta, 0, 0), sorted by (eta, e).  Two elements are related when
+ * pi - |pi - |d theta|| < |d eta|.  The set uses the 1+1 action (d = 2).
+ * 0 < eta0 < pi/2, 1 <= N <= CSG_MAX_N. */
+int csg_sprinkle_desitter(csg_ctx *ctx, int64_t N, double eta0, uint64_t seed, uint64_t seq,
+                          void *stream, csg_set **out);
+
 /* Make a set from host coordinates [4][N] (layout above, any order): copies them
  * to the device and sorts them by time like csg_sprinkle. */
 int csg_set_from_coords(csg_ctx *ctx, int d, int64_t N, const double *host_coords,

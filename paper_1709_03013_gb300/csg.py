@@ -59,6 +59,7 @@ EXPORTS = [
     "csg_action_hist", "csg_action_batch", "csg_run_batch", "csg_serve_submit", "csg_serve_poll",
     "csg_serve_cancel", "csg_export_coords", "csg_export_bitmap", "csg_set_info", "csg_set_free",
     "csg_action_noalloc", "csg_set_timing", "csg_stage_times", "csg_action_smeared",
+    "csg_sprinkle_desitter",
 ]
 
 _lib = None
@@ -99,6 +100,7 @@ def load(path: str = LIB_PATH):
         "csg_set_free": (None, [vp]),
         "csg_action_noalloc": (i32, [i32, i64, vp, i64, vp, vp]),
         "csg_set_timing": (i32, [vp, i32]),
+        "csg_sprinkle_desitter": (i32, [vp, i64, ctypes.c_double, u64, u64, vp, pp]),
         "csg_action_smeared": (i32, [vp, vp, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_double), R, vp]),
         "csg_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_double), i32]),
     }
@@ -246,6 +248,13 @@ class Context:
         h = ctypes.c_void_p()
         _check(load().csg_sprinkle(self.handle, d, N, seed, seq, _stream(stream), ctypes.byref(h)),
                "csg_sprinkle")
+        return CausalSet(self, h.value)
+
+    def sprinkle_desitter(self, N: int, eta0: float, seed: int, seq: int = 0, stream=None) -> CausalSet:
+        """Sprinkle into the 1+1 de Sitter slab |eta| <= eta0 (the paper's benchmark manifold)."""
+        h = ctypes.c_void_p()
+        _check(load().csg_sprinkle_desitter(self.handle, N, eta0, seed, seq, _stream(stream), ctypes.byref(h)),
+               "csg_sprinkle_desitter")
         return CausalSet(self, h.value)
 
     def set_from_coords(self, d: int, coords: np.ndarray, stream=None) -> CausalSet:

@@ -164,6 +164,28 @@ int csg_sprinkle(csg_ctx *ctx, int d, int64_t N, uint64_t seed, uint64_t seq, vo
     return CSG_OK;
 }
 
+int csg_sprinkle_desitter(csg_ctx *ctx, int64_t N, double eta0, uint64_t seed, uint64_t seq,
+                          void *stream, csg_set **out) {
+    if (!ctx || !out || !(eta0 > 0.0 && eta0 < 1.5707963267948966)) {
+        set_error("csg_sprinkle_desitter: bad arguments (0 < eta0 < pi/2)");
+        return CSG_E_INVAL;
+    }
+    TimerScope ts(ctx);
+    CSG_CUDA_TRY(cudaSetDevice(ctx->device));
+    csg_set *s = nullptr;
+    int rc = alloc_set(ctx, 2, N, &s);
+    if (rc != CSG_OK) return rc;
+    s->geom = GEOM_DS2;
+    SprinkleSpec sp{2, GEOM_DS2, N, seed, seq, s->coords, nullptr, tan(eta0)};
+    rc = sprinkle_sort_batch(&sp, 1, (cudaStream_t)stream, nullptr);
+    if (rc != CSG_OK) {
+        free_set(s);
+        return rc;
+    }
+    *out = s;
+    return CSG_OK;
+}
+
 int csg_set_from_coords(csg_ctx *ctx, int d, int64_t N, const double *host_coords, void *stream,
                         csg_set **out) {
     if (!ctx || !host_coords) {
@@ -208,7 +230,8 @@ int csg_link(csg_ctx *ctx, csg_set *set, void *stream) {
     }
     CSG_CUDA_TRY(cudaSetDevice(ctx->device));
     TimerScope ts(ctx);
-    LinkSpec L{set->d, 0, set->N, set->stride, set->coords, set->rows, 0, set->coord_scale};
+    LinkSpec L{set->geom ? set->geom : set->d, 0, set->N, set->stride, set->coords, set->rows, 0,
+               set->coord_scale};
     int rc = link_batch(&L, 1, (cudaStream_t)stream);
     if (rc == CSG_OK) set->linked = true;
     return rc;

@@ -61,13 +61,17 @@ struct WorkItem {
 // ---------------------------------------------------------------- kernels
 
 // Sprinkle + sort for a batch of sets sharing one launch sequence.
+// Geometry of a set: the flat diamonds (d = 2 or 4) or the 1+1 de Sitter slab of Sec. 5.1.
+constexpr int GEOM_DS2 = 3;
+
 struct SprinkleSpec {
     int32_t d;
-    int32_t pad;
+    int32_t geom;              // 2, 4 or GEOM_DS2 (0: same as d)
     int64_t N;
     uint64_t seed, seq;
     double *coords;            // [4][N] sorted output
     unsigned long long *err;   // per-set error word (the set's CNT_ERR), or null
+    double param;              // GEOM_DS2: tan(eta0)
 };
 struct SprinklePlan {
     int n = 0;
@@ -87,7 +91,7 @@ int sprinkle_sort_batch(const SprinkleSpec *specs_host, int n, cudaStream_t st,
 
 // Link a batch of sets (coords -> rows).
 struct LinkSpec {
-    int32_t d;
+    int32_t d;  // geometry: 2, 4 or GEOM_DS2
     int32_t pad;
     int64_t N;
     int64_t stride;
@@ -97,11 +101,11 @@ struct LinkSpec {
     double coord_scale;  // max(1, max |coordinate|): scales the d=4 float-screen margin
 };
 struct LinkPlan {
-    struct Part {  // the sets of one dimension (part 0: d=2, part 1: d=4)
+    struct Part {  // the sets of one geometry (part 0: d=2, 1: d=4, 2: 1+1 de Sitter)
         int n = 0;
         int64_t T = 0;
         size_t t_rows = 0, t_starts = 0;
-    } part[2];
+    } part[3];
     int64_t T = 0;
 };
 LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc);

@@ -20,6 +20,7 @@ struct csg_set {
     bool linked = false;
     bool from_bitmap = false;
     double coord_scale = 1.0;    // max(1, max |coordinate|)
+    int geom = 0;                // 0: flat diamond of dimension d; 3: 1+1 de Sitter slab
 };
 
 namespace csg {

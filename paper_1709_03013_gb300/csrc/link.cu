@@ -19,7 +19,12 @@
 // 4 * 4.01 * 2^-24, so the float value is within 80.1 * 2^-24 (< 4.8e-6) of the real
 // one, and the double expression within 40 * 2^-53 of it.  A float difference
 // beyond +-1e-5 therefore fixes the double decision.
-// Pairs inside the margin are decided in double.  Every error term scales with the
+// Pairs inside the margin are decided in double.
+//
+// The 1+1 de Sitter slab (Sec. 5.1) relates two elements when the shorter arc between
+// their angles is below |d eta|, i.e. pi - |pi - |d theta|| < |d eta| in double.  With
+// |eta| < pi/2 and theta in [0, 2 pi), the float form of |d eta| minus that arc is within
+// 2.6e-6 of the real value, so the same 1e-5 screen applies.  Every error term scales with the
 // square of the coordinate range, so sets whose coordinates exceed 1 in magnitude
 // use the margin 1e-5 * max|coordinate|^2 (coordinates are limited to 1e15, far
 // below float overflow of the squares).
@@ -71,6 +76,13 @@ __device__ __forceinline__ uint64_t order_key(double x) {
     return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
 }
 
+// 1+1 de Sitter slab (Sec. 5.1): related iff pi - |pi - |d theta|| < |d eta| in double
+__device__ __forceinline__ bool exact_ds(double ei, double thi, double ek, double thk) {
+    const double pi = 3.141592653589793;
+    const double ang = __dsub_rn(pi, fabs(__dsub_rn(pi, fabs(__dsub_rn(thk, thi)))));
+    return ang < fabs(__dsub_rn(ek, ei));
+}
+
 __device__ __forceinline__ bool exact4(double ti, double xi, double yi, double zi, double tk,
                                        double xk, double yk, double zk) {
     if (!(tk > ti)) return false;
@@ -107,6 +119,15 @@ __device__ __forceinline__ uint64_t link_word(int q, int c0, int ncol, const uin
         if (!FULL && (c < c0 || c >= ncol)) continue;
         if (D == 2) {
             if ((ui < ck[0][c]) & (vi < ck[1][c])) acc |= 1ull << b;
+        } else if (D == GEOM_DS2) {
+            // cylinder light cone: shorter arc below |d eta|
+            const float4 k4 = cf4[c];
+            const float deta = fabsf(__fsub_rn(k4.x, tf));
+            const float dth = fabsf(__fsub_rn(k4.y, xf));
+            const float ang = __fsub_rn(3.14159265f, fabsf(__fsub_rn(3.14159265f, dth)));
+            const float diff = __fsub_rn(deta, ang);
+            if (diff > screen) acc |= 1ull << b;
+            if (fabsf(diff) <= screen) amb |= 1ull << b;
         } else {
             const float4 k4 = cf4[c];
             const float dt = __fsub_rn(k4.x, tf);
@@ -119,13 +140,14 @@ __device__ __forceinline__ uint64_t link_word(int q, int c0, int ncol, const uin
             if (fabsf(diff) <= screen) amb |= 1ull << b;
         }
     }
-    if (D == 4) {
+    if (D != 2) {
         // pairs inside the screen's margin: decide in double (rare)
         while (amb) {
             const int b = __ffsll((long long)amb) - 1;
             amb &= amb - 1;
             const int c = q * 64 + b;
-            if (exact4(ti, xi, yi, zi, cd[0][c], cd[1][c], cd[2][c], cd[3][c]))
+            if (D == GEOM_DS2 ? exact_ds(ti, xi, cd[0][c], cd[1][c])
+                              : exact4(ti, xi, yi, zi, cd[0][c], cd[1][c], cd[2][c], cd[3][c]))
                 acc |= 1ull << b;
             else
                 acc &= ~(1ull << b);
@@ -168,7 +190,7 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
         if (D == 2) {
             ck[0][r] = order_key(S.coords[2 * N + kc]);
             ck[1][r] = order_key(S.coords[3 * N + kc]);
-        } else {
+        } else {  // d=4: t, x, y, z; de Sitter: eta, theta, 0, 0
             double v[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -192,7 +214,7 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
         if (D == 2) {
             ui = order_key(S.coords[2 * N + i]);
             vi = order_key(S.coords[3 * N + i]);
-        } else {
+        } else {  // d=4 and de Sitter read the same rows
             ti = S.coords[i];
             xi = S.coords[N + i];
             yi = S.coords[2 * N + i];
@@ -259,9 +281,9 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
 LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
     LinkPlan p;
     *rc = CSG_OK;
-    // one tile space per dimension: each launch runs one instantiation of the kernel
-    for (int part = 0; part < 2; ++part) {
-        const int d = part == 0 ? 2 : 4;
+    // one tile space per geometry: each launch runs one instantiation of the kernel
+    for (int part = 0; part < 3; ++part) {
+        const int d = part == 0 ? 2 : (part == 1 ? 4 : GEOM_DS2);
         std::vector<LinkRow> rows;
         std::vector<int64_t> starts;
         int64_t T = 0;
@@ -277,7 +299,7 @@ LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
             L.nb = (L.N + kTile - 1) / kTile;
             L.nbc = L.stride / kTileWords;
             L.tile_off = T;
-            L.screen = 1e-5f * (float)(specs[s].coord_scale * specs[s].coord_scale);
+            L.screen = d == GEOM_DS2 ? 1e-5f : 1e-5f * (float)(specs[s].coord_scale * specs[s].coord_scale);
             L.pad2 = 0.f;
             if (L.stride % 16 != 0 || L.nbc < L.nb) {
                 set_error("link: stride %lld does not cover N=%lld", (long long)L.stride, (long long)L.N);
@@ -308,9 +330,11 @@ LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
 void link_launch(const LinkPlan &p, const Arena &a, cudaStream_t st) {
     if (p.T == 0) return;
     stage_begin(CSG_STAGE_LINK, st);
-    const LinkPlan::Part &p2 = p.part[0], &p4 = p.part[1];
+    const LinkPlan::Part &p2 = p.part[0], &p4 = p.part[1], &p3 = p.part[2];
     if (p2.T) link_kernel<2><<<(unsigned)p2.T, kTile, 0, st>>>(a.tab<LinkRow>(p2.t_rows), a.tab<int64_t>(p2.t_starts), p2.n);
     if (p4.T) link_kernel<4><<<(unsigned)p4.T, kTile, 0, st>>>(a.tab<LinkRow>(p4.t_rows), a.tab<int64_t>(p4.t_starts), p4.n);
+    if (p3.T)
+        link_kernel<GEOM_DS2><<<(unsigned)p3.T, kTile, 0, st>>>(a.tab<LinkRow>(p3.t_rows), a.tab<int64_t>(p3.t_starts), p3.n);
     stage_end(CSG_STAGE_LINK, st);
 }
 

@@ -66,14 +66,14 @@ __device__ __forceinline__ uint64_t order_key(double x) {
 // ------------------------------------------------------------ batch tables
 
 struct SetRow {
-    int32_t d;
-    int32_t pad;
+    int32_t d;     // geometry: 2, 4 or GEOM_DS2
     int64_t N;
     uint64_t seed, seq;
     double *coords;      // sorted output [4][N]
     int64_t off;         // element offset in the flattened batch
     int64_t chunk_off;   // first chunk index of the set
     unsigned long long *err;  // set to CNT_ERR_REJECT when an element hits the attempt cap
+    double param;             // GEOM_DS2: tan(eta0)
 };
 
 __device__ __forceinline__ int find_set(const int64_t *__restrict__ starts, int n, int64_t g) {
@@ -110,6 +110,14 @@ __global__ void sprinkle_keys_kernel(const SetRow *__restrict__ sets, const int6
             c1 = tmp[E + g];
             c2 = tmp[2 * E + g];
             c3 = tmp[3 * E + g];
+        } else if (S.d == GEOM_DS2) {
+            // 1+1 de Sitter slab (Sec. 5.1): eta by inverting the sec^2 distribution,
+            // theta uniform on the circle; rows eta, theta, 0, 0
+            U64x4 r = philox4x64_10((uint64_t)e, 0, 0, 0, S.seed, S.seq);
+            c0 = atan(__dmul_rn(S.param, __dsub_rn(__dmul_rn(2.0, unit53(r.w[0])), 1.0)));
+            c1 = __dmul_rn(6.283185307179586, unit53(r.w[1]));
+            c2 = 0.0;
+            c3 = 0.0;
         } else if (S.d == 2) {
             U64x4 r = philox4x64_10((uint64_t)e, 0, 0, 0, S.seed, S.seq);
             double u = unit53(r.w[0]), v = unit53(r.w[1]);
@@ -256,8 +264,8 @@ SprinklePlan sprinkle_plan(const SprinkleSpec *specs, int n, Arena &a, bool from
     std::vector<int64_t> starts(n), cstarts(n);
     bool shared_err = false;
     for (int s = 0; s < n; ++s) {
-        rows[s].d = specs[s].d;
-        rows[s].pad = 0;
+        rows[s].d = specs[s].geom ? specs[s].geom : specs[s].d;
+        rows[s].param = specs[s].param;
         rows[s].N = specs[s].N;
         rows[s].seed = specs[s].seed;
         rows[s].seq = specs[s].seq;

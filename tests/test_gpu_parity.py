@@ -258,3 +258,27 @@ def test_smeared_rejects_bad_arguments(ctx, csg):
             s2.action_smeared(bad)
     s4.free()
     s2.free()
+
+
+@pytest.mark.parametrize("N", [1, 2, 700, 3001])
+def test_desitter_slab(ctx, csg, N):
+    # Sec. 5.1 slab: theta is the same IEEE product on both sides (bit-exact); eta goes
+    # through each side's own atan (CUDA's and the C library's differ by an ulp or two),
+    # so coordinates match to 4e-16 and the link is checked on the GPU's own coordinates
+    eta0 = 0.5
+    s = ctx.sprinkle_desitter(N, eta0, 11, 2)
+    got_c = s.coords()
+    want_c, _ = oracle.sort(oracle.DS2, oracle.sprinkle_desitter(N, eta0, 11, 2))
+    assert np.array_equal(got_c[1], want_c[1])
+    assert np.max(np.abs(got_c[0] - want_c[0]), initial=0.0) <= 4e-16
+    assert np.all(np.diff(got_c[0]) >= 0)
+    s.link()
+    rel = oracle.link(oracle.DS2, got_c)
+    assert np.array_equal(s.bitmap(), oracle.pack(rel, s.info()["stride"]))
+    want = oracle.action(rel)
+    for method in (csg.POPC, csg.TC):
+        _check_result(s.action(method), want, 2, N)
+        S, _ = s.action_smeared(2 ** -6, method)
+        S_ref = oracle.smeared(N, want["hist"], 2 ** -6)
+        assert abs(S - S_ref) <= 1e-12 * max(2 * 2 ** -6 * N + 8 * 2 ** -12 * want["R"], 1.0)
+    s.free()
