@@ -73,6 +73,8 @@ def _load():
         lib.orc_sprinkle_desitter.argtypes = [i64, dbl, u64, u64, vp]
         lib.orc_sprinkle_desitter.restype = i32
         lib.orc_smeared.restype = dbl
+        lib.orc_dalembertian.argtypes = [i64, vp, vp, dbl, vp, vp, i32]
+        lib.orc_dalembertian.restype = i32
         for f in (lib.orc_sprinkle, lib.orc_sort, lib.orc_link, lib.orc_link_row,
                   lib.orc_related, lib.orc_pack, lib.orc_action_rows, lib.orc_finalize,
                   lib.orc_action_rows_coords):
@@ -236,6 +238,22 @@ def smeared(N: int, hist: np.ndarray, eps: float) -> float:
     src = np.asarray(hist, dtype=np.uint64)
     h[:min(len(src), len(h))] = src[:len(h)]
     return float(_load().orc_smeared(N, _p(h), float(eps)))
+
+
+def dalembertian(rel: np.ndarray, phi, l: float = 1.0, threads: int = 0):
+    """Discrete d'Alembertian of Eq. b_local for every element of the time-ordered set
+    with relation matrix rel.  Returns (Bphi, L) with L[x] = (|L_1|, |L_2|, |L_3|)."""
+    rel = np.ascontiguousarray(rel, dtype=np.uint8)
+    N = rel.shape[0]
+    ph = np.ascontiguousarray(phi, dtype=np.float64)
+    if ph.shape != (N,):
+        raise ValueError("phi must have one value per element")
+    out = np.zeros(N, dtype=np.float64)
+    L = np.zeros((N, 3), dtype=np.int64)
+    rc = _load().orc_dalembertian(N, _p(rel), _p(ph), float(l), _p(out), _p(L), threads)
+    if rc != 0:
+        raise ValueError(f"orc_dalembertian failed ({rc})")
+    return out, L
 
 
 def run(d: int, N: int, seed: int, seq: int = 0, threads: int = 0) -> dict:

@@ -16,6 +16,9 @@
  *   - the 1+1 BD action S2                           (Eq. s_local)
  *   - the 3+1 BD action S4 = (4/sqrt6)(N-N0+9N1-16N2+8N3)  (Benincasa-Dowker,
  *     cited in Sec. 1.2; the paper prints only the 1+1 form)
+ *   - the smeared action S_eps                       (Eq. s_smeared)
+ *   - sprinkling into the 1+1 de Sitter slab         (Sec. 5.1)
+ *   - the discrete d'Alembertian B phi per element   (Eq. b_local)
  *
  * Readings where the paper is silent (listed in the design notes too):
  *   - RNG: Philox4x64-10 (Salmon et al., SC'11), counter (element, attempt, 0, 0),
@@ -437,4 +440,38 @@ double orc_smeared(int64_t N, const uint64_t *hist, double eps) {
         acc += (double)n_i * f2;
     }
     return 2.0 * eps * ((double)N - 2.0 * eps * acc);
+}
+
+/* ------------------------------------------------------- d'Alembertian ---- */
+
+/* Discrete d'Alembertian of Eq. b_local (Sec. 1.2), 1+1 dimensions:
+ *   B phi(x) = (2 / l^2) ( -phi(x) + 2 [ sum_{y in L_1} - 2 sum_{y in L_2} + sum_{y in L_3} ] phi(y) ),
+ * where L_i is the set of elements y preceding x with exactly i - 1 elements z strictly
+ * between them (y < z < x).  rel is the symmetric relation matrix of time-ordered
+ * elements, so y precedes x iff y < x and rel[y][x].  For every x the three sums run over
+ * y in increasing label order and are combined as printed.  The work is O(N^3). */
+int orc_dalembertian(int64_t N, const uint8_t *rel, const double *phi, double l, double *out,
+                     int64_t *L123, int threads) {
+    if (N < 0 || (N > 0 && (!rel || !phi || !out)) || !(l > 0.0)) return ORC_EINVAL;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t x = 0; x < N; ++x) {
+        double s[3] = {0.0, 0.0, 0.0};
+        int64_t cnt[3] = {0, 0, 0};
+        for (int64_t y = 0; y < x; ++y) {
+            if (!rel[y * N + x]) continue;
+            int64_t m = 0;
+            for (int64_t z = y + 1; z < x; ++z) m += rel[y * N + z] & rel[z * N + x];
+            if (m <= 2) {
+                s[m] += phi[y];
+                cnt[m] += 1;
+            }
+        }
+        out[x] = (2.0 / (l * l)) * (-phi[x] + 2.0 * (s[0] - 2.0 * s[1] + s[2]));
+        if (L123)
+            for (int k = 0; k < 3; ++k) L123[3 * x + k] = cnt[k];
+    }
+    return ORC_OK;
 }

@@ -28,8 +28,10 @@ def read_golden(name):
             if key == "rel":
                 i, j = (int(x) for x in val.split())
                 out["rel"].append((i, j))
-            elif key in ("Nk",):
+            elif key in ("Nk", "L123"):
                 out[key] = [int(x) for x in val.split()]
+            elif key in ("phi", "Bphi"):
+                out[key] = [float(x) for x in val.split()]
             elif key in ("S2", "S4") or key.startswith("Seps"):
                 out[key] = float(val)
             else:

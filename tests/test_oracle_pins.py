@@ -382,3 +382,72 @@ def test_pack_layout():
 def test_finalize_rejects_bad_dimension():
     with pytest.raises(RuntimeError):
         oracle.finalize(3, 5, [0, 0, 0, 0])
+
+
+# ------------------------------------------------------- d'Alembertian pins
+
+@pytest.mark.parametrize("name", ["diamond4.txt", "npos6.txt"])
+def test_dalembertian_golden(golden, name):
+    g = golden(name)
+    rel = inputs.rel_from_edges(g["N"], g["rel"])
+    B, L = oracle.dalembertian(rel, g["phi"], 1.0)
+    assert B.tolist() == g["Bphi"]
+    assert L.reshape(-1).tolist() == g["L123"]
+    # B scales as 1/l^2 (Eq. b_local); powers of two scale exactly
+    B2, _ = oracle.dalembertian(rel, g["phi"], 0.5)
+    assert B2.tolist() == [4.0 * b for b in g["Bphi"]]
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 12, 70])
+def test_dalembertian_chain(N):
+    # In a chain the element k steps before x has k-1 elements between it and x, so
+    # L_1, L_2, L_3 of x are x-1, x-2, x-3 (those that exist).
+    phi = np.random.default_rng(N).normal(size=N)
+    B, L = oracle.dalembertian(inputs.chain_rel(N), phi, 0.75)
+    for x in range(N):
+        terms = [(1.0, x - 1), (-2.0, x - 2), (1.0, x - 3)]
+        inner = sum(c * phi[y] for c, y in terms if y >= 0)
+        want = 2.0 / 0.75 ** 2 * (-phi[x] + 2.0 * inner)
+        assert abs(B[x] - want) <= 1e-13 * (1.0 + abs(want))
+        assert L[x].tolist() == [int(x >= 1), int(x >= 2), int(x >= 3)]
+
+
+@pytest.mark.parametrize("N", [0, 1, 9])
+def test_dalembertian_antichain(N):
+    phi = np.arange(N, dtype=np.float64) - 3.5
+    B, L = oracle.dalembertian(inputs.antichain_rel(N), phi, 2.0)
+    assert B.tolist() == (-0.5 * phi).tolist()  # 2/l^2 = 1/2, no past
+    assert not L.any()
+
+
+@pytest.mark.parametrize("d,N,seed", [(2, 40, 5), (2, 64, 6)])
+def test_dalembertian_matches_graph_library(d, N, seed):
+    pytest.importorskip("networkx")
+    rel = oracle.link(d, oracle.sprinkle_sorted(d, N, seed))
+    g, desc, anc = _nx_intervals(rel)
+    phi = np.random.default_rng(seed).uniform(-1, 1, size=N)
+    B, L = oracle.dalembertian(rel, phi, 1.0)
+    for x in range(N):
+        layers = [[], [], []]
+        for y in sorted(anc[x]):
+            m = len(desc[y] & anc[x])
+            if m <= 2:
+                layers[m].append(y)
+        assert L[x].tolist() == [len(v) for v in layers]
+        inner = math.fsum(phi[y] for y in layers[0]) - 2 * math.fsum(phi[y] for y in layers[1]) \
+            + math.fsum(phi[y] for y in layers[2])
+        want = 2.0 * (-phi[x] + 2.0 * inner)
+        bound = 2.0 * (abs(phi[x]) + 2.0 * sum(abs(phi[y]) * (2 if k == 1 else 1)
+                                               for k in range(3) for y in layers[k]))
+        assert abs(B[x] - want) <= 8 * (N + 4) * 2.0 ** -53 * bound
+
+
+@pytest.mark.parametrize("d,N,seed", [(2, 300, 7), (2, 700, 8)])
+def test_dalembertian_of_one_sums_to_minus_action(d, N, seed):
+    # With phi = 1 and l = 1, sum_x B1(x) = 2(-N + 2 n_1 - 4 n_2 + 2 n_3) = -S_BD (Eq. s_local),
+    # and every partial sum is a small integer, so the identity is exact.
+    rel = oracle.link(d, oracle.sprinkle_sorted(d, N, seed))
+    B, L = oracle.dalembertian(rel, np.ones(N), 1.0)
+    _, S2 = oracle.finalize(2, N, oracle.action(rel)["Nk"])
+    assert float(B.sum()) == -S2
+    assert L.sum(axis=0).tolist() == [int(v) for v in oracle.action(rel)["Nk"][:3]]
