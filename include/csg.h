@@ -167,6 +167,21 @@ int csg_action_hist(csg_ctx *ctx, csg_set *set, int method, uint64_t *dev_hist, 
 int csg_action_smeared(csg_ctx *ctx, csg_set *set, int method, double eps, double *S_eps,
                        csg_result *out, void *stream);
 
+/* Discrete d'Alembertian of Eq. b_local (Sec. 1.2) at every element of a 1+1 set:
+ *   Bphi[x] = (2 / l^2) ( -phi[x] + 2 [ sum_{y in L_1} - 2 sum_{y in L_2} + sum_{y in L_3} ] phi[y] ),
+ * where L_i holds the elements y preceding x with exactly i-1 elements strictly between
+ * them.  phi and Bphi are caller-owned DEVICE arrays of N doubles in the set's element
+ * order (time order for sprinkled sets, the caller's order for bitmaps); they must not
+ * overlap.  l > 0 is the discreteness scale.  The layer sums come from the same pass
+ * that counts the intervals (method CSG_POPC or CSG_TC); they are accumulated with
+ * atomic adds, so their rounding order is unspecified (each result is within the
+ * recursive-summation bound of the exact value; with integer phi, |phi| < 2^32, and l a
+ * power of two every step is exact).
+ * The set must have d = 2 (the paper gives the 1+1 form only) and a bitmap.  *out
+ * (optional) receives the action counts as from csg_action.  Synchronises the stream. */
+int csg_dalembertian(csg_ctx *ctx, csg_set *set, int method, const double *phi, double l, double *Bphi,
+                     csg_result *out, void *stream);
+
 /* Actions of n sets in one pass: all sets' work in one persistent launch over a
  * queue of (set, row group) items, longest first.  out[n] is filled in order. */
 int csg_action_batch(csg_ctx *ctx, csg_set *const *sets, int n, int method, csg_result *out,

@@ -59,7 +59,7 @@ EXPORTS = [
     "csg_action_hist", "csg_action_batch", "csg_run_batch", "csg_serve_submit", "csg_serve_poll",
     "csg_serve_cancel", "csg_export_coords", "csg_export_bitmap", "csg_set_info", "csg_set_free",
     "csg_action_noalloc", "csg_set_timing", "csg_stage_times", "csg_action_smeared",
-    "csg_sprinkle_desitter",
+    "csg_sprinkle_desitter", "csg_dalembertian",
 ]
 
 _lib = None
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
         "csg_set_timing": (i32, [vp, i32]),
         "csg_sprinkle_desitter": (i32, [vp, i64, ctypes.c_double, u64, u64, vp, pp]),
         "csg_action_smeared": (i32, [vp, vp, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_double), R, vp]),
+        "csg_dalembertian": (i32, [vp, vp, i32, vp, ctypes.c_double, vp, R, vp]),
         "csg_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_double), i32]),
     }
     for name, (res, args) in sig.items():
@@ -204,6 +205,17 @@ class CausalSet:
         _check(load().csg_action_smeared(self.ctx.handle, self.handle, method, eps, ctypes.byref(S),
                                          ctypes.byref(r), _stream(stream)), "csg_action_smeared")
         return S.value, Result.of(r)
+
+    def dalembertian(self, dev_phi_ptr: int, dev_Bphi_ptr: int, l: float = 1.0, method: int = POPC,
+                     stream=None) -> Result:
+        """Discrete d'Alembertian of Eq. b_local: reads N doubles at dev_phi_ptr, writes N
+        doubles at dev_Bphi_ptr (device memory, element order of the set); returns the
+        action counts of the same pass."""
+        r = _Result()
+        _check(load().csg_dalembertian(self.ctx.handle, self.handle, method, ctypes.c_void_p(dev_phi_ptr), l,
+                                       ctypes.c_void_p(dev_Bphi_ptr), ctypes.byref(r), _stream(stream)),
+               "csg_dalembertian")
+        return Result.of(r)
 
     def coords(self) -> np.ndarray:
         N = self.N

@@ -18,7 +18,8 @@
 //
 // The lanes' partial counts of a pair are summed with warp shuffles; the pair's m
 // goes into per-lane counters (N_0..N_3, R, sum m, W) flushed with 64-bit atomics,
-// and optionally into a full histogram in global memory.  Work items come from an
+// optionally into a full histogram in global memory and, for pairs with m <= 2, into
+// the per-element sums of the discrete d'Alembertian (Eq. b_local).  Work items come from an
 // atomic queue (persistent CTAs), in ascending i0, which is roughly longest first.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -40,6 +41,8 @@ struct Smem {
     uint64_t bar;
     int item;
     int stop;
+    const double *phi;  // the current item's d'Alembertian field and sums (or null)
+    double *acc;
 };
 
 struct Counters {
@@ -52,12 +55,13 @@ struct Counters {
 // cnt read the all-zero row at zoff.  K is 1, 2, 4 or 8, which keeps the code small
 // enough for the instruction cache.  Lane 0 books the pairs' interval sizes after a
 // warp reduction.
-template <int K>
+template <int K, bool PHI>
 __device__ __forceinline__ void sweep_rows(uint32_t mask, int cnt, int zoff, const uint64_t *__restrict__ A,
                                            int pitch,
                                            const uint64_t *__restrict__ bj, int wj, uint64_t lastmask,
                                            int lane, int64_t j, int64_t i0, Counters &c,
-                                           unsigned long long *__restrict__ hist, long long nbins) {
+                                           unsigned long long *__restrict__ hist, long long nbins,
+                                           const Smem *ctl) {
     int off[K];
     uint32_t m = mask;
     int rsum = 0;
@@ -101,6 +105,14 @@ __device__ __forceinline__ void sweep_rows(uint32_t mask, int cnt, int zoff, con
             c.n3 += v == 3u;
             c.M += v;
             if (hist != nullptr && (long long)v < nbins) atomicAdd(&hist[v], 1ull);
+            // Eq. b_local: i = i0 + r is in L_{v+1} of j, r the k-th set bit of mask
+            if (PHI && v < 3u) {
+                double *acc_phi = ctl->acc;
+                uint32_t mm = mask;  // k < cnt = popc(mask), so mm keeps a set bit
+                for (int t = 0; t < k; ++t) mm &= mm - 1;
+                const int r = __ffs(mm) - 1;
+                atomicAdd(&acc_phi[j], (v == 1u ? -2.0 : 1.0) * ctl->phi[i0 + r]);
+            }
         }
     }
     if (lane == 0) {
@@ -110,25 +122,27 @@ __device__ __forceinline__ void sweep_rows(uint32_t mask, int cnt, int zoff, con
     }
 }
 
-template <int G>
+template <int G, bool PHI>
 __device__ __forceinline__ void dispatch_rows(int cnt, uint32_t mask, const uint64_t *__restrict__ A,
                                               int pitch, const uint64_t *__restrict__ bj, int wj,
                                               uint64_t lastmask, int lane, int64_t j, int64_t i0,
                                               Counters &c, unsigned long long *__restrict__ hist,
-                                              long long nbins) {
+                                              long long nbins, const Smem *ctl) {
     const int zoff = G * pitch;  // the zero row after the G staged rows
     if (cnt <= 1)
-        sweep_rows<1>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins);
+        sweep_rows<1, PHI>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins, ctl);
     else if (cnt <= 2)
-        sweep_rows<2>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins);
+        sweep_rows<2, PHI>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins, ctl);
     else if (cnt <= 4 || G <= 4) {
-        if constexpr (G >= 4) sweep_rows<4>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins);
+        if constexpr (G >= 4)
+            sweep_rows<4, PHI>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins, ctl);
     } else {
-        if constexpr (G >= 8) sweep_rows<8>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins);
+        if constexpr (G >= 8)
+            sweep_rows<8, PHI>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins, ctl);
     }
 }
 
-template <int G>
+template <int G, bool PHI>
 __global__ void __launch_bounds__(kThreads, 1)
 action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict__ items,
                    int n_items, int pitch, unsigned int *__restrict__ queue,
@@ -173,6 +187,10 @@ action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict_
 
         // ---- stage the group's rows with bulk copies
         if (threadIdx.x == 0) {
+            if (PHI) {
+                ctl->phi = S.phi;
+                ctl->acc = S.acc;
+            }
             ptx::fence_proxy_async_smem();
             const uint32_t bytes = (uint32_t)nwa * 8u;
             ptx::mbar_arrive_expect_tx(&ctl->bar, bytes * (uint32_t)__popc(gmask));
@@ -237,7 +255,8 @@ action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict_
                         part = rest & ~t;  // the lowest 8 rows
                     }
                     rest &= ~part;
-                    dispatch_rows<G>(__popc(part), part, A, pitch, bj, wj, lastmask, lane, j, i0, cnt, hist, nbins);
+                    dispatch_rows<G, PHI>(__popc(part), part, A, pitch, bj, wj, lastmask, lane, j, i0, cnt, hist, nbins,
+                                     ctl);
                 }
             }
         }
@@ -255,10 +274,10 @@ action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict_
     }
 }
 
-template <int G>
+template <int G, bool PHI>
 int launch_g(const PopcPlan &p, const Arena &a, cudaStream_t st) {
     const size_t smem = 128 + (size_t)(G + 1) * p.pitch * sizeof(uint64_t);
-    auto kern = action_popc_kernel<G>;
+    auto kern = action_popc_kernel<G, PHI>;
     CSG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0, per_sm = 0;
     CSG_CUDA_TRY(cudaGetDevice(&dev));
@@ -294,6 +313,7 @@ PopcPlan popc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsi
     p.s_counters = s_counters;
     p.hist = hist;
     p.nbins = nbins;
+    for (int s = 0; s < n; ++s) p.phi = p.phi || sets[s].acc != nullptr;
     int64_t maxw = 0;
     for (int s = 0; s < n; ++s) maxw = std::max<int64_t>(maxw, (sets[s].N + 63) / 64 + 2);
     p.pitch = (int)((maxw + 1) & ~int64_t(1));
@@ -337,12 +357,21 @@ void popc_patch(const PopcPlan &p, Arena &a) {
 
 int popc_launch(const PopcPlan &p, const Arena &a, cudaStream_t st) {
     if (p.n_items == 0) return CSG_OK;
+    if (p.phi) {
+        switch (p.G) {
+            case 16: return launch_g<16, true>(p, a, st);
+            case 8: return launch_g<8, true>(p, a, st);
+            case 4: return launch_g<4, true>(p, a, st);
+            case 2: return launch_g<2, true>(p, a, st);
+            default: return launch_g<1, true>(p, a, st);
+        }
+    }
     switch (p.G) {
-        case 16: return launch_g<16>(p, a, st);
-        case 8: return launch_g<8>(p, a, st);
-        case 4: return launch_g<4>(p, a, st);
-        case 2: return launch_g<2>(p, a, st);
-        default: return launch_g<1>(p, a, st);
+        case 16: return launch_g<16, false>(p, a, st);
+        case 8: return launch_g<8, false>(p, a, st);
+        case 4: return launch_g<4, false>(p, a, st);
+        case 2: return launch_g<2, false>(p, a, st);
+        default: return launch_g<1, false>(p, a, st);
     }
 }
 

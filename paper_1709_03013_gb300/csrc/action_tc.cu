@@ -27,8 +27,9 @@
 //              (kind::f8f6f4, M=128, N=256, K=32, fp32 accumulate) and commits
 //              each stage back to the producer and each finished tile to the epilogue
 //   warps 2-5  epilogue: tcgen05.ld of the tile from TMEM (each thread owns one
-//              row), the S bits of the row select the related pairs, counters and
-//              the optional full histogram are updated; two TMEM accumulators let
+//              row), the S bits of the row select the related pairs, counters, the
+//              optional full histogram and the optional d'Alembertian sums
+//              (Eq. b_local) are updated; two TMEM accumulators let
 //              the epilogue of one tile overlap the product of the next.
 // Every wait is bounded (globaltimer); on expiry the kernel records an error in the
 // set's counters and winds down instead of spinning.
@@ -214,6 +215,46 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
           "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),            \
           "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])             \
         : "r"(addr))
+
+// Epilogue of one tile for the thread owning row i: reads the accumulator 16 columns
+// at a time and books the pairs (i, j) whose relation bit is set in w4.  PHI adds, for
+// pairs with m <= 2, c_m phi[i] to the d'Alembertian sums of element j (Eq. b_local);
+// it is a template argument so the plain epilogue carries none of that code.
+template <bool PHI>
+__device__ __forceinline__ unsigned long long epi_tile(uint32_t tbase, const uint64_t (&w4)[4], int64_t i,
+                                                       int64_t J0, unsigned long long &cR,
+                                                       unsigned long long &cM, unsigned long long &cW,
+                                                       unsigned long long *__restrict__ hist, long long nbins,
+                                                       double phi_i, double *__restrict__ acc_phi) {
+    unsigned long long packed = 0;  // N0..N3 of this tile, 16 bits each
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 16) {
+        uint32_t v[16];
+        TMEM_LD16(tbase + (uint32_t)c, v);
+        const uint64_t wsel = c < 64 ? w4[0] : (c < 128 ? w4[1] : (c < 192 ? w4[2] : w4[3]));
+        const uint32_t bits = (uint32_t)(wsel >> (c & 63)) & 0xFFFFu;
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (bits) {
+            // R and W of the chunk from bit counts: sum over set bits u of (J0+c+u - i - 1)
+            const unsigned pc = __popc(bits);
+            const unsigned su = __popc(bits & 0xAAAAu) + 2u * __popc(bits & 0xCCCCu) +
+                                4u * __popc(bits & 0xF0F0u) + 8u * __popc(bits & 0xFF00u);
+            cR += pc;
+            cW += (unsigned long long)pc * (unsigned long long)(J0 + c - i - 1) + su;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                if (bits >> u & 1u) {
+                    const uint32_t m = __float2uint_rn(__uint_as_float(v[u]));
+                    cM += m;
+                    if (m < 4u) packed += 1ull << (16u * m);
+                    if (hist != nullptr && (long long)m < nbins) atomicAdd(&hist[m], 1ull);
+                    if (PHI && m < 3u) atomicAdd(&acc_phi[J0 + c + u], (m == 1u ? -2.0 : 1.0) * phi_i);
+                }
+            }
+        }
+    }
+    return packed;
+}
 
 __device__ __forceinline__ void k_range(const TcTile &t, int64_t N, int &kt0, int &kt1) {
     // K runs from the tile's first row to its last column (or N)
@@ -416,40 +457,18 @@ action_tc_kernel(const TcArgs args) {
                         w4[u] &= ~((2ull << lo) - 1ull);
                 }
             }
+            const double phi_i = (S.acc != nullptr && i < N) ? S.phi[i] : 0.0;
             const bool ok = ptx::mbar_wait_bounded(&tfull[b], bph, kWaitNs);
             if (!__all_sync(0xffffffffu, ok)) {
                 bad = true;
                 break;
             }
             tc_fence_after();
-            unsigned long long packed = 0;  // N0..N3 of this tile, 16 bits each
-#pragma unroll 1
-            for (int c = 0; c < BN; c += 16) {
-                uint32_t v[16];
-                const uint32_t addr = tmem + b * BN + (uint32_t)c + ((uint32_t)(q * 32) << 16);
-                TMEM_LD16(addr, v);
-                const uint64_t wsel = c < 64 ? w4[0] : (c < 128 ? w4[1] : (c < 192 ? w4[2] : w4[3]));
-                const uint32_t bits = (uint32_t)(wsel >> (c & 63)) & 0xFFFFu;
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (bits) {
-                    // R and W of the chunk from bit counts: sum over set bits u of (J0+c+u - i - 1)
-                    const unsigned pc = __popc(bits);
-                    const unsigned su = __popc(bits & 0xAAAAu) + 2u * __popc(bits & 0xCCCCu) +
-                                        4u * __popc(bits & 0xF0F0u) + 8u * __popc(bits & 0xFF00u);
-                    cR += pc;
-                    cW += (unsigned long long)pc * (unsigned long long)(J0 + c - i - 1) + su;
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        if (bits >> u & 1u) {
-                            const uint32_t m = __float2uint_rn(__uint_as_float(v[u]));
-                            cM += m;
-                            if (m < 4u) packed += 1ull << (16u * m);
-                            if (args.hist != nullptr && (long long)m < args.nbins)
-                                atomicAdd(&args.hist[m], 1ull);
-                        }
-                    }
-                }
-            }
+            const uint32_t tbase = tmem + b * BN + ((uint32_t)(q * 32) << 16);
+            const unsigned long long packed =
+                S.acc != nullptr
+                    ? epi_tile<true>(tbase, w4, i, J0, cR, cM, cW, args.hist, args.nbins, phi_i, S.acc)
+                    : epi_tile<false>(tbase, w4, i, J0, cR, cM, cW, args.hist, args.nbins, 0.0, nullptr);
             c0 += packed & 0xFFFFull;
             c1 += (packed >> 16) & 0xFFFFull;
             c2 += (packed >> 32) & 0xFFFFull;
@@ -583,6 +602,8 @@ TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned
         D.row_lo = std::max<int64_t>(0, S.row_lo);
         D.row_hi = std::min<int64_t>(S.N, S.row_hi);
         D.counters = nullptr;
+        D.phi = S.phi;
+        D.acc = S.acc;
         D.kp = (S.N + BK - 1) / BK * BK;
         const int64_t ob = 2 * S.N * D.kp;
         if (s > cur.set_lo && chunk_bytes + ob > kChunkBytes) {

@@ -330,6 +330,31 @@ int csg_action_smeared(csg_ctx *ctx, csg_set *set, int method, double eps, doubl
     return run_smeared(set, method, eps, S_eps, out, (cudaStream_t)stream);
 }
 
+int csg_dalembertian(csg_ctx *ctx, csg_set *set, int method, const double *phi, double l, double *Bphi,
+                     csg_result *out, void *stream) {
+    if (!ctx || !set || set->ctx != ctx || !phi || !Bphi || (method != CSG_POPC && method != CSG_TC) ||
+        !(l > 0.0 && l < INFINITY)) {
+        set_error("csg_dalembertian: bad arguments (device phi and Bphi, 0 < l < inf, method POPC or TC)");
+        return CSG_E_INVAL;
+    }
+    if (set->d != 2) {
+        set_error("csg_dalembertian: the d'Alembertian of Eq. b_local is defined for 1+1 sets only");
+        return CSG_E_INVAL;
+    }
+    if (!set->linked) {
+        set_error("csg_dalembertian: set has no bitmap (call csg_link)");
+        return CSG_E_INVAL;
+    }
+    const uintptr_t a0 = (uintptr_t)phi, b0 = (uintptr_t)Bphi, len = (uintptr_t)set->N * sizeof(double);
+    if (a0 < b0 + len && b0 < a0 + len) {
+        set_error("csg_dalembertian: phi and Bphi overlap");
+        return CSG_E_INVAL;
+    }
+    CSG_CUDA_TRY(cudaSetDevice(ctx->device));
+    TimerScope ts(ctx);
+    return run_dalembertian(set, method, phi, l, Bphi, out, (cudaStream_t)stream);
+}
+
 int csg_action_batch(csg_ctx *ctx, csg_set *const *sets, int n, int method, csg_result *out,
                      void *stream) {
     if (!ctx || (n > 0 && (!sets || !out)) || n < 0 || (method != CSG_POPC && method != CSG_TC)) {

@@ -49,6 +49,10 @@ struct SetDesc {
     int64_t stride;        // words per row
     unsigned long long *counters;  // CNT_WORDS counters
     int64_t row_lo, row_hi;        // first elements i counted: [row_lo, row_hi)
+    // Optional d'Alembertian sums (Eq. b_local): for every related pair i < j with
+    // m(i,j) <= 2, acc[j] += c_m phi[i] with c = (1, -2, 1); null when not wanted.
+    const double *phi;
+    double *acc;
 };
 
 // A unit of action work: rows [i0, i0 + G) of set `set`.
@@ -122,6 +126,7 @@ void arena_free(Arena &a, cudaStream_t st);
 struct PopcPlan {
     std::vector<int> slot;  // counter slot of each set (empty: identity)
     int n_sets = 0, n_items = 0, G = 16, pitch = 0;
+    bool phi = false;  // some set wants d'Alembertian sums (selects the kernel variant)
     size_t t_sets = 0, t_items = 0, s_queue = 0, s_counters = 0;
     unsigned long long *hist = nullptr;
     int64_t nbins = 0;
@@ -138,6 +143,8 @@ struct TcSetDesc {
     unsigned long long *counters;
     uint8_t *U, *P;  // fp8 operands (strict future rows, strict past rows), N x kp bytes
     int64_t kp;      // operand row pitch (N rounded up to 128)
+    const double *phi;  // optional d'Alembertian sums, as in SetDesc
+    double *acc;
 };
 struct TcPlan {
     struct Chunk {

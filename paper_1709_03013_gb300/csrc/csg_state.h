@@ -47,6 +47,8 @@ int alloc_set(csg_ctx *ctx, int d, int64_t N, csg_set **out);
 void free_set(csg_set *s);
 
 // Action for n linked sets; writes n host results and synchronises st.
+int run_dalembertian(csg_set *set, int method, const double *phi, double l, double *Bphi, csg_result *out,
+                     cudaStream_t st);
 int run_actions(csg_set *const *sets, int n, int method, int64_t row_lo, int64_t row_hi,
                 unsigned long long *dev_hist, int64_t nbins, csg_result *out, cudaStream_t st);
 

@@ -98,7 +98,7 @@ struct Seq {
 
 int build_seq(Seq &q, csg_set *const *sets, int n, int method, int64_t row_lo, int64_t row_hi,
               unsigned long long *hist, int64_t nbins, const uint64_t *seed, const uint64_t *seq,
-              const Tune &tune = Tune()) {
+              const Tune &tune = Tune(), const double *phi = nullptr, double *acc = nullptr) {
     q.n = n;
     q.method = method;
     q.s_counters = q.a.reserve((size_t)n * CNT_WORDS * sizeof(unsigned long long));
@@ -125,6 +125,8 @@ int build_seq(Seq &q, csg_set *const *sets, int n, int method, int64_t row_lo, i
         desc[s].counters = nullptr;
         desc[s].row_lo = row_lo < 0 ? 0 : row_lo;
         desc[s].row_hi = row_hi < 0 ? sets[s]->N : std::min<int64_t>(row_hi, sets[s]->N);
+        desc[s].phi = phi;
+        desc[s].acc = acc;
         fin[s] = FinRow{sets[s]->d, 0, sets[s]->N, nullptr};
     }
     // split the sets between the two kernels (the tensor method sends small sets to the
@@ -190,10 +192,11 @@ int collect(const csg_result *out, int n) {
 }
 
 int run_seq(csg_set *const *sets, int n, int method, int64_t lo, int64_t hi, unsigned long long *hist,
-            int64_t nbins, const uint64_t *seed, const uint64_t *seq, csg_result *out, cudaStream_t st) {
+            int64_t nbins, const uint64_t *seed, const uint64_t *seq, csg_result *out, cudaStream_t st,
+            const double *phi = nullptr, double *acc = nullptr) {
     if (n <= 0) return CSG_OK;
     Seq q;
-    int rc = build_seq(q, sets, n, method, lo, hi, hist, nbins, seed, seq);
+    int rc = build_seq(q, sets, n, method, lo, hi, hist, nbins, seed, seq, Tune(), phi, acc);
     if (rc != CSG_OK) return rc;
     rc = arena_alloc(q.a, st);
     if (rc != CSG_OK) return rc;
@@ -284,6 +287,39 @@ int run_smeared(csg_set *set, int method, double eps, double *S_eps, csg_result 
     }
     if (rc == CSG_OK && out) *out = res;
     return rc;
+}
+
+// ------------------------------------------------------------------ d'Alembertian
+
+namespace {
+
+// B phi(x) = (2 / l^2) (-phi(x) + 2 A(x)), A(x) = sum over y in L_1, L_2, L_3 of x of
+// (1, -2, 1) phi(y), accumulated in B by the interval-count kernels (Eq. b_local).
+__global__ void dalembert_kernel(const double *__restrict__ phi, double *__restrict__ B, int64_t N,
+                                 double scale) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < N; x += (int64_t)gridDim.x * blockDim.x)
+        B[x] = scale * (2.0 * B[x] - phi[x]);
+}
+
+}  // namespace
+
+int run_dalembertian(csg_set *set, int method, const double *phi, double l, double *Bphi, csg_result *out,
+                     cudaStream_t st) {
+    const int64_t N = set->N;
+    CSG_CUDA_TRY(cudaMemsetAsync(Bphi, 0, (size_t)N * sizeof(double), st));
+    csg_result res;
+    csg_set *one[1] = {set};
+    int rc = run_seq(one, 1, method, -1, -1, nullptr, 0, nullptr, nullptr, &res, st, phi, Bphi);  // synchronises
+    if (rc != CSG_OK) return rc;
+    const double scale = 2.0 / (l * l);
+    const int blocks = (int)std::min<int64_t>((N + 255) / 256, 4096);
+    stage_begin(CSG_STAGE_FINALIZE, st);
+    dalembert_kernel<<<blocks, 256, 0, st>>>(phi, Bphi, N, scale);
+    stage_end(CSG_STAGE_FINALIZE, st);
+    CSG_CUDA_TRY(cudaGetLastError());
+    CSG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (out) *out = res;
+    return CSG_OK;
 }
 
 // ------------------------------------------------------------------ batch graphs

@@ -282,3 +282,100 @@ def test_desitter_slab(ctx, csg, N):
         S_ref = oracle.smeared(N, want["hist"], 2 ** -6)
         assert abs(S - S_ref) <= 1e-12 * max(2 * 2 ** -6 * N + 8 * 2 ** -12 * want["R"], 1.0)
     s.free()
+
+
+# ------------------------------------------------------------ d'Alembertian (Eq. b_local)
+
+def _dalembert_tol(phi, L, l):
+    # Both sides sum at most n_x = |L1|+|L2|+|L3| terms c_m phi(y) in some order, then form
+    # (2/l^2)(2A - phi): each is within gamma_{n_x + 3} (2/l^2) T(x) of the exact value, with
+    # T(x) = |phi(x)| + 2 sum |c_m phi(y)| <= |phi(x)| + 2 (|L1| + 2|L2| + |L3|) max|phi|.
+    n = L.sum(axis=1)
+    T = np.abs(phi) + 2.0 * (L[:, 0] + 2 * L[:, 1] + L[:, 2]) * np.abs(phi).max(initial=0.0)
+    return 2.0 * (n + 4) * 2.0 ** -53 * (2.0 / l ** 2) * T * 1.01
+
+
+@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("N", [1, 2, 3, 700, 3001])
+def test_dalembertian_matches_oracle(ctx, csg, N, method):
+    import torch
+    s = ctx.sprinkle(2, N, 21, 1).link()
+    rel = oracle.link(2, oracle.sprinkle_sorted(2, N, 21, 1))
+    phi = np.random.default_rng(N).uniform(-1.0, 1.0, size=N)
+    l = 0.3
+    want, L = oracle.dalembertian(rel, phi, l)
+    phi_d = torch.from_numpy(phi).cuda()
+    B_d = torch.full((N,), float("nan"), dtype=torch.float64, device="cuda")  # every entry is written
+    res = s.dalembertian(phi_d.data_ptr(), B_d.data_ptr(), l, method)
+    got = B_d.cpu().numpy()
+    assert np.all(np.abs(got - want) <= _dalembert_tol(phi, L, l))
+    _check_result(res, oracle.action(rel), 2, N)
+    # phi = 1, l = 1: integer arithmetic throughout, so the values are exact and sum to -S_BD
+    one = torch.ones(N, dtype=torch.float64, device="cuda")
+    res = s.dalembertian(one.data_ptr(), B_d.data_ptr(), 1.0, method)
+    want1, _ = oracle.dalembertian(rel, np.ones(N), 1.0)
+    got1 = B_d.cpu().numpy()
+    assert np.array_equal(got1, want1)
+    assert float(got1.sum()) == -res.S
+    s.free()
+
+
+@pytest.mark.parametrize("name", ["diamond4.txt", "npos6.txt"])
+def test_dalembertian_golden_on_gpu(ctx, csg, golden, name):
+    import torch
+    g = golden(name)
+    rel = inputs.rel_from_edges(g["N"], g["rel"])
+    dev = _dev_words(inputs.pack_rows(rel, 16))
+    s = ctx.set_from_bitmap(2, g["N"], dev.data_ptr(), 16)
+    phi = torch.tensor(g["phi"], dtype=torch.float64, device="cuda")
+    B = torch.empty_like(phi)
+    for method in (csg.POPC, csg.TC):
+        s.dalembertian(phi.data_ptr(), B.data_ptr(), 1.0, method)
+        assert B.cpu().tolist() == g["Bphi"]
+    s.free()
+
+
+def test_dalembertian_desitter_and_bitmap_orders(ctx, csg):
+    import torch
+    # a de Sitter slab (Sec. 5.1) and caller-made orders through the bitmap entry point
+    s = ctx.sprinkle_desitter(2500, 0.5, 3, 0).link()
+    cases = [(s, oracle.link(oracle.DS2, s.coords()), None)]
+    for r in (inputs.chain_rel(300), inputs.layered_order_rel(900, 5), inputs.random_upper_rel(600, 0.2, 6)):
+        N = r.shape[0]
+        stride = (N + 63) // 64 + 1  # a caller stride unlike the library's
+        dev = _dev_words(inputs.pack_rows(r, stride))
+        cases.append((ctx.set_from_bitmap(2, N, dev.data_ptr(), stride), r, dev))
+    for st, r, _keep in cases:
+        N = r.shape[0]
+        phi = np.random.default_rng(N).normal(size=N)
+        want, L = oracle.dalembertian(r, phi, 0.5)
+        phi_d = torch.from_numpy(phi).cuda()
+        B = torch.empty_like(phi_d)
+        for method in (csg.POPC, csg.TC):
+            st.dalembertian(phi_d.data_ptr(), B.data_ptr(), 0.5, method)
+            assert np.all(np.abs(B.cpu().numpy() - want) <= _dalembert_tol(phi, L, 0.5))
+        st.free()
+
+
+def test_dalembertian_rejects_bad_arguments(ctx, csg):
+    import torch
+    s4 = ctx.sprinkle(4, 100, 1, 0).link()
+    s2 = ctx.sprinkle(2, 100, 1, 0)
+    buf = torch.zeros(300, dtype=torch.float64, device="cuda")
+    p, q = buf.data_ptr(), buf.data_ptr() + 100 * 8
+    with pytest.raises(csg.CsgError) as e:
+        s4.dalembertian(p, q)                     # 3+1: not given by the paper
+    assert e.value.code == csg.E_INVAL
+    with pytest.raises(csg.CsgError):
+        s2.dalembertian(p, q)                     # not linked yet
+    s2.link()
+    for l in (0.0, -1.0, float("inf"), float("nan")):
+        with pytest.raises(csg.CsgError):
+            s2.dalembertian(p, q, l)
+    with pytest.raises(csg.CsgError):
+        s2.dalembertian(p, p + 50 * 8)            # phi and Bphi overlap
+    with pytest.raises(csg.CsgError):
+        s2.dalembertian(0, q)
+    s2.dalembertian(p, q, 1.0, csg.TC)            # still usable afterwards
+    s4.free()
+    s2.free()
