@@ -313,6 +313,45 @@ def bench_desitter(args):
     return 0
 
 
+def bench_dalembertian(args):
+    """Cost of the discrete d'Alembertian (Eq. b_local) beside the plain interval counts on
+    the d=2 N=131072 set (seed 2): the layer sums ride on the counting pass, so the extra
+    time is the atomics of the pairs with m <= 2 and one elementwise pass."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1709_03013_gb300 import csg
+    d, N, seed = 2, 131072, 2
+    out = {"experiment": "discrete d'Alembertian (Eq. b_local) beside the action",
+           "workload": f"d={d} N={N} seed {seed}", "phi": "t^2 - x^2 at the sprinkled coordinates", "l": 1.0}
+    with csg.Context(0) as ctx:
+        s = ctx.sprinkle(d, N, seed, 0).link()
+        c = torch.from_numpy(s.coords()).cuda()
+        phi = (c[0] * c[0] - c[1] * c[1]).contiguous()
+        B = torch.empty_like(phi)
+        stream = torch.cuda.current_stream()
+        for name, method, reps in (("tc", csg.TC, 3), ("popc", csg.POPC, 1)):
+            times = {}
+            for label, fn in (("action", lambda: s.action(method)),
+                              ("action+dalembertian", lambda: s.dalembertian(phi.data_ptr(), B.data_ptr(), 1.0, method))):
+                fn()  # warm-up
+                ms = []
+                for _ in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fn()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                times[label] = min(ms)
+            res = s.action(method)
+            out[name] = {"ms": times, "L123_pairs": [int(v) for v in res.Nk[:3]],
+                         "overhead": times["action+dalembertian"] / times["action"] - 1.0}
+        s.free()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def bench_serve(args, emit=True):
     """Requests arrive as a Poisson stream (d in {2,4} 50/50, N log-uniform in
     [1024, 65536], seed 4) and go through the continuous-batching service; latency is
@@ -413,7 +452,7 @@ def main():
     ap.add_argument("--d", type=int, default=4)
     ap.add_argument("--n", type=int, default=40000)
     ap.add_argument("--reps", type=int, default=2)
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "desitter"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "desitter", "dalembertian"],
                     help="single: the d=4 N=65536 set; batch: 4096 mixed diamonds, plain vs batched; "
                          "serve: Poisson request stream through the service, p50/p99 latency")
     ap.add_argument("--n-sets", type=int, default=4096)
@@ -431,6 +470,9 @@ def main():
         return 0
     if args.workload == "desitter":
         bench_desitter(args)
+        return 0
+    if args.workload == "dalembertian":
+        bench_dalembertian(args)
         return 0
     if args.warmup < 3:
         args.warmup = 3

@@ -16,8 +16,8 @@
 // (coalesced) and ANDs each with the staged row of every related i in the mask.
 // One read of a word of row j thus serves all related rows of the group.
 //
-// The lanes' partial counts of a pair are summed with warp shuffles; the pair's m
-// goes into per-lane counters (N_0..N_3, R, sum m, W) flushed with 64-bit atomics,
+// The lanes' partial counts of a pair are summed with one warp reduction (redux); the
+// pair's m goes into per-warp counters (N_0..N_3, R, sum m, W) flushed with 64-bit atomics,
 // optionally into a full histogram in global memory and, for pairs with m <= 2, into
 // the per-element sums of the discrete d'Alembertian (Eq. b_local).  Work items come from an
 // atomic queue (persistent CTAs), in ascending i0, which is roughly longest first.
@@ -45,8 +45,10 @@ struct Smem {
     double *acc;
 };
 
+// Per-warp totals of one work item.  Every lane holds the same R, M and W; lane k < 4
+// holds N_k in nk (the lane whose index equals m counts the pair).
 struct Counters {
-    unsigned long long n0 = 0, n1 = 0, n2 = 0, n3 = 0, R = 0, M = 0, W = 0;
+    unsigned long long nk = 0, R = 0, M = 0, W = 0;
 };
 
 // The cnt <= K group rows related to j (the set bits of mask) against row j: each lane
@@ -95,31 +97,22 @@ __device__ __forceinline__ void sweep_rows(uint32_t mask, int cnt, int zoff, con
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         if (k >= cnt) break;
-        uint32_t v = acc[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) {
-            c.n0 += v == 0u;
-            c.n1 += v == 1u;
-            c.n2 += v == 2u;
-            c.n3 += v == 3u;
-            c.M += v;
-            if (hist != nullptr && (long long)v < nbins) atomicAdd(&hist[v], 1ull);
-            // Eq. b_local: i = i0 + r is in L_{v+1} of j, r the k-th set bit of mask
-            if (PHI && v < 3u) {
-                double *acc_phi = ctl->acc;
-                uint32_t mm = mask;  // k < cnt = popc(mask), so mm keeps a set bit
-                for (int t = 0; t < k; ++t) mm &= mm - 1;
-                const int r = __ffs(mm) - 1;
-                atomicAdd(&acc_phi[j], (v == 1u ? -2.0 : 1.0) * ctl->phi[i0 + r]);
-            }
+        const uint32_t v = __reduce_add_sync(0xffffffffu, acc[k]);  // m of the pair, on every lane
+        c.nk += (uint32_t)lane == v;
+        c.M += v;
+        if (hist != nullptr && lane == 0 && (long long)v < nbins) atomicAdd(&hist[v], 1ull);
+        // Eq. b_local: i = i0 + r is in L_{v+1} of j, r the k-th set bit of mask
+        if (PHI && lane == 0 && v < 3u) {
+            double *acc_phi = ctl->acc;
+            uint32_t mm = mask;  // k < cnt = popc(mask), so mm keeps a set bit
+            for (int t = 0; t < k; ++t) mm &= mm - 1;
+            const int r = __ffs(mm) - 1;
+            atomicAdd(&acc_phi[j], (v == 1u ? -2.0 : 1.0) * ctl->phi[i0 + r]);
         }
     }
-    if (lane == 0) {
-        c.R += (unsigned long long)cnt;
-        // sum over the cnt rows r of (j - (i0 + r) - 1)
-        c.W += (unsigned long long)cnt * (unsigned long long)(j - i0 - 1) - (unsigned long long)rsum;
-    }
+    c.R += (unsigned long long)cnt;
+    // sum over the cnt rows r of (j - (i0 + r) - 1)
+    c.W += (unsigned long long)cnt * (unsigned long long)(j - i0 - 1) - (unsigned long long)rsum;
 }
 
 template <int G, bool PHI>
@@ -260,15 +253,14 @@ action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict_
                 }
             }
         }
-        if (lane == 0 && cnt.R != 0) {
+        if (cnt.R != 0) {
             unsigned long long *g = S.counters;
-            if (cnt.n0) atomicAdd(&g[CNT_N0], cnt.n0);
-            if (cnt.n1) atomicAdd(&g[CNT_N1], cnt.n1);
-            if (cnt.n2) atomicAdd(&g[CNT_N2], cnt.n2);
-            if (cnt.n3) atomicAdd(&g[CNT_N3], cnt.n3);
-            atomicAdd(&g[CNT_R], cnt.R);
-            atomicAdd(&g[CNT_SUM_M], cnt.M);
-            atomicAdd(&g[CNT_W], cnt.W);
+            if (lane < 4 && cnt.nk) atomicAdd(&g[CNT_N0 + lane], cnt.nk);
+            if (lane == 0) {
+                atomicAdd(&g[CNT_R], cnt.R);
+                atomicAdd(&g[CNT_SUM_M], cnt.M);
+                atomicAdd(&g[CNT_W], cnt.W);
+            }
         }
         __syncthreads();  // the staged rows are reused by the next item
     }
