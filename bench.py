@@ -39,6 +39,8 @@ sys.path.insert(0, ROOT)
 METRIC = "related-pair interval counts/s + p99 latency, served vs plain, bit-exact N_k"
 UNIT = "pairs/s"
 WORKLOAD = dict(d=4, N=65536, seed=1)
+# interval-count methods of the C ABI (CSG_POPC, CSG_TC, CSG_TC_FP8, CSG_TC_FP4)
+METHODS = {"popc": 0, "tc": 1, "tc8": 2, "tc4": 3}
 WORKLOAD_NAME = "d=4 flat causal diamond, N=65536, seed 1 (sprinkle+sort+link+action)"
 
 # Popcount peak of the integer pipe: 32 32-bit POPC per SM per clock (a loop of
@@ -212,7 +214,7 @@ def profile_action(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_1709_03013_gb300 import csg
-    method = csg.POPC if args.method == "popc" else csg.TC
+    method = METHODS[args.method]
     with csg.Context(0) as ctx:
         s = ctx.sprinkle(args.d, args.n, 1, 0).link()
         for r in range(args.reps):
@@ -231,7 +233,7 @@ def bench_batch(args, emit=True):
     import __graft_entry__
     __graft_entry__.build()
     from paper_1709_03013_gb300 import csg, inputs
-    method = csg.POPC if args.method == "popc" else csg.TC
+    method = METHODS[args.method]
     specs = [(s.d, s.N, s.seed, s.seq) for s in inputs.batch_workload(n_sets=args.n_sets)]
     ctx = csg.Context(0)
     stream = torch.cuda.current_stream()
@@ -269,7 +271,7 @@ def bench_batch(args, emit=True):
     line = {"metric": METRIC, "value": R / (times["batched"] / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": times["batched"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "fp8" if method == csg.TC else "u64", "data": "synthetic",
+            "dtype": {0: "u64", 3: "fp4"}.get(method, "fp8"), "data": "synthetic",
             "config": {"workload": f"batch: {len(specs)} flat diamonds, d alternating 2/4, N log-uniform "
                                    f"in [256, 8192], seed 3 (sprinkle+sort+link+action per set)",
                        "method": args.method, "sets": len(specs), "sum_R": R, "sum_W": W},
@@ -443,7 +445,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--method", default="tc", choices=["popc", "tc"])
+    ap.add_argument("--method", default="tc4", choices=list(METHODS),
+                    help="popc, or the tensor form: tc (library default format), tc8 (fp8), tc4 (fp4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the batch and serve summaries of the default line")
@@ -494,7 +497,8 @@ def main():
     __graft_entry__.build()
     from paper_1709_03013_gb300 import csg
 
-    method = csg.POPC if args.method == "popc" else csg.TC
+    method = METHODS[args.method]
+    is_tc = method != csg.POPC
     d, N, seed = WORKLOAD["d"], WORKLOAD["N"], WORKLOAD["seed"]
     seq = rank  # replicas: each rank runs its own independent set
     ctx = csg.Context(local)
@@ -539,7 +543,7 @@ def main():
     act_ms = stage_avg["action"]
 
     # ---- the other method's action kernel on the same set (reported beside the main one)
-    other = csg.TC if method == csg.POPC else csg.POPC
+    other = csg.TC_FP8 if method == csg.POPC else csg.POPC
     s = ctx.sprinkle(d, N, seed, seq).link()
     s.action(other)
     ro = s.action(other)
@@ -575,35 +579,40 @@ def main():
     clocks = clk.summary()
     sm_max = (clocks or {}).get("sm_max_mhz") or pk.get("sm_max_mhz") or 2070.0
     popc_peak = SMS * POPC_PER_SM_CLK * 32 * sm_max * 1e6          # bit-ops/s
-    fp8_peak = 2.0 * pk.get("bf16_tflops", 1900.0)                  # TFLOP/s, fp8 = 2 x bf16
+    fp4 = method == csg.TC_FP4
+    # the contraction's own dtype: measured bf16 dense burst x the nominal ratio (fp8 2, fp4 6)
+    tc_peak = (6.0 if fp4 else 2.0) * pk.get("bf16_tflops", 1900.0)
     tc_flops = 2.0 * math.comb(N, 3)                                # triangle-restricted contraction
     popc_ms = act_ms if method == csg.POPC else other_ms
-    tc_ms = act_ms if method == csg.TC else other_ms
+    tc_ms = act_ms if is_tc else other_ms
     popc_roof = {"bound": "alu", "achieved": res.W / (popc_ms / 1e3), "peak": popc_peak,
                  "unit": "bit-ops/s", "frac": res.W / (popc_ms / 1e3) / popc_peak, "traffic": None,
                  "kernel_ms": popc_ms,
                  "peak_basis": f"{SMS} SMs x {POPC_PER_SM_CLK} POPC/clk x 32 bits x {sm_max:.0f} MHz"}
     tc_ach = tc_flops / (tc_ms / 1e3) / 1e12
-    tc_roof = {"bound": "tensor", "achieved": tc_ach, "peak": fp8_peak, "unit": "TFLOP/s",
-               "frac": tc_ach / fp8_peak,
-               "traffic": recorded_traffic("action_tc_kernel", f"d={d} N={N} seed {seed}"),
+    tc_roof = {"bound": "tensor", "achieved": tc_ach, "peak": tc_peak, "unit": "TFLOP/s",
+               "frac": tc_ach / tc_peak,
+               "traffic": recorded_traffic(f"action_tc_kernel<{1 if fp4 else 0}>", f"d={d} N={N} seed {seed}"),
                "kernel_ms": tc_ms,
-               "peak_basis": "fp8 = 2 x measured bf16 dense burst (MEASURED_PEAKS.json), of measured"}
+               "peak_basis": (f"{'fp4 = 6' if fp4 else 'fp8 = 2'} x measured bf16 dense burst "
+                              "(MEASURED_PEAKS.json; nominal dense ratio), of measured")}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "fp8" if method == csg.TC else "u64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": ("fp4" if fp4 else "fp8") if is_tc else "u64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "d": d, "N": N, "seed": seed, "method": args.method,
-                   "l2": "inputs larger than L2 (512 MiB bitmap, 8 GiB fp8 operands per step)",
+                   "l2": ("inputs larger than L2 (512 MiB bitmap, "
+                          f"{'4 GiB fp4' if fp4 else '8 GiB fp8'} operands per step)"),
                    "parallelism": "replicas" if world > 1 else "single"},
-        "gpu_launches": launches_per_step(N, method == csg.TC) * args.steps,
+        "gpu_launches": launches_per_step(N, is_tc) * args.steps,
         "result": {"R": res.R, "Nk": list(res.Nk), "sum_m": res.sum_m, "W": res.W, "combo": res.combo,
                    "S": res.S},
         "stage_ms": stage_avg,
         "bitops_per_s": res.W / (act_ms / 1e3),
-        "roofline": tc_roof if method == csg.TC else popc_roof,
-        "roofline_other_method": popc_roof if method == csg.TC else tc_roof,
+        "roofline": tc_roof if is_tc else popc_roof,
+        "roofline_other_method": popc_roof if is_tc else tc_roof,
         "e2e": {"value": e_pairs / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(host_np.nbytes),
                 "d2h_bytes_per_step": 88},
     }

@@ -56,7 +56,9 @@ extern "C" {
 
 /* Methods for the interval counts (csg_action, csg_action_batch). */
 #define CSG_POPC 0 /* AND + popcount of packed row words (Alg. 5 restated for the GPU) */
-#define CSG_TC 1   /* the same counts as a masked 0/1 matrix product on tensor cores */
+#define CSG_TC 1   /* the same counts as a masked 0/1 matrix product on tensor cores (currently CSG_TC_FP4) */
+#define CSG_TC_FP8 2 /* tensor cores, 0/1 operands in fp8 e4m3 (kind::f8f6f4), two TMEM accumulators */
+#define CSG_TC_FP4 3 /* tensor cores, 0/1 operands in packed fp4 e2m1 with unit block scales (kind::mxf4) */
 
 /* Largest N a set may have. */
 #define CSG_MAX_N (1 << 18)

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libcsg.so")
 OK, PENDING = 0, 1
 E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY, E_REJECT, E_NOTFOUND, E_CANCELLED = range(-1, -9, -1)
 POPC, TC = 0, 1
+TC_FP8, TC_FP4 = 2, 3  # explicit operand formats of the tensor method
 MAX_N = 1 << 18
 
 

@@ -7,30 +7,35 @@
 // a dense contraction, so it runs on the tensor cores; only the entries with
 // S[i][j] = 1, i < j, are histogrammed (Alg. 5 counts related pairs only).
 //
-// Exactness: the operands are 0 and 1 in fp8 e4m3 (0x00, 0x38); products are exact
-// and the fp32 accumulator holds integers up to 2^24 exactly, far above the largest
-// interval (N - 2 <= 2^18).  The result is converted back to an integer before it is
-// used, so the counts are bit-exact.
+// Exactness: the operands are 0 and 1, either in fp8 e4m3 (0x00, 0x38; kind::f8f6f4) or
+// in packed fp4 e2m1 (nibbles 0x0, 0x2; kind::mxf4 with every block scale factor 1.0);
+// products are exact and the fp32 accumulator holds integers up to 2^24 exactly, far
+// above the largest interval (N - 2 <= 2^18).  The result is converted back to an
+// integer before it is used, so the counts are bit-exact in either format.
 //
-// Pass 1 (expand): one thread per packed word writes the 64 fp8 bytes of U and of P
-// it covers; only the column ranges the product reads are written.
+// Pass 1 (expand): one thread per packed word writes the operand bytes of U and of P it
+// covers (64 fp8 bytes or 32 fp4 bytes each); only the column ranges the product reads
+// are written.
 // Pass 2 (product): persistent CTAs, one per SM, take output tiles (128 rows i x 256
 // columns j, upper triangle only, K from the first row of the tile to the last
 // column) from a global work queue (an atomic counter over a tile list ordered set by
 // set, longest first, block-rasterised); claiming tiles in list order keeps the CTAs
 // on the same set's operands, which then stay in L2.
 // Warp roles per CTA:
-//   warp 0     claims tiles and passes their indices to warps 1-5 through a 4-slot
-//              shared-memory ring; TMA producer: 128-byte-swizzled K tiles of U
-//              (128 x 128) and P (256 x 128) into a 4-stage ring (mbarrier complete_tx)
-//   warp 1     allocates 512 TMEM columns; one lane issues tcgen05.mma
-//              (kind::f8f6f4, M=128, N=256, K=32, fp32 accumulate) and commits
-//              each stage back to the producer and each finished tile to the epilogue
-//   warps 2-5  epilogue: tcgen05.ld of the tile from TMEM (each thread owns one
-//              row), the S bits of the row select the related pairs, counters, the
-//              optional full histogram and the optional d'Alembertian sums
-//              (Eq. b_local) are updated; two TMEM accumulators let
-//              the epilogue of one tile overlap the product of the next.
+//   warp 0     claims tiles and passes their indices to warps 1-9 through a 4-slot
+//              shared-memory ring; TMA producer: 128-byte-swizzled K stages of U
+//              (128 rows x 128 bytes) and P (256 x 128 bytes) into a 4-stage ring
+//   warp 1     allocates 512 TMEM columns; one lane issues the MMAs (M=128, N=256,
+//              32 bytes of K each: 32 fp8 or 64 fp4 elements) and commits each stage
+//              back to the producer and each finished tile to the epilogue
+//   warps 2-9  epilogue: tcgen05.ld of the tile from TMEM (each thread owns one row and
+//              half of the columns), the S bits of the row select the related pairs,
+//              counters, the optional full histogram and the optional d'Alembertian
+//              sums (Eq. b_local) are updated.  The fp8 form keeps two accumulators
+//              (columns 0 and 256) so the epilogue of one tile overlaps the product of
+//              the next; the fp4 form keeps one accumulator at column 0 and its scale
+//              factors in columns 256..511, and releases the accumulator as soon as the
+//              last columns are in registers.
 // Every wait is bounded (globaltimer); on expiry the kernel records an error in the
 // set's counters and winds down instead of spinning.
 #include <cuda.h>
@@ -53,12 +58,12 @@ namespace {
 
 constexpr int BM = 128;          // rows i per tile
 constexpr int BN = 256;          // columns j per tile
-constexpr int BK = 128;          // K elements (= bytes) per stage
+constexpr int BKB = 128;         // bytes of each operand row per stage (one 128-byte swizzle row)
 constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BK;
-constexpr int B_BYTES = BN * BK;
+constexpr int A_BYTES = BM * BKB;
+constexpr int B_BYTES = BN * BKB;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int EPI_WARPS = 4;
+constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, one for each half of the tile's columns
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
 constexpr uint32_t TMEM_COLS = 2 * BN;
 constexpr uint64_t kWaitNs = 4000000000ull;
@@ -103,6 +108,22 @@ __device__ __forceinline__ uint32_t nibble_fp8(uint32_t nib) {
     return ((nib * 0x00204081u) & 0x01010101u) * (uint32_t)kOne;
 }
 
+// Eight relation bits -> four bytes of packed fp4 e2m1 (1.0 = 0x2): byte k holds elements
+// 2k (low nibble) and 2k+1 (high nibble).  Each multiply moves the even (odd) bits to bit
+// 8k+1 (8k+5) of byte k; the other partial products land on bits the mask drops.
+__device__ __forceinline__ uint32_t octet_fp4(uint32_t o) {
+    return (((o & 0x55u) * 0x00082082u) & 0x02020202u) | (((o & 0xAAu) * 0x00410410u) & 0x20202020u);
+}
+
+__device__ __forceinline__ void put64_fp4(uint8_t *dst, uint64_t m) {
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    const uint32_t lo = (uint32_t)m, hi = (uint32_t)(m >> 32);
+    d4[0] = make_uint4(octet_fp4(lo & 0xFFu), octet_fp4((lo >> 8) & 0xFFu), octet_fp4((lo >> 16) & 0xFFu),
+                       octet_fp4(lo >> 24));
+    d4[1] = make_uint4(octet_fp4(hi & 0xFFu), octet_fp4((hi >> 8) & 0xFFu), octet_fp4((hi >> 16) & 0xFFu),
+                       octet_fp4(hi >> 24));
+}
+
 __device__ __forceinline__ void put64(uint8_t *dst, uint64_t m) {
     uint4 *d4 = reinterpret_cast<uint4 *>(dst);
     const uint32_t lo = (uint32_t)m, hi = (uint32_t)(m >> 32);
@@ -114,27 +135,34 @@ __device__ __forceinline__ void put64(uint8_t *dst, uint64_t m) {
     }
 }
 
-// One thread per packed word of the sets [set_lo, set_lo + nset): writes the 64 fp8
-// bytes of U and of P the word covers, where the product reads them.
+// One thread per packed word of the sets [set_lo, set_lo + nset): writes the operand
+// bytes of U and of P the word covers (64 fp8 bytes or 32 packed fp4 bytes each), where
+// the product reads them.  FMT 0: fp8 e4m3, 128 elements per stage; FMT 1: fp4 e2m1, 256.
+template <int FMT>
 __global__ void expand_kernel(const TcSetDesc *__restrict__ sets, const int64_t *__restrict__ wstarts,
                               int set_lo, int nset, int64_t total) {
+    constexpr int64_t KSTAGE = FMT ? 256 : 128;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
          g += (int64_t)gridDim.x * blockDim.x) {
         const int ls = find_set(wstarts, nset, g);
         const TcSetDesc S = sets[set_lo + ls];
-        const int64_t wpr = S.kp / 64;
+        const int64_t wpr = (FMT ? 2 * S.kp : S.kp) / 64;  // words per operand row
         const int64_t gl = g - wstarts[ls];
         const int64_t i = gl / wpr, w = gl - i * wpr;
         const int64_t k0 = w * 64;
         const uint64_t word = S.rows[i * S.stride + w];
-        // U row i is read from column BM*floor(i/BM); P row i up to column BN*(floor(i/BN)+1)
-        if (k0 + 64 > (i / BM) * BM) {
+        // U row i is read from the stage holding column BM*floor(i/BM); P row i up to
+        // column BN*(floor(i/BN)+1)
+        if (k0 + 64 > (i / BM) * BM / KSTAGE * KSTAGE) {
             uint64_t m = word;
             if (k0 + 63 <= i)
                 m = 0;
             else if (k0 <= i)
                 m &= ~((2ull << (i - k0)) - 1ull);  // keep k > i
-            put64(S.U + i * S.kp + k0, m);
+            if (FMT)
+                put64_fp4(S.U + i * S.kp + k0 / 2, m);
+            else
+                put64(S.U + i * S.kp + k0, m);
         }
         if (k0 < (i / BN + 1) * BN) {
             uint64_t m = word;
@@ -142,7 +170,10 @@ __global__ void expand_kernel(const TcSetDesc *__restrict__ sets, const int64_t 
                 m = 0;
             else if (k0 + 63 >= i)
                 m &= (1ull << (i - k0)) - 1ull;  // keep k < i
-            put64(S.P + i * S.kp + k0, m);
+            if (FMT)
+                put64_fp4(S.P + i * S.kp + k0 / 2, m);
+            else
+                put64(S.P + i * S.kp + k0, m);
         }
     }
 }
@@ -162,6 +193,13 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
 // kind::f8f6f4, A = B = e4m3, D = f32, K-major A and B, M = 128, N = 256
 constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
                             ((uint32_t)(BM >> 4) << 24);
+// kind::mxf4 with block scaling: A = B = e2m1 (1), scale factors ue8m0 (bit 23), scale
+// factor ids 0, D = f32, K-major A and B, M = 128, N = 256
+constexpr uint32_t kIdescF4 = (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | (1u << 23) |
+                              ((uint32_t)(BM >> 4) << 24);
+// TMEM columns of the fp4 form: accumulator 0..255, scale factors of A at 256 and of B at
+// 384 (every scale factor is 1.0, so columns 256..511 are filled with the byte 0x7F)
+constexpr uint32_t kSfA = 256, kSfB = 384;
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
                                             uint64_t *bar) {
@@ -177,6 +215,16 @@ __device__ __forceinline__ void mma_f8(uint32_t dtmem, uint64_t ad, uint64_t bd,
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
         "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_f4(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t sfa, uint32_t sfb,
+                                       uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %6, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n}\n" ::"r"(
+            dtmem),
+        "l"(ad), "l"(bd), "r"(kIdescF4), "r"(sfa), "r"(sfb), "r"(acc)
         : "memory");
 }
 
@@ -216,56 +264,86 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
           "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])             \
         : "r"(addr))
 
-// Epilogue of one tile for the thread owning row i: reads the accumulator 16 columns
-// at a time and books the pairs (i, j) whose relation bit is set in w4.  PHI adds, for
-// pairs with m <= 2, c_m phi[i] to the d'Alembertian sums of element j (Eq. b_local);
-// it is a template argument so the plain epilogue carries none of that code.
+// Books the pairs (i, j) of one 16-column chunk whose relation bits are set in `bits`
+// (column u of the chunk is element jbase + u).  PHI adds, for pairs with m <= 2, c_m phi[i]
+// to the d'Alembertian sums of element j (Eq. b_local).
+template <bool PHI>
+__device__ __forceinline__ void book16(const uint32_t (&v)[16], uint32_t bits, int64_t jbase, int64_t i,
+                                       unsigned long long &packed, unsigned long long &cR,
+                                       unsigned long long &cM, unsigned long long &cW,
+                                       unsigned long long *__restrict__ hist, long long nbins, double phi_i,
+                                       double *__restrict__ acc_phi) {
+    if (!bits) return;
+    // R and W of the chunk from bit counts: sum over set bits u of (jbase + u - i - 1)
+    const unsigned pc = __popc(bits);
+    const unsigned su = __popc(bits & 0xAAAAu) + 2u * __popc(bits & 0xCCCCu) + 4u * __popc(bits & 0xF0F0u) +
+                        8u * __popc(bits & 0xFF00u);
+    cR += pc;
+    cW += (unsigned long long)pc * (unsigned long long)(jbase - i - 1) + su;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        if (bits >> u & 1u) {
+            const uint32_t m = __float2uint_rn(__uint_as_float(v[u]));
+            cM += m;
+            if (m < 4u) packed += 1ull << (16u * m);
+            if (hist != nullptr && (long long)m < nbins) atomicAdd(&hist[m], 1ull);
+            if (PHI && m < 3u) atomicAdd(&acc_phi[jbase + u], (m == 1u ? -2.0 : 1.0) * phi_i);
+        }
+    }
+}
+
+// Epilogue of one tile for the thread owning row i and columns [cb, ce) of it (half the
+// tile: two warps share each TMEM lane quarter): reads the accumulator 64 columns at a
+// time (four loads, one wait, so the TMEM latency is paid four times per tile instead of
+// sixteen) and books the pairs (i, j) whose relation bit is set in w4.  The accumulator is
+// released (arrival on `release`) as soon as its last columns are in registers, before
+// they are booked.  PHI is a template argument so the plain epilogue carries none of the
+// d'Alembertian code.
 template <bool PHI>
 __device__ __forceinline__ unsigned long long epi_tile(uint32_t tbase, const uint64_t (&w4)[4], int64_t i,
                                                        int64_t J0, unsigned long long &cR,
                                                        unsigned long long &cM, unsigned long long &cW,
                                                        unsigned long long *__restrict__ hist, long long nbins,
-                                                       double phi_i, double *__restrict__ acc_phi) {
-    unsigned long long packed = 0;  // N0..N3 of this tile, 16 bits each
+                                                       double phi_i, double *__restrict__ acc_phi,
+                                                       uint64_t *release, int cb, int ce) {
+    unsigned long long packed = 0;  // N0..N3 of this thread's columns [cb, ce), 16 bits each
 #pragma unroll 1
-    for (int c = 0; c < BN; c += 16) {
-        uint32_t v[16];
-        TMEM_LD16(tbase + (uint32_t)c, v);
-        const uint64_t wsel = c < 64 ? w4[0] : (c < 128 ? w4[1] : (c < 192 ? w4[2] : w4[3]));
-        const uint32_t bits = (uint32_t)(wsel >> (c & 63)) & 0xFFFFu;
+    for (int c = cb; c < ce; c += 64) {
+        uint32_t v0[16], v1[16], v2[16], v3[16];
+        TMEM_LD16(tbase + (uint32_t)c, v0);
+        TMEM_LD16(tbase + (uint32_t)c + 16u, v1);
+        TMEM_LD16(tbase + (uint32_t)c + 32u, v2);
+        TMEM_LD16(tbase + (uint32_t)c + 48u, v3);
+        const uint64_t w = c < 64 ? w4[0] : (c < 128 ? w4[1] : (c < 192 ? w4[2] : w4[3]));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (bits) {
-            // R and W of the chunk from bit counts: sum over set bits u of (J0+c+u - i - 1)
-            const unsigned pc = __popc(bits);
-            const unsigned su = __popc(bits & 0xAAAAu) + 2u * __popc(bits & 0xCCCCu) +
-                                4u * __popc(bits & 0xF0F0u) + 8u * __popc(bits & 0xFF00u);
-            cR += pc;
-            cW += (unsigned long long)pc * (unsigned long long)(J0 + c - i - 1) + su;
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                if (bits >> u & 1u) {
-                    const uint32_t m = __float2uint_rn(__uint_as_float(v[u]));
-                    cM += m;
-                    if (m < 4u) packed += 1ull << (16u * m);
-                    if (hist != nullptr && (long long)m < nbins) atomicAdd(&hist[m], 1ull);
-                    if (PHI && m < 3u) atomicAdd(&acc_phi[J0 + c + u], (m == 1u ? -2.0 : 1.0) * phi_i);
-                }
-            }
+        if (c + 64 == ce) {
+            tc_fence_before();
+            mbar_arrive(release);
         }
+        book16<PHI>(v0, (uint32_t)w & 0xFFFFu, J0 + c, i, packed, cR, cM, cW, hist, nbins, phi_i, acc_phi);
+        book16<PHI>(v1, (uint32_t)(w >> 16) & 0xFFFFu, J0 + c + 16, i, packed, cR, cM, cW, hist, nbins, phi_i,
+                    acc_phi);
+        book16<PHI>(v2, (uint32_t)(w >> 32) & 0xFFFFu, J0 + c + 32, i, packed, cR, cM, cW, hist, nbins, phi_i,
+                    acc_phi);
+        book16<PHI>(v3, (uint32_t)(w >> 48), J0 + c + 48, i, packed, cR, cM, cW, hist, nbins, phi_i, acc_phi);
     }
     return packed;
 }
 
+template <int FMT>
 __device__ __forceinline__ void k_range(const TcTile &t, int64_t N, int &kt0, int &kt1) {
-    // K runs from the tile's first row to its last column (or N)
+    // K runs from the tile's first row to its last column (or N), in stages of KSTAGE
+    constexpr int64_t KSTAGE = FMT ? 256 : 128;
     const int64_t I0 = (int64_t)t.ti * BM;
     const int64_t J1 = min((int64_t)(t.tj + 1) * BN, N);
-    kt0 = (int)(I0 / BK);
-    kt1 = (int)((J1 + BK - 1) / BK);
+    kt0 = (int)(I0 / KSTAGE);
+    kt1 = (int)((J1 + KSTAGE - 1) / KSTAGE);
 }
 
+template <int FMT>
 __global__ void __launch_bounds__(THREADS, 1)
 action_tc_kernel(const TcArgs args) {
+    constexpr uint32_t NACC = FMT ? 1u : 2u;  // TMEM accumulators (the fp4 form keeps its scale factors in the rest)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -305,6 +383,22 @@ action_tc_kernel(const TcArgs args) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     bool bad = false;
+    if (FMT && warp >= 2 && warp < 6) {
+        // scale factors 1.0 (ue8m0 0x7F) in columns 256..511 of this warp's lane quarter
+        const uint32_t one4 = 0x7F7F7F7Fu;
+        for (uint32_t c = 256; c < TMEM_COLS; c += 32) {
+            const uint32_t addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + c;
+            asm volatile(
+                "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+                "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(addr),
+                "r"(one4)
+                : "memory");
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -324,7 +418,7 @@ action_tc_kernel(const TcArgs args) {
                 if (t >= args.n_tiles) break;
                 const TcTile tile = args.tiles[t];
                 int kt0, kt1;
-                k_range(tile, args.sets[tile.set].N, kt0, kt1);
+                k_range<FMT>(tile, args.sets[tile.set].N, kt0, kt1);
                 const CUtensorMap *mU = args.maps + 2 * tile.set, *mP = mU + 1;
                 for (int kt = kt0; kt < kt1; ++kt) {
                     if (!ptx::mbar_wait_bounded(&empty[s], ph ^ 1u, kWaitNs)) {
@@ -333,8 +427,8 @@ action_tc_kernel(const TcArgs args) {
                     }
                     ptx::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
                     unsigned char *st = base + s * STAGE_BYTES;
-                    tma_load_2d(st, mU, kt * BK, tile.ti * BM, &full[s]);
-                    tma_load_2d(st + A_BYTES, mP, kt * BK, tile.tj * BN, &full[s]);
+                    tma_load_2d(st, mU, kt * BKB, tile.ti * BM, &full[s]);
+                    tma_load_2d(st + A_BYTES, mP, kt * BKB, tile.tj * BN, &full[s]);
                     if (++s == STAGES) {
                         s = 0;
                         ph ^= 1u;
@@ -357,7 +451,7 @@ action_tc_kernel(const TcArgs args) {
                 if (t < 0) break;
                 const TcTile tile = args.tiles[t];
                 int kt0, kt1;
-                k_range(tile, args.sets[tile.set].N, kt0, kt1);
+                k_range<FMT>(tile, args.sets[tile.set].N, kt0, kt1);
                 if (!ptx::mbar_wait_bounded(&tempty[b], bph ^ 1u, kWaitNs)) {
                     bad = true;
                     break;
@@ -372,10 +466,13 @@ action_tc_kernel(const TcArgs args) {
                     tc_fence_after();
                     const uint32_t sa = ptx::smem_addr(base + s * STAGE_BYTES);
 #pragma unroll
-                    for (int k = 0; k < BK / 32; ++k) {
+                    for (int k = 0; k < BKB / 32; ++k) {  // 32 bytes: K = 32 fp8 or 64 fp4 elements
                         const uint64_t ad = smem_desc_sw128(sa + 32 * k);
                         const uint64_t bd = smem_desc_sw128(sa + A_BYTES + 32 * k);
-                        mma_f8(dt, ad, bd, (kt > kt0 || k > 0) ? 1u : 0u);
+                        if (FMT)
+                            mma_f4(dt, ad, bd, tmem + kSfA, tmem + kSfB, (kt > kt0 || k > 0) ? 1u : 0u);
+                        else
+                            mma_f8(dt, ad, bd, (kt > kt0 || k > 0) ? 1u : 0u);
                     }
                     mma_commit(&empty[s]);
                     if (++s == STAGES) {
@@ -385,14 +482,16 @@ action_tc_kernel(const TcArgs args) {
                 }
                 if (bad) break;
                 mma_commit(&tfull[b]);
-                b ^= 1u;
+                if (NACC == 2) b ^= 1u;
                 if (b == 0) bph ^= 1u;
             }
         }
     } else {
-        // epilogue: TMEM lane quarter of this warp
+        // epilogue: TMEM lane quarter of this warp, and which half of the tile's columns
         const int q = warp & 3;
         const int r = q * 32 + lane;
+        const int g = (warp - 2) >> 2;
+        const int cb = g * (BN / 2), ce = cb + BN / 2;
         // per-thread counters; N0..N3 are packed 16 bits each and spilled into the
         // 64-bit totals after every tile (a tile holds at most 256 pairs per row)
         unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, cR = 0, cM = 0, cW = 0;
@@ -440,12 +539,12 @@ action_tc_kernel(const TcArgs args) {
             const int64_t N = S.N;
             const int64_t i = (int64_t)tile.ti * BM + r;
             const int64_t J0 = (int64_t)tile.tj * BN;
-            // the row's relation bits for columns J0..J0+255, fetched before the wait
+            // the row's relation bits for this warp's columns of J0..J0+255, fetched before the wait
             uint64_t w4[4] = {0, 0, 0, 0};
             if (i < N && i >= S.row_lo && i < S.row_hi) {
                 const uint64_t *src = S.rows + i * S.stride + J0 / 64;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) w4[u] = (J0 + 64 * u < N) ? __ldg(src + u) : 0ull;
+                for (int u = 0; u < 4; ++u) w4[u] = ((u >> 1) == g && J0 + 64 * u < N) ? __ldg(src + u) : 0ull;
                 // only columns j > i
                 const int64_t rel = i - J0;  // bit positions k > rel survive
 #pragma unroll
@@ -467,15 +566,15 @@ action_tc_kernel(const TcArgs args) {
             const uint32_t tbase = tmem + b * BN + ((uint32_t)(q * 32) << 16);
             const unsigned long long packed =
                 S.acc != nullptr
-                    ? epi_tile<true>(tbase, w4, i, J0, cR, cM, cW, args.hist, args.nbins, phi_i, S.acc)
-                    : epi_tile<false>(tbase, w4, i, J0, cR, cM, cW, args.hist, args.nbins, 0.0, nullptr);
+                    ? epi_tile<true>(tbase, w4, i, J0, cR, cM, cW, args.hist, args.nbins, phi_i, S.acc, &tempty[b],
+                                     cb, ce)
+                    : epi_tile<false>(tbase, w4, i, J0, cR, cM, cW, args.hist, args.nbins, 0.0, nullptr,
+                                      &tempty[b], cb, ce);
             c0 += packed & 0xFFFFull;
             c1 += (packed >> 16) & 0xFFFFull;
             c2 += (packed >> 32) & 0xFFFFull;
             c3 += packed >> 48;
-            tc_fence_before();
-            mbar_arrive(&tempty[b]);
-            b ^= 1u;
+            if (NACC == 2) b ^= 1u;
             if (b == 0) bph ^= 1u;
         }
         if (cur >= 0) flush(cur);
@@ -554,7 +653,7 @@ int encode_map(CUtensorMap *m, void *base, int64_t rows, int64_t kp, int box_row
     }
     cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)kp};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)BKB, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -574,9 +673,11 @@ static constexpr int64_t kTcMaxN = 1 << 17;
 static constexpr int64_t kChunkBytes = 16ll << 30;
 
 TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned long long *hist,
-               int64_t nbins, int *rc, const int *slots, int super) {
+               int64_t nbins, int *rc, const int *slots, int super, int fmt) {
     TcPlan p;
     *rc = CSG_OK;
+    fmt = fmt ? 1 : 0;
+    p.fmt = fmt;
     if (slots) p.slot.assign(slots, slots + n);
     if (super < BN) super = BN;
     p.n_sets = n;
@@ -604,7 +705,8 @@ TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned
         D.counters = nullptr;
         D.phi = S.phi;
         D.acc = S.acc;
-        D.kp = (S.N + BK - 1) / BK * BK;
+        // operand row bytes: N rounded up to a whole stage (128 fp8 or 256 fp4 elements)
+        D.kp = fmt ? (S.N + 255) / 256 * 128 : (S.N + 127) / 128 * 128;
         const int64_t ob = 2 * S.N * D.kp;
         if (s > cur.set_lo && chunk_bytes + ob > kChunkBytes) {
             cur.set_hi = s;
@@ -631,7 +733,7 @@ TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned
         std::vector<TcTile> tiles;
         for (int s = c.set_lo; s < c.set_hi; ++s) {
             wstarts.push_back(total);
-            total += desc[s].N * (desc[s].kp / 64);
+            total += desc[s].N * ((fmt ? 2 * desc[s].kp : desc[s].kp) / 64);
         }
         if (c.set_hi - c.set_lo == 1) {
             const TcSetDesc &D = desc[c.set_lo];
@@ -681,9 +783,10 @@ int tc_patch(const TcPlan &p, Arena &a) {
     return CSG_OK;
 }
 
-int tc_launch(const TcPlan &p, const Arena &a, cudaStream_t st) {
+template <int FMT>
+static int tc_launch_fmt(const TcPlan &p, const Arena &a, cudaStream_t st) {
     const size_t smem = 1024 + STAGES * STAGE_BYTES + 512;
-    CSG_CUDA_TRY(cudaFuncSetAttribute(action_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CSG_CUDA_TRY(cudaFuncSetAttribute(action_tc_kernel<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     unsigned int *queues = a.scr<unsigned int>(p.s_queues);
     CSG_CUDA_TRY(cudaMemsetAsync(queues, 0, p.chunks.size() * sizeof(unsigned int), st));
     int dev = 0, sms = 0;
@@ -695,8 +798,8 @@ int tc_launch(const TcPlan &p, const Arena &a, cudaStream_t st) {
         if (c.words > 0) {
             const int blocks = (int)std::min<int64_t>((c.words + 255) / 256, (int64_t)sms * 32);
             stage_begin(CSG_STAGE_EXPAND, st);
-            expand_kernel<<<blocks, 256, 0, st>>>(d_sets, a.tab<int64_t>(c.t_wstarts), c.set_lo,
-                                                  c.set_hi - c.set_lo, c.words);
+            expand_kernel<FMT><<<blocks, 256, 0, st>>>(d_sets, a.tab<int64_t>(c.t_wstarts), c.set_lo,
+                                                       c.set_hi - c.set_lo, c.words);
             stage_end(CSG_STAGE_EXPAND, st);
         }
         if (c.n_tiles > 0) {
@@ -709,12 +812,16 @@ int tc_launch(const TcPlan &p, const Arena &a, cudaStream_t st) {
             args.hist = p.hist;
             args.nbins = (long long)p.nbins;
             stage_begin(CSG_STAGE_ACTION, st);
-            action_tc_kernel<<<std::min(sms, c.n_tiles), THREADS, smem, st>>>(args);
+            action_tc_kernel<FMT><<<std::min(sms, c.n_tiles), THREADS, smem, st>>>(args);
             stage_end(CSG_STAGE_ACTION, st);
         }
         CSG_CUDA_TRY(cudaGetLastError());
     }
     return CSG_OK;
+}
+
+int tc_launch(const TcPlan &p, const Arena &a, cudaStream_t st) {
+    return p.fmt ? tc_launch_fmt<1>(p, a, st) : tc_launch_fmt<0>(p, a, st);
 }
 
 }  // namespace csg

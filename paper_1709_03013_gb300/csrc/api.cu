@@ -269,7 +269,7 @@ int csg_set_from_bitmap(csg_ctx *ctx, int d, int64_t N, const uint64_t *dev_rows
 
 static int action_common(csg_ctx *ctx, csg_set *set, int method, int64_t lo, int64_t hi,
                          unsigned long long *hist, int64_t nbins, csg_result *out, void *stream) {
-    if (!ctx || !set || !out || set->ctx != ctx || (method != CSG_POPC && method != CSG_TC)) {
+    if (!ctx || !set || !out || set->ctx != ctx || !method_ok(method)) {
         set_error("csg_action: bad arguments");
         return CSG_E_INVAL;
     }
@@ -312,7 +312,7 @@ int csg_action_hist(csg_ctx *ctx, csg_set *set, int method, uint64_t *dev_hist, 
 
 int csg_action_smeared(csg_ctx *ctx, csg_set *set, int method, double eps, double *S_eps,
                        csg_result *out, void *stream) {
-    if (!ctx || !set || !S_eps || set->ctx != ctx || (method != CSG_POPC && method != CSG_TC) ||
+    if (!ctx || !set || !S_eps || set->ctx != ctx || !method_ok(method) ||
         !(eps > 0.0 && eps < 1.0)) {
         set_error("csg_action_smeared: bad arguments (0 < eps < 1, method POPC or TC)");
         return CSG_E_INVAL;
@@ -332,7 +332,7 @@ int csg_action_smeared(csg_ctx *ctx, csg_set *set, int method, double eps, doubl
 
 int csg_dalembertian(csg_ctx *ctx, csg_set *set, int method, const double *phi, double l, double *Bphi,
                      csg_result *out, void *stream) {
-    if (!ctx || !set || set->ctx != ctx || !phi || !Bphi || (method != CSG_POPC && method != CSG_TC) ||
+    if (!ctx || !set || set->ctx != ctx || !phi || !Bphi || !method_ok(method) ||
         !(l > 0.0 && l < INFINITY)) {
         set_error("csg_dalembertian: bad arguments (device phi and Bphi, 0 < l < inf, method POPC or TC)");
         return CSG_E_INVAL;
@@ -357,7 +357,7 @@ int csg_dalembertian(csg_ctx *ctx, csg_set *set, int method, const double *phi, 
 
 int csg_action_batch(csg_ctx *ctx, csg_set *const *sets, int n, int method, csg_result *out,
                      void *stream) {
-    if (!ctx || (n > 0 && (!sets || !out)) || n < 0 || (method != CSG_POPC && method != CSG_TC)) {
+    if (!ctx || (n > 0 && (!sets || !out)) || n < 0 || !method_ok(method)) {
         set_error("csg_action_batch: bad arguments");
         return CSG_E_INVAL;
     }
@@ -382,7 +382,7 @@ int csg_run_batch(csg_ctx *ctx, int n, const int32_t *d, const int64_t *N, const
             set_error("csg_run_batch: bad spec %d (d=%d, N=%lld)", s, d[s], (long long)N[s]);
             return CSG_E_INVAL;
         }
-    if (method != CSG_POPC && method != CSG_TC) {
+    if (!method_ok(method)) {
         set_error("csg_run_batch: bad method");
         return CSG_E_INVAL;
     }

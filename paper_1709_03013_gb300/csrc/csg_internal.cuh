@@ -141,8 +141,8 @@ struct TcSetDesc {
     const uint64_t *rows;
     int64_t N, stride, row_lo, row_hi;
     unsigned long long *counters;
-    uint8_t *U, *P;  // fp8 operands (strict future rows, strict past rows), N x kp bytes
-    int64_t kp;      // operand row pitch (N rounded up to 128)
+    uint8_t *U, *P;  // 0/1 operands (strict future rows, strict past rows), N x kp bytes
+    int64_t kp;      // operand row bytes: N rounded up to 128 (fp8) or to 256 elements / 2 (fp4)
     const double *phi;  // optional d'Alembertian sums, as in SetDesc
     double *acc;
 };
@@ -154,6 +154,7 @@ struct TcPlan {
     };
     std::vector<int> slot;  // counter slot of each set (empty: identity)
     int n_sets = 0;
+    int fmt = 0;            // operand format: 0 fp8 e4m3 (two TMEM accumulators), 1 fp4 e2m1 (block-scaled, one)
     size_t t_sets = 0, t_maps = 0, s_ops = 0, s_counters = 0, s_queues = 0;
     unsigned long long *hist = nullptr;
     int64_t nbins = 0;
@@ -161,7 +162,7 @@ struct TcPlan {
 };
 // super: side of the square blocks (in elements) in which output tiles are rasterised
 TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned long long *hist,
-               int64_t nbins, int *rc, const int *slots = nullptr, int super = 2048);
+               int64_t nbins, int *rc, const int *slots = nullptr, int super = 2048, int fmt = 0);
 int tc_patch(const TcPlan &p, Arena &a);
 int tc_launch(const TcPlan &p, const Arena &a, cudaStream_t st);
 

@@ -47,6 +47,10 @@ int alloc_set(csg_ctx *ctx, int d, int64_t N, csg_set **out);
 void free_set(csg_set *s);
 
 // Action for n linked sets; writes n host results and synchronises st.
+// Interval-count methods of the ABI and the tensor operand format each one selects.
+inline bool method_ok(int m) { return m == CSG_POPC || m == CSG_TC || m == CSG_TC_FP8 || m == CSG_TC_FP4; }
+constexpr int kTcDefaultFmt = 1;  // format of CSG_TC: 0 fp8, 1 fp4 (measured faster on GB300)
+inline int tc_format(int m) { return m == CSG_TC_FP4 ? 1 : (m == CSG_TC_FP8 ? 0 : kTcDefaultFmt); }
 int run_dalembertian(csg_set *set, int method, const double *phi, double l, double *Bphi, csg_result *out,
                      cudaStream_t st);
 int run_actions(csg_set *const *sets, int n, int method, int64_t row_lo, int64_t row_hi,

@@ -146,7 +146,7 @@ int build_seq(Seq &q, csg_set *const *sets, int n, int method, int64_t row_lo, i
     if (!dt.empty()) {
         q.has_tc = true;
         q.tp = tc_plan(dt.data(), (int)dt.size(), q.a, q.s_counters, hist, nbins, &rc, st_slot.data(),
-                       tune.super);
+                       tune.super, tc_format(method));
         if (rc != CSG_OK) return rc;
     }
     q.t_fin = q.a.put(fin.data(), n * sizeof(FinRow));
@@ -359,7 +359,7 @@ void free_batch_graph(csg_ctx *ctx) {
 // ~/.cache/csg/autotune.jsonl); CSG_AUTOTUNE=0 skips tuning, and batches of fewer
 // than 16 sets keep the defaults.
 
-static std::string tune_key(int n, const int32_t *d, const int64_t *N) {
+static std::string tune_key(int n, const int32_t *d, const int64_t *N, int method) {
     cudaDeviceProp prop;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -371,7 +371,8 @@ static std::string tune_key(int n, const int32_t *d, const int64_t *N) {
         d2 += d[s] == 2;
     }
     char buf[256];
-    snprintf(buf, sizeof buf, "%s|tc|n=%d|sumN=%lld|maxN=%lld|d2=%lld", prop.name, n, sumN, maxN, d2);
+    snprintf(buf, sizeof buf, "%s|tc%d|n=%d|sumN=%lld|maxN=%lld|d2=%lld", prop.name, tc_format(method), n, sumN,
+             maxN, d2);
     return buf;
 }
 
@@ -418,12 +419,12 @@ static void tune_store(const std::string &key, const Tune &t, double ms) {
 }
 
 static int autotune(csg_ctx *ctx, csg_set *const *sets, int n, const int32_t *d, const int64_t *N,
-                    const uint64_t *seed, const uint64_t *seq, Tune *best) {
+                    const uint64_t *seed, const uint64_t *seq, int method, Tune *best) {
     (void)ctx;
     const char *env = getenv("CSG_AUTOTUNE");
     if (env && env[0] == '0') return CSG_OK;
     if (n < 16) return CSG_OK;  // small batches keep the defaults
-    const std::string key = tune_key(n, d, N);
+    const std::string key = tune_key(n, d, N, method);
     if (tune_lookup(key, best)) return CSG_OK;
     const Tune cands[] = {{0, 2048}, {1024, 2048}, {2048, 2048}, {0, 1024}};
     cudaStream_t st = nullptr;
@@ -438,7 +439,7 @@ static int autotune(csg_ctx *ctx, csg_set *const *sets, int n, const int32_t *d,
     int rc = CSG_OK;
     for (const Tune &t : cands) {
         Seq q;
-        rc = build_seq(q, sets, n, CSG_TC, -1, -1, nullptr, 0, seed, seq, t);
+        rc = build_seq(q, sets, n, method, -1, -1, nullptr, 0, seed, seq, t);
         if (rc != CSG_OK) break;
         rc = arena_alloc(q.a, st);
         if (rc != CSG_OK) break;
@@ -487,7 +488,7 @@ static int build_batch_graph(csg_ctx *ctx, int n, const int32_t *d, const int64_
         if (rc == CSG_OK) g->sets.push_back(x);
     }
     Tune tune;
-    if (rc == CSG_OK && method == CSG_TC) rc = autotune(ctx, g->sets.data(), n, d, N, seed, seq, &tune);
+    if (rc == CSG_OK && method != CSG_POPC) rc = autotune(ctx, g->sets.data(), n, d, N, seed, seq, method, &tune);
     if (rc == CSG_OK) rc = build_seq(g->q, g->sets.data(), n, method, -1, -1, nullptr, 0, seed, seq, tune);
     if (rc == CSG_OK && cudaMalloc((void **)&g->q.a.dev, g->q.a.bytes()) != cudaSuccess) {
         cudaGetLastError();

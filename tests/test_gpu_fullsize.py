@@ -123,6 +123,8 @@ def test_full_size_set(ctx, csg, d, N, seed, rows):
     assert tc.N == N and tc.d == d and tc.status == 0
     pc = s.action(csg.POPC)                                        # independent kernel
     _same(pc, tc)
+    for fmt in (csg.TC_FP8, csg.TC_FP4):                           # both tensor operand formats
+        _same(s.action(fmt), tc)
     combo, S = oracle.finalize(d, N, tc.Nk)
     assert tc.combo == combo and abs(tc.S - S) <= TOL_S * max(abs(S), 1.0)
     _check_rows(s, d, coords, rows, csg)                           # sampled N_k against the oracle
@@ -136,6 +138,9 @@ def test_batch_4096_sets(ctx, csg):
     tc = ctx.run_batch(tup, csg.TC)
     pc = ctx.run_batch(tup, csg.POPC)
     for a, b in zip(tc, pc):
+        _same(a, b)
+    other = csg.TC_FP4 if csg.TC != csg.TC_FP4 else csg.TC_FP8
+    for a, b in zip(ctx.run_batch(tup, other), tc):                # the other tensor operand format
         _same(a, b)
     rng = np.random.default_rng(7)
     sample = sorted(set(rng.choice(4096, 10, replace=False).tolist()) |

@@ -112,7 +112,7 @@ def test_golden_fixtures_on_gpu(ctx, csg, golden, name):
     dev = _dev_words(inputs.pack_rows(rel, 16))
     for d, key in ((2, "S2"), (4, "S4")):
         s = ctx.set_from_bitmap(d, g["N"], dev.data_ptr(), 16)
-        for method in (csg.POPC, csg.TC):
+        for method in (csg.POPC, csg.TC, csg.TC_FP8, csg.TC_FP4):
             r = s.action(method)
             assert list(r.Nk) == g["Nk"] and r.R == g["R"] and r.sum_m == g["sum_m"]
             assert r.combo == g["combo2" if d == 2 else "combo4"]
@@ -379,3 +379,50 @@ def test_dalembertian_rejects_bad_arguments(ctx, csg):
     s2.dalembertian(p, q, 1.0, csg.TC)            # still usable afterwards
     s4.free()
     s2.free()
+
+
+# ------------------------------------------------------------ tensor operand formats
+
+FORMATS = [2, 3]  # CSG_TC_FP8 (e4m3, kind::f8f6f4) and CSG_TC_FP4 (packed e2m1, kind::mxf4)
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+@pytest.mark.parametrize("d,N", [(2, 1), (2, 2), (4, 3), (2, 129), (4, 257), (2, 1000), (4, 2500),
+                                 (2, 4099), (4, 5000)])
+def test_tensor_formats_match_oracle(ctx, csg, fmt, d, N):
+    seed, seq = 1000 + N, d
+    s = ctx.sprinkle(d, N, seed, seq).link()
+    want = oracle.action(oracle.link(d, oracle.sprinkle_sorted(d, N, seed, seq)))
+    _check_result(s.action(fmt), want, d, N)
+    s.free()
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_tensor_formats_hist_bitmaps_batch_rows(ctx, csg, fmt):
+    import torch
+    # full histogram
+    N = 3000
+    s = ctx.sprinkle(2, N, 7, 0).link()
+    want = oracle.action(oracle.link(2, oracle.sprinkle_sorted(2, N, 7, 0)))
+    h = torch.full((N,), 7, dtype=torch.int64, device="cuda")
+    _check_result(s.action_hist(h.data_ptr(), N, fmt), want, 2, N)
+    assert np.array_equal(h.cpu().numpy().astype(np.uint64), want["hist"][:N])
+    # a row range
+    res = s.action_rows(300, 2100, fmt)
+    rr = oracle.action(oracle.link(2, oracle.sprinkle_sorted(2, N, 7, 0)), rows=(300, 2100))
+    assert res.R == rr["R"] and list(res.Nk) == [int(x) for x in rr["Nk"]] and res.W == rr["W"]
+    s.free()
+    # caller bitmaps, including orders no sprinkle produces
+    for rel in (inputs.random_upper_rel(700, 0.3, 1), inputs.layered_order_rel(1200, 3), inputs.chain_rel(1030)):
+        n = rel.shape[0]
+        stride = (n + 63) // 64 + 3
+        dev = _dev_words(inputs.pack_rows(rel, stride))
+        b = ctx.set_from_bitmap(2, n, dev.data_ptr(), stride)
+        _check_result(b.action(fmt), oracle.action(rel), 2, n)
+        b.free()
+    # several sets in one launch
+    sets = [ctx.sprinkle(d, n, 40 + k, 1).link() for k, (d, n) in enumerate([(2, 500), (4, 1700), (2, 2600), (4, 90)])]
+    got = ctx.action_batch(sets, fmt)
+    for st, r, (d, n, k) in zip(sets, got, [(2, 500, 0), (4, 1700, 1), (2, 2600, 2), (4, 90, 3)]):
+        _check_result(r, oracle.action(oracle.link(d, oracle.sprinkle_sorted(d, n, 40 + k, 1))), d, n)
+        st.free()
