@@ -16,26 +16,32 @@
 // Pass 1 (expand): one thread per packed word writes the operand bytes of U and of P it
 // covers (64 fp8 bytes or 32 fp4 bytes each); only the column ranges the product reads
 // are written.
-// Pass 2 (product): persistent CTAs, one per SM, take output tiles (128 rows i x 256
-// columns j, upper triangle only, K from the first row of the tile to the last
-// column) from a global work queue (an atomic counter over a tile list ordered set by
-// set, longest first, block-rasterised); claiming tiles in list order keeps the CTAs
-// on the same set's operands, which then stay in L2.
+// Pass 2 (product): persistent CTA pairs (clusters of two CTAs, one per SM) take pair tiles
+// (256 rows i x 256 columns j, upper triangle only, K from the first row of the tile to its
+// last column) from a global work queue: the leader CTA claims each tile with an atomic
+// counter over a tile list ordered set by set, longest first, block-rasterised, and mails the
+// index to the other CTA; claiming in list order keeps the tiles running at once on the same
+// set's operands, which then stay in L2.  The pair runs 2-SM MMAs (cta_group::2): each CTA
+// stages its own 128 rows of U and 128 of the tile's 256 rows of P, the leader issues the
+// MMAs, and each CTA's TMEM receives the accumulator of its own 128 rows, so each SM loads
+// 32 KB per stage instead of the 48 KB a one-SM 128 x 256 tile needs.
 // Warp roles per CTA:
-//   warp 0     claims tiles and passes their indices to warps 1-9 through a 4-slot
-//              shared-memory ring; TMA producer: 128-byte-swizzled K stages of U
-//              (128 rows x 128 bytes) and P (256 x 128 bytes) into a 4-stage ring
-//   warp 1     allocates 512 TMEM columns; one lane issues the MMAs (M=128, N=256,
-//              32 bytes of K each: 32 fp8 or 64 fp4 elements) and commits each stage
-//              back to the producer and each finished tile to the epilogue
-//   warps 2-9  epilogue: tcgen05.ld of the tile from TMEM (each thread owns one row and
-//              half of the columns), the S bits of the row select the related pairs,
-//              counters, the optional full histogram and the optional d'Alembertian
-//              sums (Eq. b_local) are updated.  The fp8 form keeps two accumulators
-//              (columns 0 and 256) so the epilogue of one tile overlaps the product of
-//              the next; the fp4 form keeps one accumulator at column 0 and its scale
-//              factors in columns 256..511, and releases the accumulator as soon as the
-//              last columns are in registers.
+//   warp 0     the tile queue (leader) or its mailbox (other CTA), handed to warps 1-9
+//              through a 4-slot shared-memory ring; TMA producer: 128-byte-swizzled K
+//              stages of 128 rows of U and 128 rows of P (16 KB each) into a 6-stage ring
+//              whose transaction bytes are counted on the leader's barrier
+//   warp 1     allocates 512 TMEM columns together with the other CTA; in the leader one
+//              lane issues the MMAs (M=256, N=256, 32 bytes of K each: 32 fp8 or 64 fp4
+//              elements) and commits each stage back to both producers and each finished
+//              tile to both epilogues
+//   warps 2-9  epilogue: tcgen05.ld of the CTA's 128 rows from TMEM (each thread owns one
+//              row and half of the columns), the S bits of the row select the related pairs,
+//              counters, the optional full histogram and the optional d'Alembertian sums
+//              (Eq. b_local) are updated.  The fp8 form keeps two accumulators (columns 0
+//              and 256) so the epilogue of one tile overlaps the product of the next; the
+//              fp4 form keeps one accumulator at column 0 and its scale factors in columns
+//              256..511, and releases the accumulator as soon as the last columns are in
+//              registers.  Both CTAs' epilogues release an accumulator to the leader.
 // Every wait is bounded (globaltimer); on expiry the kernel records an error in the
 // set's counters and winds down instead of spinning.
 #include <cuda.h>
@@ -56,12 +62,12 @@
 namespace csg {
 namespace {
 
-constexpr int BM = 128;          // rows i per tile
+constexpr int BM = 128;          // rows i per CTA; a pair tile of the two CTAs of a cluster has 2 * BM
 constexpr int BN = 256;          // columns j per tile
 constexpr int BKB = 128;         // bytes of each operand row per stage (one 128-byte swizzle row)
-constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BKB;
-constexpr int B_BYTES = BN * BKB;
+constexpr int STAGES = 6;
+constexpr int A_BYTES = BM * BKB;        // this CTA's 128 rows of U
+constexpr int B_BYTES = (BN / 2) * BKB;  // this CTA's 128 of the tile's 256 rows of P
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, one for each half of the tile's columns
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
@@ -141,7 +147,6 @@ __device__ __forceinline__ void put64(uint8_t *dst, uint64_t m) {
 template <int FMT>
 __global__ void expand_kernel(const TcSetDesc *__restrict__ sets, const int64_t *__restrict__ wstarts,
                               int set_lo, int nset, int64_t total) {
-    constexpr int64_t KSTAGE = FMT ? 256 : 128;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
          g += (int64_t)gridDim.x * blockDim.x) {
         const int ls = find_set(wstarts, nset, g);
@@ -151,9 +156,9 @@ __global__ void expand_kernel(const TcSetDesc *__restrict__ sets, const int64_t 
         const int64_t i = gl / wpr, w = gl - i * wpr;
         const int64_t k0 = w * 64;
         const uint64_t word = S.rows[i * S.stride + w];
-        // U row i is read from the stage holding column BM*floor(i/BM); P row i up to
-        // column BN*(floor(i/BN)+1)
-        if (k0 + 64 > (i / BM) * BM / KSTAGE * KSTAGE) {
+        // U row i is read from the first column of its pair tile, 2*BM*floor(i/(2*BM)) (a
+        // whole number of stages in either format); P row i up to column BN*(floor(i/BN)+1)
+        if (k0 + 64 > (i / (2 * BM)) * (2 * BM)) {
             uint64_t m = word;
             if (k0 + 63 <= i)
                 m = 0;
@@ -190,30 +195,76 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
     return d;
 }
 
-// kind::f8f6f4, A = B = e4m3, D = f32, K-major A and B, M = 128, N = 256
+// kind::f8f6f4, A = B = e4m3, D = f32, K-major A and B, M = 256 (two CTAs), N = 256
 constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
+                            ((uint32_t)((2 * BM) >> 4) << 24);
 // kind::mxf4 with block scaling: A = B = e2m1 (1), scale factors ue8m0 (bit 23), scale
-// factor ids 0, D = f32, K-major A and B, M = 128, N = 256
+// factor ids 0, D = f32, K-major A and B, M = 256 (two CTAs), N = 256
 constexpr uint32_t kIdescF4 = (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | (1u << 23) |
-                              ((uint32_t)(BM >> 4) << 24);
+                              ((uint32_t)((2 * BM) >> 4) << 24);
 // TMEM columns of the fp4 form: accumulator 0..255, scale factors of A at 256 and of B at
 // 384 (every scale factor is 1.0, so columns 256..511 are filled with the byte 0x7F)
 constexpr uint32_t kSfA = 256, kSfB = 384;
 
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
-                                            uint64_t *bar) {
+// TMA tile load into this CTA's shared memory whose bytes are counted on the pair's
+// barrier `bar` (a shared::cluster address: the leader CTA's barrier)
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            ptx::smem_addr(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(ptx::smem_addr(bar))
+        "cp.async.bulk.tensor.2d.shared::cta.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(ptx::smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
 
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// shared::cluster address of this CTA's shared variable at `p` as seen in CTA `rank`
+__device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(ptx::smem_addr(p)), "r"(rank));
+    return r;
+}
+
+// All threads of both CTAs of the cluster (release / acquire at cluster scope).
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+// Bounded wait with cluster-scope acquire (the barriers of this kernel are completed by
+// the other CTA of the pair as well).
+__device__ __forceinline__ bool mbar_wait_cl(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    auto try_wait = [&]() {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(ptx::smem_addr(bar)), "r"(parity)
+            : "memory");
+        return ok != 0;
+    };
+    if (try_wait()) return true;
+    const uint64_t t0 = ptx::globaltimer_ns();
+    while (!try_wait()) {
+        if (ptx::globaltimer_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+// One MMA of the CTA pair (issued by the leader): A rows 0..127 from the leader's shared
+// memory and 128..255 from the other CTA's, B rows split the same way, D into both TMEMs.
 __device__ __forceinline__ void mma_f8(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t acc) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
         "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
         : "memory");
 }
@@ -222,16 +273,20 @@ __device__ __forceinline__ void mma_f4(uint32_t dtmem, uint64_t ad, uint64_t bd,
                                        uint32_t acc) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %6, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n}\n" ::"r"(
+        "tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n}\n" ::"r"(
             dtmem),
         "l"(ad), "l"(bd), "r"(kIdescF4), "r"(sfa), "r"(sfb), "r"(acc)
         : "memory");
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     ptx::smem_addr(bar))
-                 : "memory");
+// Arrive on the barrier at the same offset in both CTAs of the pair once the leader's
+// issued MMAs have completed.
+__device__ __forceinline__ void mma_commit_pair(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            ptx::smem_addr(bar)),
+        "h"((uint16_t)0x3)
+        : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_after() {
@@ -296,8 +351,8 @@ __device__ __forceinline__ void book16(const uint32_t (&v)[16], uint32_t bits, i
 // tile: two warps share each TMEM lane quarter): reads the accumulator 64 columns at a
 // time (four loads, one wait, so the TMEM latency is paid four times per tile instead of
 // sixteen) and books the pairs (i, j) whose relation bit is set in w4.  The accumulator is
-// released (arrival on `release`) as soon as its last columns are in registers, before
-// they are booked.  PHI is a template argument so the plain epilogue carries none of the
+// released (an arrival on the leader CTA's barrier `release`, a shared::cluster address)
+// as soon as its last columns are in registers, before they are booked.  PHI is a template argument so the plain epilogue carries none of the
 // d'Alembertian code.
 template <bool PHI>
 __device__ __forceinline__ unsigned long long epi_tile(uint32_t tbase, const uint64_t (&w4)[4], int64_t i,
@@ -305,7 +360,7 @@ __device__ __forceinline__ unsigned long long epi_tile(uint32_t tbase, const uin
                                                        unsigned long long &cM, unsigned long long &cW,
                                                        unsigned long long *__restrict__ hist, long long nbins,
                                                        double phi_i, double *__restrict__ acc_phi,
-                                                       uint64_t *release, int cb, int ce) {
+                                                       uint32_t release, int cb, int ce) {
     unsigned long long packed = 0;  // N0..N3 of this thread's columns [cb, ce), 16 bits each
 #pragma unroll 1
     for (int c = cb; c < ce; c += 64) {
@@ -317,8 +372,10 @@ __device__ __forceinline__ unsigned long long epi_tile(uint32_t tbase, const uin
         const uint64_t w = c < 64 ? w4[0] : (c < 128 ? w4[1] : (c < 192 ? w4[2] : w4[3]));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (c + 64 == ce) {
+            // the warp's reads of the accumulator are done: one arrival of 32 on the leader's barrier
             tc_fence_before();
-            mbar_arrive(release);
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0) mbar_arrive_cluster(release, 32);
         }
         book16<PHI>(v0, (uint32_t)w & 0xFFFFu, J0 + c, i, packed, cR, cM, cW, hist, nbins, phi_i, acc_phi);
         book16<PHI>(v1, (uint32_t)(w >> 16) & 0xFFFFu, J0 + c + 16, i, packed, cR, cM, cW, hist, nbins, phi_i,
@@ -341,9 +398,13 @@ __device__ __forceinline__ void k_range(const TcTile &t, int64_t N, int &kt0, in
 }
 
 template <int FMT>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
 action_tc_kernel(const TcArgs args) {
     constexpr uint32_t NACC = FMT ? 1u : 2u;  // TMEM accumulators (the fp4 form keeps its scale factors in the rest)
+    // The two CTAs of a cluster form a tensor-core pair: each stages its 128 rows of U and
+    // 128 of the tile's 256 rows of P, the leader (rank 0) issues the MMAs of the 256 x 256
+    // pair tile, and each CTA's TMEM receives the accumulator of its own 128 rows.
+    const uint32_t rank = cluster_rank();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -351,33 +412,39 @@ action_tc_kernel(const TcArgs args) {
     uint64_t *full = bars, *empty = bars + STAGES, *tfull = bars + 2 * STAGES,
              *tempty = bars + 2 * STAGES + 2;
     uint64_t *rfull = bars + 2 * STAGES + 4, *rempty = rfull + RING;
-    int *ring = reinterpret_cast<int *>(rempty + RING);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ring + RING);
+    // tile indices the leader claims and mails to the other CTA (slots in the other CTA's
+    // shared memory): mail_full lives with the reader, mail_empty with the leader
+    uint64_t *mail_full = rempty + RING, *mail_empty = mail_full + RING;
+    int *ring = reinterpret_cast<int *>(mail_empty + RING);
+    int *mail = ring + RING;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mail + RING);
     int *bad_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            ptx::mbar_init(&full[s], 1);
-            ptx::mbar_init(&empty[s], 1);
+            ptx::mbar_init(&full[s], 1);   // leader: its own arrival + the bytes of both CTAs' loads
+            ptx::mbar_init(&empty[s], 1);  // the leader's commit, multicast to both CTAs
         }
         for (int b = 0; b < 2; ++b) {
-            ptx::mbar_init(&tfull[b], 1);
-            ptx::mbar_init(&tempty[b], EPI_WARPS * 32);
+            ptx::mbar_init(&tfull[b], 1);                   // the leader's commit, multicast
+            ptx::mbar_init(&tempty[b], 2 * EPI_WARPS * 32);  // leader: the epilogue threads of both CTAs
         }
         for (int q = 0; q < RING; ++q) {
             ptx::mbar_init(&rfull[q], 1);
             ptx::mbar_init(&rempty[q], 1 + EPI_WARPS * 32);  // the MMA lane and every epilogue thread
+            ptx::mbar_init(&mail_full[q], 1);   // other CTA: the leader's remote arrival
+            ptx::mbar_init(&mail_empty[q], 1);  // leader: the other CTA's producer has read the slot
         }
         *bad_flag = 0;
         ptx::fence_mbar_init();
     }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+    if (warp == 1) {  // one warp of each CTA of the pair allocates together
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          ptx::smem_addr(tmem_slot)),
                      "r"(TMEM_COLS)
                      : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
     }
     __syncthreads();
     tc_fence_after();
@@ -398,6 +465,7 @@ action_tc_kernel(const TcArgs args) {
     }
     tc_fence_before();
     __syncthreads();
+    cluster_sync();  // both CTAs' barriers and scale factors exist before either uses the other's
     tc_fence_after();
 
     if (warp == 0) {
@@ -405,14 +473,33 @@ action_tc_kernel(const TcArgs args) {
             int s = 0;
             uint32_t ph = 0;
             for (int n = 0; !bad; ++n) {
-                // claim the next tile and hand its index to the MMA and epilogue warps
+                // the pair's next tile: the leader claims it from the global queue (in list
+                // order, so the tiles running at once stay neighbours in L2) and mails the index
+                // to the other CTA; each producer hands it to its own MMA and epilogue warps
                 const int slot = n % RING;
                 const uint32_t rph = (uint32_t)(n / RING) & 1u;
                 if (!ptx::mbar_wait_bounded(&rempty[slot], rph ^ 1u, kWaitNs)) {
                     bad = true;
                     break;
                 }
-                const int t = (int)atomicAdd(args.queue, 1u);
+                int t;
+                if (rank == 0) {
+                    if (!mbar_wait_cl(&mail_empty[slot], rph ^ 1u, kWaitNs)) {
+                        bad = true;
+                        break;
+                    }
+                    t = (int)atomicAdd(args.queue, 1u);
+                    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr(&mail[slot], 1)), "r"(t)
+                                 : "memory");
+                    mbar_arrive_cluster(cluster_addr(&mail_full[slot], 1), 1);
+                } else {
+                    if (!mbar_wait_cl(&mail_full[slot], rph, kWaitNs)) {
+                        bad = true;
+                        break;
+                    }
+                    t = mail[slot];
+                    mbar_arrive_cluster(cluster_addr(&mail_empty[slot], 0), 1);
+                }
                 ring[slot] = t < args.n_tiles ? t : -1;
                 mbar_arrive(&rfull[slot]);
                 if (t >= args.n_tiles) break;
@@ -421,14 +508,15 @@ action_tc_kernel(const TcArgs args) {
                 k_range<FMT>(tile, args.sets[tile.set].N, kt0, kt1);
                 const CUtensorMap *mU = args.maps + 2 * tile.set, *mP = mU + 1;
                 for (int kt = kt0; kt < kt1; ++kt) {
-                    if (!ptx::mbar_wait_bounded(&empty[s], ph ^ 1u, kWaitNs)) {
+                    if (!mbar_wait_cl(&empty[s], ph ^ 1u, kWaitNs)) {
                         bad = true;
                         break;
                     }
-                    ptx::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                    if (rank == 0) ptx::mbar_arrive_expect_tx(&full[s], 2 * STAGE_BYTES);
                     unsigned char *st = base + s * STAGE_BYTES;
-                    tma_load_2d(st, mU, kt * BKB, tile.ti * BM, &full[s]);
-                    tma_load_2d(st + A_BYTES, mP, kt * BKB, tile.tj * BN, &full[s]);
+                    const uint32_t lead_full = cluster_addr(&full[s], 0);
+                    tma_load_2d_pair(st, mU, kt * BKB, (tile.ti + (int)rank) * BM, lead_full);
+                    tma_load_2d_pair(st + A_BYTES, mP, kt * BKB, tile.tj * BN + (int)rank * (BN / 2), lead_full);
                     if (++s == STAGES) {
                         s = 0;
                         ph ^= 1u;
@@ -449,17 +537,19 @@ action_tc_kernel(const TcArgs args) {
                 const int t = ring[slot];
                 mbar_arrive(&rempty[slot]);
                 if (t < 0) break;
+                if (rank != 0) continue;  // the leader issues the pair's MMAs
                 const TcTile tile = args.tiles[t];
                 int kt0, kt1;
                 k_range<FMT>(tile, args.sets[tile.set].N, kt0, kt1);
-                if (!ptx::mbar_wait_bounded(&tempty[b], bph ^ 1u, kWaitNs)) {
+                // both CTAs' epilogues have drained accumulator b
+                if (!mbar_wait_cl(&tempty[b], bph ^ 1u, kWaitNs)) {
                     bad = true;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t dt = tmem + b * BN;
                 for (int kt = kt0; kt < kt1; ++kt) {
-                    if (!ptx::mbar_wait_bounded(&full[s], ph, kWaitNs)) {
+                    if (!mbar_wait_cl(&full[s], ph, kWaitNs)) {
                         bad = true;
                         break;
                     }
@@ -474,14 +564,14 @@ action_tc_kernel(const TcArgs args) {
                         else
                             mma_f8(dt, ad, bd, (kt > kt0 || k > 0) ? 1u : 0u);
                     }
-                    mma_commit(&empty[s]);
+                    mma_commit_pair(&empty[s]);  // frees stage s in both CTAs
                     if (++s == STAGES) {
                         s = 0;
                         ph ^= 1u;
                     }
                 }
                 if (bad) break;
-                mma_commit(&tfull[b]);
+                mma_commit_pair(&tfull[b]);  // accumulator b complete in both CTAs
                 if (NACC == 2) b ^= 1u;
                 if (b == 0) bph ^= 1u;
             }
@@ -537,7 +627,7 @@ action_tc_kernel(const TcArgs args) {
             }
             const TcSetDesc S = args.sets[tile.set];
             const int64_t N = S.N;
-            const int64_t i = (int64_t)tile.ti * BM + r;
+            const int64_t i = (int64_t)(tile.ti + (int)rank) * BM + r;
             const int64_t J0 = (int64_t)tile.tj * BN;
             // the row's relation bits for this warp's columns of J0..J0+255, fetched before the wait
             uint64_t w4[4] = {0, 0, 0, 0};
@@ -557,7 +647,7 @@ action_tc_kernel(const TcArgs args) {
                 }
             }
             const double phi_i = (S.acc != nullptr && i < N) ? S.phi[i] : 0.0;
-            const bool ok = ptx::mbar_wait_bounded(&tfull[b], bph, kWaitNs);
+            const bool ok = mbar_wait_cl(&tfull[b], bph, kWaitNs);
             if (!__all_sync(0xffffffffu, ok)) {
                 bad = true;
                 break;
@@ -566,10 +656,10 @@ action_tc_kernel(const TcArgs args) {
             const uint32_t tbase = tmem + b * BN + ((uint32_t)(q * 32) << 16);
             const unsigned long long packed =
                 S.acc != nullptr
-                    ? epi_tile<true>(tbase, w4, i, J0, cR, cM, cW, args.hist, args.nbins, phi_i, S.acc, &tempty[b],
-                                     cb, ce)
+                    ? epi_tile<true>(tbase, w4, i, J0, cR, cM, cW, args.hist, args.nbins, phi_i, S.acc,
+                                     cluster_addr(&tempty[b], 0), cb, ce)
                     : epi_tile<false>(tbase, w4, i, J0, cR, cM, cW, args.hist, args.nbins, 0.0, nullptr,
-                                      &tempty[b], cb, ce);
+                                      cluster_addr(&tempty[b], 0), cb, ce);
             c0 += packed & 0xFFFFull;
             c1 += (packed >> 16) & 0xFFFFull;
             c2 += (packed >> 32) & 0xFFFFull;
@@ -582,11 +672,14 @@ action_tc_kernel(const TcArgs args) {
     if (bad) atomicExch(bad_flag, 1);
     tc_fence_before();
     __syncthreads();
+    // neither CTA frees TMEM or leaves while the other may still load into it, commit to its
+    // barriers or arrive on them
+    cluster_sync();
     if (*bad_flag && threadIdx.x == 0 && args.n_tiles > 0)
         atomicExch(&args.sets[args.tiles[0].set].counters[CNT_ERR], CNT_ERR_TIMEOUT);
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
                      : "memory");
     }
 }
@@ -610,7 +703,8 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
 // Output tiles of the upper triangle of one set, longest K first at the granularity
 // of super x super blocks (block pairs by decreasing extent bj - bi, then bi), and
 // column-major inside a block pair, so tiles sharing a P panel run together.  The
-// list is generated in that order directly and kept per (N, row range, block).
+// list is generated in that order directly and kept per (N, row range, block).  Each
+// entry is a pair tile: 256 rows (row tiles ti and ti + 1, ti even) by 256 columns.
 struct TileCache {
     std::mutex mu;
     std::map<std::tuple<int64_t, int64_t, int64_t, int>, std::vector<TcTile>> lists;
@@ -637,7 +731,9 @@ std::vector<TcTile> single_set_tiles(int64_t N, int64_t lo, int64_t hi, int supe
                     if (I1 <= lo || I0 >= hi) continue;
                     const int64_t J1 = std::min<int64_t>((int64_t)(tj + 1) * BN, N);
                     if (J1 <= I0 + 1) continue;
-                    tiles.push_back(TcTile{0, ti, tj, 0});
+                    // as a pair tile: row tiles ti & ~1 and (ti & ~1) + 1 go to the two CTAs of a pair
+                    const TcTile pt{0, ti & ~1, tj, 0};
+                    if (tiles.empty() || tiles.back().ti != pt.ti || tiles.back().tj != pt.tj) tiles.push_back(pt);
                 }
             }
         }
@@ -777,7 +873,7 @@ int tc_patch(const TcPlan &p, Arena &a) {
         D.U = ops + reinterpret_cast<uintptr_t>(D.U);
         D.P = ops + reinterpret_cast<uintptr_t>(D.P);
         int rc = encode_map(&maps[2 * s], D.U, D.N, D.kp, BM);
-        if (rc == CSG_OK) rc = encode_map(&maps[2 * s + 1], D.P, D.N, D.kp, BN);
+        if (rc == CSG_OK) rc = encode_map(&maps[2 * s + 1], D.P, D.N, D.kp, BN / 2);  // each CTA's half
         if (rc != CSG_OK) return rc;
     }
     return CSG_OK;
@@ -787,6 +883,19 @@ template <int FMT>
 static int tc_launch_fmt(const TcPlan &p, const Arena &a, cudaStream_t st) {
     const size_t smem = 1024 + STAGES * STAGE_BYTES + 512;
     CSG_CUDA_TRY(cudaFuncSetAttribute(action_tc_kernel<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // CTA pairs (clusters of two, one CTA per SM) that can be resident at once
+    int clusters = 0;
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2, 1, 1);
+        cfg.blockDim = dim3(THREADS, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        if (cudaOccupancyMaxActiveClusters(&clusters, (const void *)action_tc_kernel<FMT>, &cfg) != cudaSuccess ||
+            clusters < 1) {
+            cudaGetLastError();
+            clusters = 0;
+        }
+    }
     unsigned int *queues = a.scr<unsigned int>(p.s_queues);
     CSG_CUDA_TRY(cudaMemsetAsync(queues, 0, p.chunks.size() * sizeof(unsigned int), st));
     int dev = 0, sms = 0;
@@ -812,7 +921,8 @@ static int tc_launch_fmt(const TcPlan &p, const Arena &a, cudaStream_t st) {
             args.hist = p.hist;
             args.nbins = (long long)p.nbins;
             stage_begin(CSG_STAGE_ACTION, st);
-            action_tc_kernel<FMT><<<std::min(sms, c.n_tiles), THREADS, smem, st>>>(args);
+            const int pairs = std::min(clusters > 0 ? clusters : sms / 2, c.n_tiles);
+            action_tc_kernel<FMT><<<2 * pairs, THREADS, smem, st>>>(args);
             stage_end(CSG_STAGE_ACTION, st);
         }
         CSG_CUDA_TRY(cudaGetLastError());
