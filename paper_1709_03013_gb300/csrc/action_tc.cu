@@ -387,6 +387,44 @@ __device__ __forceinline__ unsigned long long epi_tile(uint32_t tbase, const uin
     return packed;
 }
 
+// The fp4 form's epilogue (one accumulator, so its drain is on the critical path): all 128
+// columns of this thread's half row come into registers with eight loads and one wait, the
+// accumulator is released at once, and the pairs are booked from registers afterwards.
+template <bool PHI>
+__device__ __forceinline__ unsigned long long epi_tile_all(uint32_t tbase, const uint64_t (&w4)[4], int64_t i,
+                                                           int64_t J0, unsigned long long &cR,
+                                                           unsigned long long &cM, unsigned long long &cW,
+                                                           unsigned long long *__restrict__ hist, long long nbins,
+                                                           double phi_i, double *__restrict__ acc_phi,
+                                                           uint32_t release, int cb) {
+    uint32_t v0[16], v1[16], v2[16], v3[16], v4[16], v5[16], v6[16], v7[16];
+    const uint32_t t = tbase + (uint32_t)cb;
+    TMEM_LD16(t, v0);
+    TMEM_LD16(t + 16u, v1);
+    TMEM_LD16(t + 32u, v2);
+    TMEM_LD16(t + 48u, v3);
+    TMEM_LD16(t + 64u, v4);
+    TMEM_LD16(t + 80u, v5);
+    TMEM_LD16(t + 96u, v6);
+    TMEM_LD16(t + 112u, v7);
+    const uint64_t wl = cb == 0 ? w4[0] : w4[2], wh = cb == 0 ? w4[1] : w4[3];
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    tc_fence_before();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive_cluster(release, 32);
+    unsigned long long packed = 0;
+    const int64_t j0 = J0 + cb;
+    book16<PHI>(v0, (uint32_t)wl & 0xFFFFu, j0, i, packed, cR, cM, cW, hist, nbins, phi_i, acc_phi);
+    book16<PHI>(v1, (uint32_t)(wl >> 16) & 0xFFFFu, j0 + 16, i, packed, cR, cM, cW, hist, nbins, phi_i, acc_phi);
+    book16<PHI>(v2, (uint32_t)(wl >> 32) & 0xFFFFu, j0 + 32, i, packed, cR, cM, cW, hist, nbins, phi_i, acc_phi);
+    book16<PHI>(v3, (uint32_t)(wl >> 48), j0 + 48, i, packed, cR, cM, cW, hist, nbins, phi_i, acc_phi);
+    book16<PHI>(v4, (uint32_t)wh & 0xFFFFu, j0 + 64, i, packed, cR, cM, cW, hist, nbins, phi_i, acc_phi);
+    book16<PHI>(v5, (uint32_t)(wh >> 16) & 0xFFFFu, j0 + 80, i, packed, cR, cM, cW, hist, nbins, phi_i, acc_phi);
+    book16<PHI>(v6, (uint32_t)(wh >> 32) & 0xFFFFu, j0 + 96, i, packed, cR, cM, cW, hist, nbins, phi_i, acc_phi);
+    book16<PHI>(v7, (uint32_t)(wh >> 48), j0 + 112, i, packed, cR, cM, cW, hist, nbins, phi_i, acc_phi);
+    return packed;
+}
+
 template <int FMT>
 __device__ __forceinline__ void k_range(const TcTile &t, int64_t N, int &kt0, int &kt1) {
     // K runs from the tile's first row to its last column (or N), in stages of KSTAGE
@@ -654,12 +692,18 @@ action_tc_kernel(const TcArgs args) {
             }
             tc_fence_after();
             const uint32_t tbase = tmem + b * BN + ((uint32_t)(q * 32) << 16);
-            const unsigned long long packed =
-                S.acc != nullptr
-                    ? epi_tile<true>(tbase, w4, i, J0, cR, cM, cW, args.hist, args.nbins, phi_i, S.acc,
-                                     cluster_addr(&tempty[b], 0), cb, ce)
-                    : epi_tile<false>(tbase, w4, i, J0, cR, cM, cW, args.hist, args.nbins, 0.0, nullptr,
-                                      cluster_addr(&tempty[b], 0), cb, ce);
+            const uint32_t release = cluster_addr(&tempty[b], 0);
+            unsigned long long packed;
+            if (FMT)
+                packed = S.acc != nullptr ? epi_tile_all<true>(tbase, w4, i, J0, cR, cM, cW, args.hist, args.nbins,
+                                                               phi_i, S.acc, release, cb)
+                                          : epi_tile_all<false>(tbase, w4, i, J0, cR, cM, cW, args.hist, args.nbins,
+                                                                0.0, nullptr, release, cb);
+            else
+                packed = S.acc != nullptr ? epi_tile<true>(tbase, w4, i, J0, cR, cM, cW, args.hist, args.nbins, phi_i,
+                                                           S.acc, release, cb, ce)
+                                          : epi_tile<false>(tbase, w4, i, J0, cR, cM, cW, args.hist, args.nbins, 0.0,
+                                                            nullptr, release, cb, ce);
             c0 += packed & 0xFFFFull;
             c1 += (packed >> 16) & 0xFFFFull;
             c2 += (packed >> 32) & 0xFFFFull;
