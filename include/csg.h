@@ -107,7 +107,11 @@ const char *csg_last_error(void);
  *   d=4: (t,x,y,z) = 2U-1 from the four words; the first attempt with
  *        |t| + sqrt((x*x + y*y) + z*z) <= 1 is kept (at most 256, else CSG_E_REJECT).
  * Sorting key: (t, u, e) for d=2, (t, e) for d=4.  1 <= N <= CSG_MAX_N.
- * The new set has coordinates but no bitmap until csg_link. */
+ * The new set has coordinates but no bitmap until csg_link.  The call enqueues the work
+ * on `stream` and returns without waiting; the set's memory comes from the stream-ordered
+ * pool on that stream.  An element that exhausts the rejection cap (probability below
+ * 1e-15 per element) is reported as CSG_E_REJECT by the next call that reads the set's
+ * results (csg_action and its variants, csg_export_*). */
 int csg_sprinkle(csg_ctx *ctx, int d, int64_t N, uint64_t seed, uint64_t seq, void *stream,
                  csg_set **out);
 
@@ -118,7 +122,7 @@ int csg_sprinkle(csg_ctx *ctx, int d, int64_t N, uint64_t seed, uint64_t seq, vo
  * (seed, seq), and theta = 2 pi U' from word 1.  Coordinates are stored as rows
  * (eta, theta, 0, 0), sorted by (eta, e).  Two elements are related when
  * pi - |pi - |d theta|| < |d eta|.  The set uses the 1+1 action (d = 2).
- * 0 < eta0 < pi/2, 1 <= N <= CSG_MAX_N. */
+ * 0 < eta0 < pi/2, 1 <= N <= CSG_MAX_N.  Enqueues and returns like csg_sprinkle. */
 int csg_sprinkle_desitter(csg_ctx *ctx, int64_t N, double eta0, uint64_t seed, uint64_t seq,
                           void *stream, csg_set **out);
 
@@ -206,7 +210,8 @@ int csg_serve_poll(csg_ctx *ctx, uint64_t ticket, csg_result *out, int timeout_m
 int csg_serve_cancel(csg_ctx *ctx, uint64_t ticket);
 
 /* Copy a set's sorted coordinates ([4][N] doubles) or bitmap (N*stride words) to
- * host memory; cap is the host buffer's capacity in elements. */
+ * host memory; cap is the host buffer's capacity in elements.  Waits for the device;
+ * returns CSG_E_REJECT if the set's sprinkle hit the rejection cap. */
 int csg_export_coords(csg_set *set, double *host, size_t cap_doubles);
 int csg_export_bitmap(csg_set *set, uint64_t *host, size_t cap_words);
 
@@ -214,6 +219,9 @@ int csg_export_bitmap(csg_set *set, uint64_t *host, size_t cap_words);
 int csg_set_info(const csg_set *set, int *d, int64_t *N, int64_t *stride_words,
                  const uint64_t **dev_rows, const double **dev_coords);
 
+/* Release a set.  Its device memory returns to the pool in stream order on the stream
+ * the set was created with; work that uses the set on other streams must be complete
+ * (or ordered before that stream) when this is called. */
 void csg_set_free(csg_set *set);
 
 /* Per-stage device timing (a tracing aid; Sec. 5 of the paper reports stage times).

@@ -24,7 +24,9 @@ void set_error(const char *fmt, ...) {
 
 // ------------------------------------------------------------------ sets
 
-int alloc_set(csg_ctx *ctx, int d, int64_t N, csg_set **out) {
+// Set memory comes from the stream-ordered pool on the creating stream (no device-wide
+// synchronisation on free); a word after the coordinates carries the sprinkle's error flag.
+int alloc_set(csg_ctx *ctx, int d, int64_t N, csg_set **out, cudaStream_t st) {
     if (!ctx || !out || (d != 2 && d != 4) || N < 1 || N > CSG_MAX_N) {
         set_error("bad set arguments (d=%d, N=%lld)", d, (long long)N);
         return CSG_E_INVAL;
@@ -44,11 +46,16 @@ int alloc_set(csg_ctx *ctx, int d, int64_t N, csg_set **out) {
         }
         ctx->used += s->bytes;
     }
-    cudaError_t e1 = cudaMalloc((void **)&s->coords, (size_t)N * 4 * sizeof(double));
-    cudaError_t e2 = cudaMalloc((void **)&s->rows, (size_t)N * s->stride * sizeof(uint64_t));
+    s->stream = st;
+    cudaError_t e1 = cudaMallocAsync((void **)&s->coords, (size_t)N * 4 * sizeof(double) + 256, st);
+    cudaError_t e2 = cudaMallocAsync((void **)&s->rows, (size_t)N * s->stride * sizeof(uint64_t), st);
+    if (e1 == cudaSuccess && e2 == cudaSuccess) {
+        s->err = reinterpret_cast<unsigned long long *>(s->coords + (size_t)N * 4);
+        e1 = cudaMemsetAsync(s->err, 0, sizeof(unsigned long long), st);
+    }
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
-        if (s->coords) cudaFree(s->coords);
-        if (s->rows) cudaFree(s->rows);
+        if (s->coords) cudaFreeAsync(s->coords, st);
+        if (s->rows) cudaFreeAsync(s->rows, st);
         {
             std::lock_guard<std::mutex> g(ctx->mu);
             ctx->used -= s->bytes;
@@ -66,12 +73,15 @@ int alloc_set(csg_ctx *ctx, int d, int64_t N, csg_set **out) {
     return CSG_OK;
 }
 
-void free_set(csg_set *s) {
+void free_set(csg_set *s, bool device_synced) {
     if (!s) return;
     csg_ctx *ctx = s->ctx;
     cudaSetDevice(ctx->device);
-    if (s->coords) cudaFree(s->coords);
-    if (s->rows) cudaFree(s->rows);
+    // stream-ordered on the creating stream; after a device-wide synchronisation (context
+    // teardown, where that stream may no longer exist) on the legacy stream instead
+    cudaStream_t st = device_synced ? nullptr : s->stream;
+    if (s->coords) cudaFreeAsync(s->coords, st);
+    if (s->rows) cudaFreeAsync(s->rows, st);
     {
         std::lock_guard<std::mutex> g(ctx->mu);
         ctx->used -= s->bytes;
@@ -141,7 +151,9 @@ void csg_finalize(csg_ctx *ctx) {
         std::lock_guard<std::mutex> g(ctx->mu);
         all.assign(ctx->sets.begin(), ctx->sets.end());
     }
-    for (csg_set *s : all) free_set(s);
+    cudaDeviceSynchronize();
+    for (csg_set *s : all) free_set(s, true);
+    cudaDeviceSynchronize();
     delete ctx;
 }
 
@@ -151,10 +163,10 @@ int csg_sprinkle(csg_ctx *ctx, int d, int64_t N, uint64_t seed, uint64_t seq, vo
     TimerScope ts(ctx);
     CSG_CUDA_TRY(cudaSetDevice(ctx->device));
     csg_set *s = nullptr;
-    int rc = alloc_set(ctx, d, N, &s);
+    int rc = alloc_set(ctx, d, N, &s, (cudaStream_t)stream);
     if (rc != CSG_OK) return rc;
-    SprinkleSpec sp{d, 0, N, seed, seq, s->coords, nullptr};
-    rc = sprinkle_sort_batch(&sp, 1, (cudaStream_t)stream, nullptr);
+    SprinkleSpec sp{d, 0, N, seed, seq, s->coords, s->err};
+    rc = sprinkle_sort_batch(&sp, 1, (cudaStream_t)stream, nullptr, /*sync=*/false);
     if (rc != CSG_OK) {
         free_set(s);
         return rc;
@@ -173,11 +185,11 @@ int csg_sprinkle_desitter(csg_ctx *ctx, int64_t N, double eta0, uint64_t seed, u
     TimerScope ts(ctx);
     CSG_CUDA_TRY(cudaSetDevice(ctx->device));
     csg_set *s = nullptr;
-    int rc = alloc_set(ctx, 2, N, &s);
+    int rc = alloc_set(ctx, 2, N, &s, (cudaStream_t)stream);
     if (rc != CSG_OK) return rc;
     s->geom = GEOM_DS2;
-    SprinkleSpec sp{2, GEOM_DS2, N, seed, seq, s->coords, nullptr, tan(eta0)};
-    rc = sprinkle_sort_batch(&sp, 1, (cudaStream_t)stream, nullptr);
+    SprinkleSpec sp{2, GEOM_DS2, N, seed, seq, s->coords, s->err, tan(eta0)};
+    rc = sprinkle_sort_batch(&sp, 1, (cudaStream_t)stream, nullptr, /*sync=*/false);
     if (rc != CSG_OK) {
         free_set(s);
         return rc;
@@ -205,7 +217,7 @@ int csg_set_from_coords(csg_ctx *ctx, int d, int64_t N, const double *host_coord
     }
     CSG_CUDA_TRY(cudaSetDevice(ctx->device));
     csg_set *s = nullptr;
-    int rc = alloc_set(ctx, d, N, &s);
+    int rc = alloc_set(ctx, d, N, &s, (cudaStream_t)stream);
     if (rc != CSG_OK) return rc;
     SprinkleSpec sp{d, 0, N, 0, 0, s->coords, nullptr};
     const double *hc[1] = {host_coords};
@@ -245,7 +257,7 @@ int csg_set_from_bitmap(csg_ctx *ctx, int d, int64_t N, const uint64_t *dev_rows
     }
     CSG_CUDA_TRY(cudaSetDevice(ctx->device));
     csg_set *s = nullptr;
-    int rc = alloc_set(ctx, d, N, &s);
+    int rc = alloc_set(ctx, d, N, &s, (cudaStream_t)stream);
     if (rc != CSG_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t wN = (N + 63) / 64;
@@ -391,6 +403,18 @@ int csg_run_batch(csg_ctx *ctx, int n, const int32_t *d, const int64_t *N, const
     return run_batch_graph(ctx, n, d, N, seed, seq, method, out, (cudaStream_t)stream);
 }
 
+// The sprinkle of a set reports a rejection-cap failure in the set's error word; calls
+// that read the set back check it after they synchronise.
+static int check_set_err(const csg_set *set) {
+    unsigned long long e = 0;
+    CSG_CUDA_TRY(cudaMemcpy(&e, set->err, sizeof e, cudaMemcpyDeviceToHost));
+    if (e != 0) {
+        set_error("sprinkle: an element hit the 256-attempt rejection cap");
+        return CSG_E_REJECT;
+    }
+    return CSG_OK;
+}
+
 int csg_export_coords(csg_set *set, double *host, size_t cap) {
     if (!set || !host || cap < (size_t)(4 * set->N)) {
         set_error("csg_export_coords: bad arguments");
@@ -399,7 +423,7 @@ int csg_export_coords(csg_set *set, double *host, size_t cap) {
     CSG_CUDA_TRY(cudaSetDevice(set->ctx->device));
     CSG_CUDA_TRY(cudaDeviceSynchronize());
     CSG_CUDA_TRY(cudaMemcpy(host, set->coords, 4 * set->N * sizeof(double), cudaMemcpyDeviceToHost));
-    return CSG_OK;
+    return check_set_err(set);
 }
 
 int csg_export_bitmap(csg_set *set, uint64_t *host, size_t cap) {
@@ -415,7 +439,7 @@ int csg_export_bitmap(csg_set *set, uint64_t *host, size_t cap) {
     CSG_CUDA_TRY(cudaDeviceSynchronize());
     CSG_CUDA_TRY(cudaMemcpy(host, set->rows, set->N * set->stride * sizeof(uint64_t),
                             cudaMemcpyDeviceToHost));
-    return CSG_OK;
+    return check_set_err(set);
 }
 
 int csg_set_info(const csg_set *set, int *d, int64_t *N, int64_t *stride_words,

@@ -89,9 +89,10 @@ SprinklePlan sprinkle_plan(const SprinkleSpec *specs, int n, Arena &a, bool from
                            size_t s_counters = (size_t)-1);
 void sprinkle_patch(const SprinklePlan &p, Arena &a);  // after allocation, before upload
 void sprinkle_launch(const SprinklePlan &p, const Arena &a, cudaStream_t st);
-// standalone: allocate, run, synchronise; host_coords (optional) replaces the sprinkle
+// standalone: allocate, run and (sync) synchronise; host_coords (optional) replaces the
+// sprinkle.  Without sync every spec must carry its own error word.
 int sprinkle_sort_batch(const SprinkleSpec *specs_host, int n, cudaStream_t st,
-                        const double *const *host_coords /*null: sprinkle*/);
+                        const double *const *host_coords /*null: sprinkle*/, bool sync = true);
 
 // Link a batch of sets (coords -> rows).
 struct LinkSpec {

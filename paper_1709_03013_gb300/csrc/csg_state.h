@@ -21,6 +21,8 @@ struct csg_set {
     bool from_bitmap = false;
     double coord_scale = 1.0;    // max(1, max |coordinate|)
     int geom = 0;                // 0: flat diamond of dimension d; 3: 1+1 de Sitter slab
+    cudaStream_t stream = nullptr;      // the stream the set was created on; its memory is freed there
+    unsigned long long *err = nullptr;  // device word after the coordinates: nonzero if the sprinkle failed
 };
 
 namespace csg {
@@ -43,8 +45,8 @@ struct csg_ctx {
 
 namespace csg {
 
-int alloc_set(csg_ctx *ctx, int d, int64_t N, csg_set **out);
-void free_set(csg_set *s);
+int alloc_set(csg_ctx *ctx, int d, int64_t N, csg_set **out, cudaStream_t st);
+void free_set(csg_set *s, bool device_synced = false);
 
 // Action for n linked sets; writes n host results and synchronises st.
 // Interval-count methods of the ABI and the tensor operand format each one selects.

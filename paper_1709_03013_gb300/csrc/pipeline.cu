@@ -46,6 +46,7 @@ struct FinRow {
     int32_t pad;
     int64_t N;
     const unsigned long long *counters;
+    const unsigned long long *set_err;  // the set's sprinkle error word, or null
 };
 
 __global__ void finalize_kernel(const FinRow *__restrict__ rows, int n, csg_result *__restrict__ out) {
@@ -54,7 +55,8 @@ __global__ void finalize_kernel(const FinRow *__restrict__ rows, int n, csg_resu
         const unsigned long long *c = F.counters;
         csg_result r;
         r.d = F.d;
-        r.status = c[CNT_ERR] == 0 ? CSG_OK : (c[CNT_ERR] == CNT_ERR_REJECT ? CSG_E_REJECT : CSG_E_TIMEOUT);
+        const unsigned long long e = (F.set_err != nullptr && *F.set_err != 0) ? CNT_ERR_REJECT : c[CNT_ERR];
+        r.status = e == 0 ? CSG_OK : (e == CNT_ERR_REJECT ? CSG_E_REJECT : CSG_E_TIMEOUT);
         r.N = F.N;
         r.R = c[CNT_R];
         for (int k = 0; k < 4; ++k) r.Nk[k] = c[CNT_N0 + k];
@@ -127,7 +129,7 @@ int build_seq(Seq &q, csg_set *const *sets, int n, int method, int64_t row_lo, i
         desc[s].row_hi = row_hi < 0 ? sets[s]->N : std::min<int64_t>(row_hi, sets[s]->N);
         desc[s].phi = phi;
         desc[s].acc = acc;
-        fin[s] = FinRow{sets[s]->d, 0, sets[s]->N, nullptr};
+        fin[s] = FinRow{sets[s]->d, 0, sets[s]->N, nullptr, sets[s]->err};
     }
     // split the sets between the two kernels (the tensor method sends small sets to the
     // popcount kernel when tuned to)
@@ -484,8 +486,13 @@ static int build_batch_graph(csg_ctx *ctx, int n, const int32_t *d, const int64_
     int rc = CSG_OK;
     for (int s = 0; s < n && rc == CSG_OK; ++s) {
         csg_set *x = nullptr;
-        rc = alloc_set(ctx, d[s], N[s], &x);
+        rc = alloc_set(ctx, d[s], N[s], &x, nullptr);
         if (rc == CSG_OK) g->sets.push_back(x);
+    }
+    // the sets' stream-ordered allocations are complete before any other stream uses them
+    if (rc == CSG_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) {
+        set_error("batch: set allocation failed");
+        rc = CSG_E_CUDA;
     }
     Tune tune;
     if (rc == CSG_OK && method != CSG_POPC) rc = autotune(ctx, g->sets.data(), n, d, N, seed, seq, method, &tune);

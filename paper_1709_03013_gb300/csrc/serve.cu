@@ -137,7 +137,7 @@ void worker_main(ServeState *S) {
                 N = S->reqs[batch[q]].N;
             }
             csg_set *x = nullptr;
-            rc = alloc_set(ctx, d, N, &x);
+            rc = alloc_set(ctx, d, N, &x, st);
             if (rc == CSG_OK) sets.push_back(x);
         }
         {

@@ -329,7 +329,7 @@ void sprinkle_launch(const SprinklePlan &p, const Arena &a, cudaStream_t st) {
 }
 
 int sprinkle_sort_batch(const SprinkleSpec *specs, int n, cudaStream_t st,
-                        const double *const *host_coords) {
+                        const double *const *host_coords, bool sync) {
     if (n <= 0) return CSG_OK;
     Arena a;
     SprinklePlan p = sprinkle_plan(specs, n, a, host_coords != nullptr);
@@ -359,6 +359,7 @@ int sprinkle_sort_batch(const SprinkleSpec *specs, int n, cudaStream_t st,
         cudaMemcpyAsync(&err_host, a.scr<unsigned long long>(p.s_err), sizeof err_host,
                         cudaMemcpyDeviceToHost, st);
     arena_free(a, st);
+    if (!sync) return rc;  // stream-ordered; each set's own error word carries a rejection
     cudaError_t se = cudaStreamSynchronize(st);
     if (rc == CSG_OK && se != cudaSuccess) {
         set_error("sprinkle/sort: %s", cudaGetErrorString(se));
