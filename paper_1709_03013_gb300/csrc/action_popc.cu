@@ -33,8 +33,9 @@
 namespace csg {
 namespace {
 
-constexpr int kWarps = 16;
+constexpr int kWarps = 32;
 constexpr int kThreads = kWarps * 32;
+constexpr int kMaxK = 4;  // group rows per pass over row j (1024 threads leave 64 registers a thread)
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s for a bulk copy to land
 
 struct Smem {
@@ -126,11 +127,11 @@ __device__ __forceinline__ void dispatch_rows(int cnt, uint32_t mask, const uint
         sweep_rows<1, PHI>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins, ctl);
     else if (cnt <= 2)
         sweep_rows<2, PHI>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins, ctl);
-    else if (cnt <= 4 || G <= 4) {
+    else if (cnt <= 4 || G <= 4 || kMaxK <= 4) {
         if constexpr (G >= 4)
             sweep_rows<4, PHI>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins, ctl);
     } else {
-        if constexpr (G >= 8)
+        if constexpr (G >= 8 && kMaxK >= 8)
             sweep_rows<8, PHI>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins, ctl);
     }
 }
@@ -237,15 +238,15 @@ action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict_
                 const int wj = (int)((j >> 6) - w0a);                 // last word, relative
                 const uint64_t lastmask = (1ull << (j & 63)) - 1ull;  // bits k < j
                 const uint64_t *__restrict__ bj = rows + j * stride + w0a;
-                // at most 8 rows per pass keeps the row slots and sums in registers
+                // at most kMaxK rows per pass keeps the row slots and sums in registers
                 uint32_t rest = mask;
                 while (rest) {
                     uint32_t part = rest;
-                    if (__popc(rest) > 8) {
+                    if (__popc(rest) > kMaxK) {
                         uint32_t t = rest;
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) t &= t - 1;
-                        part = rest & ~t;  // the lowest 8 rows
+                        for (int k = 0; k < kMaxK; ++k) t &= t - 1;
+                        part = rest & ~t;  // the lowest kMaxK rows
                     }
                     rest &= ~part;
                     dispatch_rows<G, PHI>(__popc(part), part, A, pitch, bj, wj, lastmask, lane, j, i0, cnt, hist, nbins,
