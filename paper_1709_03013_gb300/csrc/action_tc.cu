@@ -319,31 +319,71 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
           "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])             \
         : "r"(addr))
 
+// The value of the 16-column chunk at runtime column u (0..15), by a select tree: registers
+// cannot be indexed at run time without going through local memory.
+__device__ __forceinline__ uint32_t pick16(const uint32_t (&v)[16], int u) {
+    const bool s1 = u & 1, s2 = u & 2, s4 = u & 4, s8 = u & 8;
+    const uint32_t a0 = s1 ? v[1] : v[0], a1 = s1 ? v[3] : v[2], a2 = s1 ? v[5] : v[4], a3 = s1 ? v[7] : v[6];
+    const uint32_t a4 = s1 ? v[9] : v[8], a5 = s1 ? v[11] : v[10], a6 = s1 ? v[13] : v[12], a7 = s1 ? v[15] : v[14];
+    const uint32_t b0 = s2 ? a1 : a0, b1 = s2 ? a3 : a2, b2 = s2 ? a5 : a4, b3 = s2 ? a7 : a6;
+    const uint32_t c0 = s4 ? b1 : b0, c1 = s4 ? b3 : b2;
+    return s8 ? c1 : c0;
+}
+
+// Books the pair (i, jbase + u) whose accumulator value (an exact integer in fp32) is x.
+template <bool PHI>
+__device__ __forceinline__ void book1(uint32_t x, int64_t j, unsigned long long &packed, unsigned long long &cM,
+                                      unsigned long long *__restrict__ hist, long long nbins, double phi_i,
+                                      double *__restrict__ acc_phi) {
+    const uint32_t m = __float2uint_rn(__uint_as_float(x));
+    cM += m;
+    if (m < 4u) packed += 1ull << (16u * m);
+    if (hist != nullptr && (long long)m < nbins) atomicAdd(&hist[m], 1ull);
+    if (PHI && m < 3u) atomicAdd(&acc_phi[j], (m == 1u ? -2.0 : 1.0) * phi_i);
+}
+
 // Books the pairs (i, j) of one 16-column chunk whose relation bits are set in `bits`
-// (column u of the chunk is element jbase + u).  PHI adds, for pairs with m <= 2, c_m phi[i]
-// to the d'Alembertian sums of element j (Eq. b_local).
+// (column u of the chunk is element jbase + u).  Without a full histogram the sum of m over
+// the chunk is taken in fp32 (exact: at most 16 integers below 2^18) and only the pairs with
+// m < 4, found by a compare on the fp32 value, go through the counters one by one; with a
+// histogram every pair does.  PHI adds, for pairs with m <= 2, c_m phi[i] to the
+// d'Alembertian sums of element j (Eq. b_local).
 template <bool PHI>
 __device__ __forceinline__ void book16(const uint32_t (&v)[16], uint32_t bits, int64_t jbase, int64_t i,
                                        unsigned long long &packed, unsigned long long &cR,
                                        unsigned long long &cM, unsigned long long &cW,
                                        unsigned long long *__restrict__ hist, long long nbins, double phi_i,
                                        double *__restrict__ acc_phi) {
-    if (!bits) return;
+    if (!__any_sync(0xffffffffu, bits != 0u)) return;
     // R and W of the chunk from bit counts: sum over set bits u of (jbase + u - i - 1)
     const unsigned pc = __popc(bits);
     const unsigned su = __popc(bits & 0xAAAAu) + 2u * __popc(bits & 0xCCCCu) + 4u * __popc(bits & 0xF0F0u) +
                         8u * __popc(bits & 0xFF00u);
     cR += pc;
     cW += (unsigned long long)pc * (unsigned long long)(jbase - i - 1) + su;
+    if (hist != nullptr) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+            if (bits >> u & 1u) book1<PHI>(v[u], jbase + u, packed, cM, hist, nbins, phi_i, acc_phi);
+        return;
+    }
+    float sum = 0.f;
+    uint32_t small = 0;
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
         if (bits >> u & 1u) {
-            const uint32_t m = __float2uint_rn(__uint_as_float(v[u]));
-            cM += m;
-            if (m < 4u) packed += 1ull << (16u * m);
-            if (hist != nullptr && (long long)m < nbins) atomicAdd(&hist[m], 1ull);
-            if (PHI && m < 3u) atomicAdd(&acc_phi[jbase + u], (m == 1u ? -2.0 : 1.0) * phi_i);
+            const float x = __uint_as_float(v[u]);
+            sum += x;
+            if (x < 4.0f) small |= 1u << u;
         }
+    }
+    cM += (unsigned long long)__float2uint_rn(sum);
+    while (small) {
+        const int u = __ffs(small) - 1;
+        small &= small - 1;
+        const uint32_t m = __float2uint_rn(__uint_as_float(pick16(v, u)));
+        packed += 1ull << (16u * m);
+        if (PHI && m < 3u) atomicAdd(&acc_phi[jbase + u], (m == 1u ? -2.0 : 1.0) * phi_i);
     }
 }
 
