@@ -130,13 +130,26 @@ __global__ void sprinkle_keys_kernel(const SetRow *__restrict__ sets, const int6
             c0 = c1 = c2 = c3 = 0.0;
             for (int a = 0; a < 256 && !found; ++a) {
                 U64x4 r = philox4x64_10((uint64_t)e, (uint64_t)a, 0, 0, S.seed, S.seq);
+                // fp32 screen: the top 24 bits of each word give the coordinate within 2^-23,
+                // and the screened sum is within 2e-6 of the fp64 one; attempts closer than
+                // 4e-6 to the boundary take the exact fp64 test (the decision is the fp64 one)
+                const float tf = __fmaf_rn((float)(uint32_t)(r.w[0] >> 40), 0x1.0p-23f, -1.0f);
+                const float xf = __fmaf_rn((float)(uint32_t)(r.w[1] >> 40), 0x1.0p-23f, -1.0f);
+                const float yf = __fmaf_rn((float)(uint32_t)(r.w[2] >> 40), 0x1.0p-23f, -1.0f);
+                const float zf = __fmaf_rn((float)(uint32_t)(r.w[3] >> 40), 0x1.0p-23f, -1.0f);
+                const float sf = fabsf(tf) + sqrtf(__fmaf_rn(xf, xf, __fmaf_rn(yf, yf, zf * zf)));
+                if (sf > 1.0f + 4e-6f) continue;
                 double t = __dsub_rn(__dmul_rn(2.0, unit53(r.w[0])), 1.0);
                 double x = __dsub_rn(__dmul_rn(2.0, unit53(r.w[1])), 1.0);
                 double y = __dsub_rn(__dmul_rn(2.0, unit53(r.w[2])), 1.0);
                 double z = __dsub_rn(__dmul_rn(2.0, unit53(r.w[3])), 1.0);
-                double rr = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)),
-                                                 __dmul_rn(z, z)));
-                if (__dadd_rn(fabs(t), rr) <= 1.0) {
+                bool accept = sf < 1.0f - 4e-6f;
+                if (!accept) {
+                    double rr = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)),
+                                                     __dmul_rn(z, z)));
+                    accept = __dadd_rn(fabs(t), rr) <= 1.0;
+                }
+                if (accept) {
                     c0 = t;
                     c1 = x;
                     c2 = y;
