@@ -141,44 +141,50 @@ __device__ __forceinline__ void put64(uint8_t *dst, uint64_t m) {
     }
 }
 
-// One thread per packed word of the sets [set_lo, set_lo + nset): writes the operand
-// bytes of U and of P the word covers (64 fp8 bytes or 32 packed fp4 bytes each), where
-// the product reads them.  FMT 0: fp8 e4m3, 128 elements per stage; FMT 1: fp4 e2m1, 256.
+// One warp per operand row of the sets [set_lo, set_lo + nset) (rows numbered across the
+// sets, rstarts[s] = first row of set s): the lanes walk the row's words and write the
+// operand bytes (64 fp8 bytes or 32 packed fp4 bytes per word) where the product reads them:
+// U row i from the first column of its pair tile, 2*BM*floor(i/(2*BM)) (a whole number of
+// stages in either format), P row i up to column BN*(floor(i/BN)+1).
+// FMT 0: fp8 e4m3, 128 elements per stage; FMT 1: fp4 e2m1, 256.
 template <int FMT>
-__global__ void expand_kernel(const TcSetDesc *__restrict__ sets, const int64_t *__restrict__ wstarts,
-                              int set_lo, int nset, int64_t total) {
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int ls = find_set(wstarts, nset, g);
-        const TcSetDesc S = sets[set_lo + ls];
+__global__ void expand_kernel(const TcSetDesc *__restrict__ sets, const int64_t *__restrict__ rstarts,
+                              int set_lo, int nset, int64_t total_rows) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t gr = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); gr < total_rows; gr += warps) {
+        const int ls = find_set(rstarts, nset, gr);  // warp-uniform
+        const TcSetDesc &S = sets[set_lo + ls];
+        const int64_t i = gr - rstarts[ls];
         const int64_t wpr = (FMT ? 2 * S.kp : S.kp) / 64;  // words per operand row
-        const int64_t gl = g - wstarts[ls];
-        const int64_t i = gl / wpr, w = gl - i * wpr;
-        const int64_t k0 = w * 64;
-        const uint64_t word = S.rows[i * S.stride + w];
-        // U row i is read from the first column of its pair tile, 2*BM*floor(i/(2*BM)) (a
-        // whole number of stages in either format); P row i up to column BN*(floor(i/BN)+1)
-        if (k0 + 64 > (i / (2 * BM)) * (2 * BM)) {
-            uint64_t m = word;
+        const uint64_t *__restrict__ row = S.rows + i * S.stride;
+        uint8_t *__restrict__ urow = S.U + i * S.kp;
+        uint8_t *__restrict__ prow = S.P + i * S.kp;
+        const int64_t u0 = (i / (2 * BM)) * (2 * BM) / 64;                  // first U word read
+        const int64_t p1 = min(wpr, (i / BN + 1) * BN / 64);                // P words read: [0, p1)
+        for (int64_t w = u0 + lane; w < wpr; w += 32) {
+            const int64_t k0 = w * 64;
+            uint64_t m = __ldg(row + w);
             if (k0 + 63 <= i)
                 m = 0;
             else if (k0 <= i)
                 m &= ~((2ull << (i - k0)) - 1ull);  // keep k > i
             if (FMT)
-                put64_fp4(S.U + i * S.kp + k0 / 2, m);
+                put64_fp4(urow + k0 / 2, m);
             else
-                put64(S.U + i * S.kp + k0, m);
+                put64(urow + k0, m);
         }
-        if (k0 < (i / BN + 1) * BN) {
-            uint64_t m = word;
+        for (int64_t w = lane; w < p1; w += 32) {
+            const int64_t k0 = w * 64;
+            uint64_t m = __ldg(row + w);
             if (k0 >= i)
                 m = 0;
             else if (k0 + 63 >= i)
                 m &= (1ull << (i - k0)) - 1ull;  // keep k < i
             if (FMT)
-                put64_fp4(S.P + i * S.kp + k0 / 2, m);
+                put64_fp4(prow + k0 / 2, m);
             else
-                put64(S.P + i * S.kp + k0, m);
+                put64(prow + k0, m);
         }
     }
 }
@@ -908,12 +914,12 @@ TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned
     p.s_ops = a.reserve((size_t)max_chunk);
     p.s_queues = a.reserve(p.chunks.size() * sizeof(unsigned int));
     for (TcPlan::Chunk &c : p.chunks) {
-        std::vector<int64_t> wstarts;
+        std::vector<int64_t> rstarts;  // first operand row of each set of the chunk
         int64_t total = 0;
         std::vector<TcTile> tiles;
         for (int s = c.set_lo; s < c.set_hi; ++s) {
-            wstarts.push_back(total);
-            total += desc[s].N * ((fmt ? 2 * desc[s].kp : desc[s].kp) / 64);
+            rstarts.push_back(total);
+            total += desc[s].N;
         }
         if (c.set_hi - c.set_lo == 1) {
             const TcSetDesc &D = desc[c.set_lo];
@@ -939,8 +945,8 @@ TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned
             *rc = CSG_E_INVAL;
             return p;
         }
-        c.words = total;
-        c.t_wstarts = a.put(wstarts.data(), wstarts.size() * sizeof(int64_t));
+        c.rows = total;
+        c.t_rstarts = a.put(rstarts.data(), rstarts.size() * sizeof(int64_t));
         c.n_tiles = (int)tiles.size();
         c.t_tiles = a.put(tiles.data(), tiles.size() * sizeof(TcTile));
     }
@@ -988,11 +994,11 @@ static int tc_launch_fmt(const TcPlan &p, const Arena &a, cudaStream_t st) {
     const TcSetDesc *d_sets = a.tab<TcSetDesc>(p.t_sets);
     for (size_t ci = 0; ci < p.chunks.size(); ++ci) {
         const TcPlan::Chunk &c = p.chunks[ci];
-        if (c.words > 0) {
-            const int blocks = (int)std::min<int64_t>((c.words + 255) / 256, (int64_t)sms * 32);
+        if (c.rows > 0) {
+            const int blocks = (int)std::min<int64_t>((c.rows + 7) / 8, (int64_t)sms * 16);  // a warp per row
             stage_begin(CSG_STAGE_EXPAND, st);
-            expand_kernel<FMT><<<blocks, 256, 0, st>>>(d_sets, a.tab<int64_t>(c.t_wstarts), c.set_lo,
-                                                       c.set_hi - c.set_lo, c.words);
+            expand_kernel<FMT><<<blocks, 256, 0, st>>>(d_sets, a.tab<int64_t>(c.t_rstarts), c.set_lo,
+                                                       c.set_hi - c.set_lo, c.rows);
             stage_end(CSG_STAGE_EXPAND, st);
         }
         if (c.n_tiles > 0) {

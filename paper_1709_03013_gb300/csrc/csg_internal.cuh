@@ -150,8 +150,8 @@ struct TcSetDesc {
 struct TcPlan {
     struct Chunk {
         int set_lo = 0, set_hi = 0, n_tiles = 0;
-        int64_t words = 0;
-        size_t t_wstarts = 0, t_tiles = 0;
+        int64_t rows = 0;  // operand rows the expand pass writes (sum of N)
+        size_t t_rstarts = 0, t_tiles = 0;
     };
     std::vector<int> slot;  // counter slot of each set (empty: identity)
     int n_sets = 0;
