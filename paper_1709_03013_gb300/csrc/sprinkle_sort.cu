@@ -178,7 +178,9 @@ __device__ __forceinline__ bool key_less(uint64_t a1, uint64_t a2, uint32_t ai, 
     return ai < bi;
 }
 
-// Rank each key of a chunk among the chunk's keys (all distinct) and scatter.
+// Sort each chunk of kChunk keys in shared memory with a bitonic network (the keys of a
+// set are all distinct, so the order is the same total order the rank would give); a
+// partial last chunk is padded with keys above every real one.
 __global__ void __launch_bounds__(kSortThreads)
 chunk_sort_kernel(const SetRow *__restrict__ sets, const int64_t *__restrict__ chunk_starts, int n,
                   Keys in, Keys out) {
@@ -190,20 +192,39 @@ chunk_sort_kernel(const SetRow *__restrict__ sets, const int64_t *__restrict__ c
     const int64_t base = S.off + c * kChunk;
     const int64_t rem = S.N - c * kChunk;
     const int len = rem < kChunk ? (int)rem : kChunk;
-    for (int t = threadIdx.x; t < len; t += kSortThreads) {
-        s1[t] = in.k1[base + t];
-        s2[t] = in.k2[base + t];
-        si[t] = in.idx[base + t];
+    for (int t = threadIdx.x; t < kChunk; t += kSortThreads) {
+        const bool real = t < len;
+        s1[t] = real ? in.k1[base + t] : ~0ull;
+        s2[t] = real ? in.k2[base + t] : ~0ull;
+        si[t] = real ? in.idx[base + t] : 0xFFFFFFFFu;
     }
     __syncthreads();
+    for (int k = 2; k <= kChunk; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < kChunk; t += kSortThreads) {
+                const int u = t ^ j;
+                if (u > t) {
+                    const bool up = (t & k) == 0;  // this pair's half of the network sorts ascending
+                    const bool gt = key_less(s1[u], s2[u], si[u], s1[t], s2[t], si[t]);
+                    if (gt == up) {
+                        const uint64_t a1 = s1[t], a2 = s2[t];
+                        const uint32_t ai = si[t];
+                        s1[t] = s1[u];
+                        s2[t] = s2[u];
+                        si[t] = si[u];
+                        s1[u] = a1;
+                        s2[u] = a2;
+                        si[u] = ai;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
     for (int t = threadIdx.x; t < len; t += kSortThreads) {
-        const uint64_t a1 = s1[t], a2 = s2[t];
-        const uint32_t ai = si[t];
-        int rank = 0;
-        for (int q = 0; q < len; ++q) rank += key_less(s1[q], s2[q], si[q], a1, a2, ai);
-        out.k1[base + rank] = a1;
-        out.k2[base + rank] = a2;
-        out.idx[base + rank] = ai;
+        out.k1[base + t] = s1[t];
+        out.k2[base + t] = s2[t];
+        out.idx[base + t] = si[t];
     }
 }
 

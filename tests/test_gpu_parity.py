@@ -426,3 +426,31 @@ def test_tensor_formats_hist_bitmaps_batch_rows(ctx, csg, fmt):
     for st, r, (d, n, k) in zip(sets, got, [(2, 500, 0), (4, 1700, 1), (2, 2600, 2), (4, 90, 3)]):
         _check_result(r, oracle.action(oracle.link(d, oracle.sprinkle_sorted(d, n, 40 + k, 1))), d, n)
         st.free()
+
+
+# ------------------------------------------------------------ stream-ordered sets
+
+def test_sets_on_side_streams(ctx, csg):
+    # sprinkle enqueues and returns; set memory is allocated and freed in stream order on the
+    # creating stream.  Sets made, used and freed back to back on two side streams, with
+    # their memory recycled between rounds, must give the oracle's counts every time.
+    import torch
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    cases = [(4, 3000, 5), (2, 5000, 6), (4, 1200, 7), (2, 700, 8)]
+    wants = {k: oracle.action(oracle.link(d, oracle.sprinkle_sorted(d, N, seed, 0))) for k, (d, N, seed) in enumerate(cases)}
+    for rnd in range(3):
+        for k, (d, N, seed) in enumerate(cases):
+            st = streams[(k + rnd) % 2]
+            s = ctx.sprinkle(d, N, seed, 0, stream=st)
+            s.link(stream=st)
+            for method in (csg.POPC, csg.TC):
+                _check_result(s.action(method, stream=st), wants[k], d, N)
+            s.free()
+    # a set made on one stream and read on another after an explicit wait
+    s = ctx.sprinkle(4, 2000, 9, 0, stream=streams[0])
+    s.link(stream=streams[0])
+    streams[1].wait_stream(streams[0])
+    _check_result(s.action(csg.TC, stream=streams[1]),
+                  oracle.action(oracle.link(4, oracle.sprinkle_sorted(4, 2000, 9, 0))), 4, 2000)
+    torch.cuda.synchronize()
+    s.free()
