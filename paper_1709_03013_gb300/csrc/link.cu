@@ -3,31 +3,49 @@
 // staged in shared memory, dense output).
 //
 // A CTA owns a 256 x 256 tile (row block bi <= column block bj) of the upper
-// triangle.  Thread r evaluates the 256 pairs (R+r, K+c) with column coordinates
-// read from shared memory (broadcast) and keeps the four row words in registers.
-// The lower triangle is the same tile transposed: a warp ballot over its 32 rows
-// per column gives 32 bits of the mirrored row, staged in shared memory and
-// written as 32-byte row segments.  Column blocks run to the row stride, so every
-// word of every row -- padding included -- is written exactly once and no memset
-// is needed.
+// triangle.  Warp w computes the 64-column word q = w / 2 of the tile for 4 x 32 rows
+// (rows 32 (w & 1) + 64 s + lane, s = 0..3), so the column coordinates it reads from
+// shared memory are the same for all of its lanes (broadcast 16-byte loads, one load
+// per coordinate for four columns, used for four rows).  Row words are staged in shared
+// memory and written as 32-byte row segments.  The lower triangle is the same tile
+// transposed: a five-step warp-shuffle transpose per 32 x 32 block, staged in shared
+// memory and written the same way.  Column blocks run to the row stride, so every word
+// of every row -- padding included -- is written exactly once and no memset is needed.
 //
-// d=4 decisions are the exact IEEE double ones (t_k > t_i and dt*dt > (dx*dx +
-// dy*dy) + dz*dz, separately rounded).  A float screen settles almost every pair
-// first: with coordinates in [-1, 1], rounding them to float moves each difference
-// by at most 4.0001 * 2^-24 and each square by at most 16.004 * 2^-24; the four
-// fused multiply-adds that form dt^2 - ((dx^2 + dy^2) + dz^2) add at most
-// 4 * 4.01 * 2^-24, so the float value is within 80.1 * 2^-24 (< 4.8e-6) of the real
-// one, and the double expression within 40 * 2^-53 of it.  A float difference
-// beyond +-1e-5 therefore fixes the double decision.
-// Pairs inside the margin are decided in double.
+// Each pair is settled by a float screen, and the few pairs the screen cannot settle are
+// decided exactly in double, so the bitmap equals the one of the exact (IEEE double)
+// predicate:
 //
-// The 1+1 de Sitter slab (Sec. 5.1) relates two elements when the shorter arc between
-// their angles is below |d eta|, i.e. pi - |pi - |d theta|| < |d eta| in double.  With
-// |eta| < pi/2 and theta in [0, 2 pi), the float form of |d eta| minus that arc is within
-// 2.6e-6 of the real value, so the same 1e-5 screen applies.  Every error term scales with the
-// square of the coordinate range, so sets whose coordinates exceed 1 in magnitude
-// use the margin 1e-5 * max|coordinate|^2 (coordinates are limited to 1e15, far
-// below float overflow of the squares).
+// d=4 (flat diamond): related iff t_k > t_i and dt*dt > (dx*dx + dy*dy) + dz*dz in
+// double, the elements time-sorted so that k > i.  The screen evaluates the interval in
+// its expanded form,
+//     e = p - h_k - h_i = -s^2 / 2,   p = t_k t_i - x_k x_i - y_k y_i - z_k z_i,
+//     h = (t^2 - x^2 - y^2 - z^2) / 2 (formed in double, rounded once to float),
+// as one float add and four fused multiply-adds on packed pairs of columns
+// (f32x2), and takes the relation from the sign bit of e (a funnel shift packs 32
+// sign bits into a word).  With every |coordinate| <= S (S >= 1), u = 2^-24: rounding
+// the coordinates to float moves the four products by at most 2u * 4 S^2; |h| <= 1.5 S^2,
+// so rounding the two h moves e by at most 3u S^2; the first add (|sum| <= 3 S^2) rounds by
+// at most 3u S^2 and the four fused multiply-adds (partial sums below 4, 5, 6, 7 S^2) by
+// 22u S^2.  So |e + s^2/2| <= 36u S^2 < 2.2e-6 S^2 (plus terms of order u^2), the double
+// predicate is within 1e-14 S^2 of the real one, and |e| > 3e-6 S^2 fixes the double
+// decision.  A word whose smallest |e| is within that margin is redone pair by pair, and
+// only its pairs inside the margin are evaluated in double.
+//
+// d=2 (flat diamond): related iff u_i < u_k and v_i < v_k (light-cone coordinates) in
+// double.  Rounding to float keeps order (x <= y => fl(x) <= fl(y)) and the float
+// difference of two floats is zero only if they are equal, so e = max(U_i - U_k,
+// V_i - V_k) < 0 means related, e > 0 unrelated, and e == 0 (a float tie) is decided
+// in double.  -0 is folded onto +0 first, so that equal values give e = +0.
+//
+// 1+1 de Sitter slab (Sec. 5.1): related when the shorter arc between the angles is below
+// |d eta|, i.e. pi - |pi - |d theta|| < |d eta| in double.  With |eta| < pi/2 and theta in
+// [0, 2 pi), the float form of |d eta| minus that arc is within 2.6e-6 of the real value,
+// so a float difference beyond +-1e-5 fixes the decision; this geometry is evaluated
+// pair by pair.
+//
+// Coordinates are limited to 1e15 in magnitude (checked where sets are made), far below
+// float overflow of every product and sum above.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -38,18 +56,25 @@ namespace {
 
 constexpr int kTile = 256;      // rows and columns per tile
 constexpr int kTileWords = 4;   // 64-bit words per tile row
+constexpr int kRowsPer = 4;     // rows per thread (one 64-column word each)
+constexpr int kLinkMinBlocks = 4;  // resident CTAs per SM the register budget allows
 
 struct LinkRow {
-    int32_t d;  // 2 or 4
+    int32_t d;  // 2, 4 or GEOM_DS2
     int32_t pad;
     int64_t N, stride;
     const double *coords;
     uint64_t *rows;
     int64_t tile_off;
     int64_t nb, nbc;  // row blocks, column blocks
-    float screen;     // d=4 float-screen margin: 1e-5 * max(1, max |coordinate|)^2
+    int64_t eoff;     // first element of the set within its geometry's elements
+    int64_t foff;     // first float of the set's screen values (kFloats[D] rows of N)
+    float margin;     // float-screen margin: d=4 4e-6 S^2 on e, de Sitter 1e-5, d=2 0
     float pad2;
 };
+
+// float screen values per element: d=4 T, X, Y, Z, -H; d=2 U, V; de Sitter eta, theta
+__host__ __device__ constexpr int screen_floats(int d) { return d == 4 ? 5 : 2; }
 
 __device__ __forceinline__ int find_set(const int64_t *__restrict__ starts, int n, int64_t g) {
     int lo = 0, hi = n - 1;
@@ -68,13 +93,30 @@ __device__ __forceinline__ int64_t tiles_before(int64_t b, int64_t nbc) {
     return b * nbc - b * (b - 1) / 2;
 }
 
-// order-preserving encoding of a double (no NaN); -0 is folded onto +0, so that
-// integer order equals IEEE order
-__device__ __forceinline__ uint64_t order_key(double x) {
-    if (x == 0.0) x = 0.0;
-    uint64_t b = (uint64_t)__double_as_longlong(x);
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+// packed pairs of floats (f32x2): low half = first column, high half = second
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
 }
+__device__ __forceinline__ void unpack2(uint64_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t fadd2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// shift the sign bit of e in at the bottom of acc
+__device__ __forceinline__ uint32_t push_sign(float e, uint32_t acc) {
+    return __funnelshift_l(__float_as_uint(e), acc, 1);
+}
+__device__ __forceinline__ float fold_zero(float x) { return x == 0.f ? 0.f : x; }
 
 // 1+1 de Sitter slab (Sec. 5.1): related iff pi - |pi - |d theta|| < |d eta| in double
 __device__ __forceinline__ bool exact_ds(double ei, double thi, double ek, double thk) {
@@ -105,67 +147,195 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
     return x;
 }
 
-// One 64-column word of row i: bit b set iff i and column K + q*64 + b are related.
-// FULL: every column of the word is a valid later column (no bounds checks).
-template <int D, bool FULL>
-__device__ __forceinline__ uint64_t link_word(int q, int c0, int ncol, const uint64_t (*ck)[kTile],
-                                              const float4 *cf4, const double (*cd)[kTile], uint64_t ui,
-                                              uint64_t vi, float tf, float xf, float yf, float zf,
-                                              double ti, double xi, double yi, double zi, float screen) {
-    uint64_t acc = 0, amb = 0;
+// Screen values of one element from its double coordinates (rounded once to float):
+// d=4 T, X, Y, Z, -H with H = fl(h), h = (t^2 - x^2 - y^2 - z^2) / 2 formed in double;
+// d=2 U, V with -0 folded onto +0; de Sitter eta, theta.
+template <int D>
+__device__ __forceinline__ void screen_values(const double *v, float *f) {
+    if (D == 2) {
+        f[0] = fold_zero(__double2float_rn(v[2]));
+        f[1] = fold_zero(__double2float_rn(v[3]));
+    } else if (D == 4) {
 #pragma unroll
+        for (int a = 0; a < 4; ++a) f[a] = __double2float_rn(v[a]);
+        f[4] = -__double2float_rn(0.5 * (v[0] * v[0] - ((v[1] * v[1] + v[2] * v[2]) + v[3] * v[3])));
+    } else {
+        f[0] = __double2float_rn(v[0]);
+        f[1] = __double2float_rn(v[1]);
+    }
+}
+
+// Writes every element's screen values once per set (the tiles then read floats only):
+// F[foff + a N + e] = value a of element e.
+template <int D>
+__global__ void __launch_bounds__(256)
+link_screen_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ estarts, int n, int64_t E,
+                   float *__restrict__ F) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= E) return;
+    const LinkRow &S = sets[find_set(estarts, n, g)];
+    const int64_t e = g - S.eoff, N = S.N;
+    double v[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) v[a] = S.coords[a * N + e];
+    float f[5];
+    screen_values<D>(v, f);
+#pragma unroll
+    for (int a = 0; a < screen_floats(D); ++a) F[S.foff + a * N + e] = f[a];
+}
+
+// The double decision for tile row rt and tile column c (Sec. 2.2; d=4 and d=2 in the
+// time order of the set, de Sitter on the cylinder).  rd, cd: the tile's row and column
+// coordinates in double (d=4 t, x, y, z; d=2 u, v; de Sitter eta, theta).
+template <int D>
+__device__ __forceinline__ bool exact_pair(const double (*rd)[kTile], const double (*cd)[kTile], int rt, int c) {
+    if (D == 2) return rd[0][rt] < cd[0][c] && rd[1][rt] < cd[1][c];
+    if (D == 4) return exact4(rd[0][rt], rd[1][rt], rd[2][rt], rd[3][rt], cd[0][c], cd[1][c], cd[2][c], cd[3][c]);
+    return exact_ds(rd[0][rt], rd[1][rt], cd[0][c], cd[1][c]);
+}
+
+// One 64-column word of tile row rt evaluated pair by pair: bit b set iff the row and
+// column 64 q + b are related; columns outside [c0, ncol) stay 0.  Used for the words on
+// and beside the diagonal, the ragged last column block and the de Sitter slab.  cf: the
+// tile's column screen values (d=2 negated); Fs: the set's screen values (row i's read).
+template <int D>
+__device__ __noinline__ uint64_t word_by_pair(int q, int c0, int ncol, const float (*cf)[kTile],
+                                              const double (*rd)[kTile], const double (*cd)[kTile], int rt,
+                                              const float *__restrict__ Fs, int64_t N, int64_t i, float m) {
+    float f[5];
+#pragma unroll
+    for (int a = 0; a < screen_floats(D); ++a) f[a] = Fs[a * N + i];
+    uint64_t acc = 0;
     for (int b = 0; b < 64; ++b) {
         const int c = q * 64 + b;
-        if (!FULL && (c < c0 || c >= ncol)) continue;
+        if (c < c0 || c >= ncol) continue;
+        bool rel;
         if (D == 2) {
-            if ((ui < ck[0][c]) & (vi < ck[1][c])) acc |= 1ull << b;
-        } else if (D == GEOM_DS2) {
+            // cf holds -U_k, -V_k
+            const float e = fmaxf(__fadd_rn(f[0], cf[0][c]), __fadd_rn(f[1], cf[1][c]));
+            rel = e < 0.f || (e == 0.f && exact_pair<D>(rd, cd, rt, c));
+        } else if (D == 4) {
+            // cf holds T_k, X_k, Y_k, Z_k, -H_k; f holds T_i, X_i, Y_i, Z_i, -H_i; e = -s^2 / 2
+            float e = __fadd_rn(cf[4][c], f[4]);
+            e = __fmaf_rn(cf[0][c], f[0], e);
+            e = __fmaf_rn(cf[1][c], -f[1], e);
+            e = __fmaf_rn(cf[2][c], -f[2], e);
+            e = __fmaf_rn(cf[3][c], -f[3], e);
+            rel = e < -m || (e <= m && exact_pair<D>(rd, cd, rt, c));
+        } else {
             // cylinder light cone: shorter arc below |d eta|
-            const float4 k4 = cf4[c];
-            const float deta = fabsf(__fsub_rn(k4.x, tf));
-            const float dth = fabsf(__fsub_rn(k4.y, xf));
+            const float deta = fabsf(__fsub_rn(cf[0][c], f[0]));
+            const float dth = fabsf(__fsub_rn(cf[1][c], f[1]));
             const float ang = __fsub_rn(3.14159265f, fabsf(__fsub_rn(3.14159265f, dth)));
             const float diff = __fsub_rn(deta, ang);
-            if (diff > screen) acc |= 1ull << b;
-            if (fabsf(diff) <= screen) amb |= 1ull << b;
-        } else {
-            const float4 k4 = cf4[c];
-            const float dt = __fsub_rn(k4.x, tf);
-            const float dx = __fsub_rn(k4.y, xf);
-            const float dy = __fsub_rn(k4.z, yf);
-            const float dz = __fsub_rn(k4.w, zf);
-            const float sp = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
-            const float diff = __fmaf_rn(dt, dt, -sp);
-            if (diff > screen) acc |= 1ull << b;
-            if (fabsf(diff) <= screen) amb |= 1ull << b;
+            rel = diff > m || (diff >= -m && exact_pair<D>(rd, cd, rt, c));
         }
-    }
-    if (D != 2) {
-        // pairs inside the screen's margin: decide in double (rare)
-        while (amb) {
-            const int b = __ffsll((long long)amb) - 1;
-            amb &= amb - 1;
-            const int c = q * 64 + b;
-            if (D == GEOM_DS2 ? exact_ds(ti, xi, cd[0][c], cd[1][c])
-                              : exact4(ti, xi, yi, zi, cd[0][c], cd[1][c], cd[2][c], cd[3][c]))
-                acc |= 1ull << b;
-            else
-                acc &= ~(1ull << b);
-        }
+        if (rel) acc |= 1ull << b;
     }
     return acc;
 }
 
-template <int D>
-__global__ void __launch_bounds__(kTile)
-link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts, int n) {
-    __shared__ double cd[4][kTile];       // column coordinates (d=4: t,x,y,z)
-    __shared__ uint64_t ck[2][kTile];     // column order keys of u and v (d=2)
-    __shared__ float4 cf4[kTile];         // column coordinates in float (d=4): t, x, y, z
-    __shared__ uint32_t tb[kTile][9];     // mirrored bits: tb[c][w] = rows 32w..32w+31 of column c
+// The packed screen over one full 64-column word for the thread's four rows (d=2 and
+// d=4).  a[s][0..4]: row s's screen values, each duplicated into both halves of a
+// packed pair.  Bit b of a word stands for column 64 q + b.
+//   d=4: a[s][4] is fl(-H_i + m), so the chain gives e' ~ e + m; A[s] holds the sign
+//        bits of e' (certainly related) and B[s] those of e' - 2m (related, or inside
+//        the margin): B & ~A are the pairs to decide in double.
+//   d=2: A[s] holds the sign bits of e (related unless a float tie).  TIES: B[s] holds
+//        the sign bits of e - 2^-149, i.e. e <= 0 (ties and related; denormals are kept);
+//        otherwise B[s] is all-ones when some |e| of the word is 0 (cheaper, for words
+//        off the diagonal, where ties are rare: the whole word is then decided in double).
+template <int D, bool TIES>
+__device__ __forceinline__ void word_packed(int q, const float (*cf)[kTile], const uint64_t (*a)[5],
+                                            uint64_t m2n, uint64_t *A, uint64_t *B) {
+    float mn[kRowsPer];
+#pragma unroll
+    for (int s = 0; s < kRowsPer; ++s) {
+        mn[s] = __int_as_float(0x7f800000);  // +inf
+        A[s] = 0;
+        B[s] = 0;
+    }
+    // columns from the top of the word down, so that column 64 q + b ends at bit b
+#pragma unroll 1
+    for (int h = 1; h >= 0; --h) {
+        uint32_t acc[kRowsPer] = {0, 0, 0, 0}, bcc[kRowsPer] = {0, 0, 0, 0};
+#pragma unroll 1
+        for (int j = 7; j >= 0; --j) {
+            const int c = 64 * q + 32 * h + 4 * j;
+            if (D == 4) {
+                const ulonglong2 cT = *reinterpret_cast<const ulonglong2 *>(&cf[0][c]);
+                const ulonglong2 cX = *reinterpret_cast<const ulonglong2 *>(&cf[1][c]);
+                const ulonglong2 cY = *reinterpret_cast<const ulonglong2 *>(&cf[2][c]);
+                const ulonglong2 cZ = *reinterpret_cast<const ulonglong2 *>(&cf[3][c]);
+                const ulonglong2 cH = *reinterpret_cast<const ulonglong2 *>(&cf[4][c]);
+#pragma unroll
+                for (int s = 0; s < kRowsPer; ++s) {
+                    uint64_t e01 = fadd2(cH.x, a[s][4]);
+                    uint64_t e23 = fadd2(cH.y, a[s][4]);
+                    e01 = ffma2(cT.x, a[s][0], e01);
+                    e23 = ffma2(cT.y, a[s][0], e23);
+                    e01 = ffma2(cX.x, a[s][1], e01);
+                    e23 = ffma2(cX.y, a[s][1], e23);
+                    e01 = ffma2(cY.x, a[s][2], e01);
+                    e23 = ffma2(cY.y, a[s][2], e23);
+                    e01 = ffma2(cZ.x, a[s][3], e01);
+                    e23 = ffma2(cZ.y, a[s][3], e23);
+                    float e0, e1, e2, e3, f0, f1, f2, f3;
+                    unpack2(e01, e0, e1);
+                    unpack2(e23, e2, e3);
+                    unpack2(fadd2(e01, m2n), f0, f1);
+                    unpack2(fadd2(e23, m2n), f2, f3);
+                    acc[s] = push_sign(e0, push_sign(e1, push_sign(e2, push_sign(e3, acc[s]))));
+                    bcc[s] = push_sign(f0, push_sign(f1, push_sign(f2, push_sign(f3, bcc[s]))));
+                }
+            } else {
+                const ulonglong2 cU = *reinterpret_cast<const ulonglong2 *>(&cf[0][c]);
+                const ulonglong2 cV = *reinterpret_cast<const ulonglong2 *>(&cf[1][c]);
+#pragma unroll
+                for (int s = 0; s < kRowsPer; ++s) {
+                    float u0, u1, u2, u3, w0, w1, w2, w3;
+                    unpack2(fadd2(cU.x, a[s][0]), u0, u1);
+                    unpack2(fadd2(cU.y, a[s][0]), u2, u3);
+                    unpack2(fadd2(cV.x, a[s][1]), w0, w1);
+                    unpack2(fadd2(cV.y, a[s][1]), w2, w3);
+                    const float e0 = fmaxf(u0, w0), e1 = fmaxf(u1, w1), e2 = fmaxf(u2, w2), e3 = fmaxf(u3, w3);
+                    acc[s] = push_sign(e0, push_sign(e1, push_sign(e2, push_sign(e3, acc[s]))));
+                    if (TIES) {
+                        const float dn = -0x1p-149f;
+                        bcc[s] = push_sign(__fadd_rn(e0, dn),
+                                           push_sign(__fadd_rn(e1, dn),
+                                                     push_sign(__fadd_rn(e2, dn), push_sign(__fadd_rn(e3, dn), bcc[s]))));
+                    } else {
+                        mn[s] = fminf(mn[s], fminf(fminf(fabsf(e0), fabsf(e1)), fminf(fabsf(e2), fabsf(e3))));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < kRowsPer; ++s) {
+            A[s] |= (uint64_t)acc[s] << (32 * h);
+            if (D == 4 || TIES) B[s] |= (uint64_t)bcc[s] << (32 * h);
+        }
+    }
+    if (D == 2 && !TIES) {
+#pragma unroll
+        for (int s = 0; s < kRowsPer; ++s) B[s] = mn[s] == 0.f ? ~0ull : A[s];
+    }
+}
 
-    const int s = find_set(starts, n, blockIdx.x);
-    const LinkRow S = sets[s];
+template <int D>
+__global__ void __launch_bounds__(kTile, kLinkMinBlocks)
+link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts, int n,
+            const float *__restrict__ F) {
+    constexpr int ND = D == 4 ? 4 : 2;             // double coordinates the exact test reads
+    __shared__ __align__(16) float cf[5][kTile];  // column screen values (negated for d=2)
+    __shared__ double cd[ND][kTile];              // column coordinates in double
+    __shared__ double rd[ND][kTile];              // row coordinates in double
+    __shared__ uint64_t ow[kTileWords][kTile];    // row words: ow[q][r] = word q of tile row r
+    __shared__ uint32_t tb[kTile][9];             // mirrored bits: tb[c][g] = rows 32g..32g+31 of column c
+
+    const int s_idx = find_set(starts, n, blockIdx.x);
+    const LinkRow S = sets[s_idx];
     const int64_t t = blockIdx.x - S.tile_off;
     // row block: largest b with tiles_before(b) <= t
     int64_t lo = 0, hi = S.nb - 1;
@@ -183,95 +353,126 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
     const bool diag = (bi == bj);
     const int r = threadIdx.x;
     const int lane = r & 31, warp = r >> 5;
-    const int64_t i = R + r;
-    const int64_t kc = K + r;  // column staged by this thread
+    const float *__restrict__ Fs = F + S.foff;
+    const double *__restrict__ co = S.coords;
+    constexpr int base = D == 2 ? 2 : 0;           // first coordinate row the exact test reads
 
-    if (kc < N) {
-        if (D == 2) {
-            ck[0][r] = order_key(S.coords[2 * N + kc]);
-            ck[1][r] = order_key(S.coords[3 * N + kc]);
-        } else {  // d=4: t, x, y, z; de Sitter: eta, theta, 0, 0
-            double v[4];
+    // stage column K + r and row R + r (beyond N: zeros; no word reads them)
+    {
+        const int64_t kc = K + r, i = R + r;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                v[q] = S.coords[q * N + kc];
-                cd[q][r] = v[q];
-            }
-            cf4[r] = make_float4(__double2float_rn(v[0]), __double2float_rn(v[1]), __double2float_rn(v[2]),
-                                 __double2float_rn(v[3]));
+        for (int a = 0; a < screen_floats(D); ++a) {
+            const float x = kc < N ? Fs[a * N + kc] : 0.f;
+            cf[a][r] = D == 2 ? -x : x;
+        }
+#pragma unroll
+        for (int a = 0; a < ND; ++a) {
+            cd[a][r] = kc < N ? co[(base + a) * N + kc] : 0.0;
+            rd[a][r] = i < N ? co[(base + a) * N + i] : 0.0;
         }
     }
     __syncthreads();
 
-    uint64_t w[kTileWords] = {0, 0, 0, 0};
-    const int64_t ncol_l = N - K;
-    const int ncol = ncol_l <= 0 ? 0 : (ncol_l >= kTile ? kTile : (int)ncol_l);
-    if (i < N) {
-        const int c0 = diag ? r + 1 : 0;   // first column strictly after row i
-        uint64_t ui = 0, vi = 0;
-        double ti = 0, xi = 0, yi = 0, zi = 0;
-        float tf = 0, xf = 0, yf = 0, zf = 0;
-        if (D == 2) {
-            ui = order_key(S.coords[2 * N + i]);
-            vi = order_key(S.coords[3 * N + i]);
-        } else {  // d=4 and de Sitter read the same rows
-            ti = S.coords[i];
-            xi = S.coords[N + i];
-            yi = S.coords[2 * N + i];
-            zi = S.coords[3 * N + i];
-            tf = __double2float_rn(ti);
-            xf = __double2float_rn(xi);
-            yf = __double2float_rn(yi);
-            zf = __double2float_rn(zi);
-        }
-        const bool full = !diag && ncol == kTile;
-#pragma unroll 1
-        for (int q = 0; q < kTileWords; ++q) {
-            const uint64_t word =
-                full ? link_word<D, true>(q, c0, ncol, ck, cf4, cd, ui, vi, tf, xf, yf, zf, ti, xi, yi, zi, S.screen)
-                     : link_word<D, false>(q, c0, ncol, ck, cf4, cd, ui, vi, tf, xf, yf, zf, ti, xi, yi, zi, S.screen);
-            if (q == 0) w[0] = word;
-            else if (q == 1) w[1] = word;
-            else if (q == 2) w[2] = word;
-            else w[3] = word;
+    const int ncol = N - K <= 0 ? 0 : (N - K >= kTile ? kTile : (int)(N - K));
+    const int q = warp >> 1;                       // this warp's 64-column word
+    const int rfirst = 32 * (warp & 1);            // tile rows rfirst + 64 s + lane
+    const float m = S.margin;
+
+    // the rows' screen values, each duplicated into a packed pair; d=4 rows carry the
+    // signs of the space products and the margin: T, -X, -Y, -Z, fl(-H + m)
+    uint64_t a[kRowsPer][5];
+#pragma unroll
+    for (int s = 0; s < kRowsPer; ++s) {
+        const int64_t i = R + rfirst + 64 * s + lane;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            float x = 0.f;
+            if (c < screen_floats(D) && i < N) x = Fs[c * N + i];
+            if (D == 4 && c >= 1 && c <= 3) x = -x;
+            if (D == 4 && c == 4) x = __fadd_rn(x, m);
+            a[s][c] = pack2(x, x);
         }
     }
 
-    // mirrored half: transpose each 32 x 32 block of this warp's rows
+    // Rows of this slot with any column of the word after them and before N (the same for
+    // all lanes of the warp: slots start at multiples of 32, words at multiples of 64).
+    bool any = false;
+    bool live[kRowsPer];
 #pragma unroll
-    for (int g = 0; g < kTile / 32; ++g) {
-        const uint64_t word = w[g >> 1];
-        const uint32_t x = (uint32_t)(word >> (32 * (g & 1)));
-        tb[32 * g + lane][warp] = warp_transpose32(x, lane);
+    for (int s = 0; s < kRowsPer; ++s) {
+        const int rlo = rfirst + 64 * s;
+        live[s] = 64 * q < ncol && !(diag && rlo >= 64 * q + 64);
+        any |= live[s];
+    }
+
+    uint64_t A[kRowsPer] = {0, 0, 0, 0}, B[kRowsPer] = {0, 0, 0, 0};
+    if (D != GEOM_DS2 && any) {
+        const float m2 = -(m + m);
+        if (D == 2 && diag)
+            word_packed<D, true>(q, cf, a, 0, A, B);
+        else
+            word_packed<D, false>(q, cf, a, pack2(m2, m2), A, B);
+    }
+#pragma unroll
+    for (int s = 0; s < kRowsPer; ++s) {
+        const int rt = rfirst + 64 * s + lane;     // tile row
+        const int64_t i = R + rt;
+        uint64_t wd = 0;
+        if (i < N && live[s]) {
+            // the word's columns after the row (diagonal tile) and before N
+            const int lo = diag ? max(rt + 1 - 64 * q, 0) : 0;
+            const int hi = min(ncol - 64 * q, 64);
+            const uint64_t mask = lo >= hi ? 0ull : ((hi == 64 ? ~0ull : (1ull << hi) - 1) & ~((1ull << lo) - 1));
+            if (D != GEOM_DS2) {
+                // pairs the screen left open: decide them in double
+                wd = A[s] & mask;
+                uint64_t amb = B[s] & ~A[s] & mask;
+                while (amb) {
+                    const int b = __ffsll((long long)amb) - 1;
+                    amb &= amb - 1;
+                    if (exact_pair<D>(rd, cd, rt, 64 * q + b))
+                        wd |= 1ull << b;
+                    else
+                        wd &= ~(1ull << b);
+                }
+            } else {
+                wd = word_by_pair<D>(q, lo + 64 * q, ncol, cf, rd, cd, rt, Fs, N, i, m);
+            }
+        }
+        ow[q][rt] = wd;
+        // mirrored half: columns 64 q + 32 h + lane get the bits of rows 32 g .. 32 g + 31
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            tb[64 * q + 32 * h + lane][(warp & 1) + 2 * s] = warp_transpose32((uint32_t)(wd >> (32 * h)), lane);
     }
     __syncthreads();
 
     uint64_t *rows = S.rows;
     const int64_t stride = S.stride;
+    const int64_t i = R + r;
+    const int64_t kc = K + r;
     if (diag) {
         // both halves land in the same words: OR them
         if (i < N) {
             uint64_t *dst = rows + i * stride + K / 64;
 #pragma unroll
-            for (int q = 0; q < kTileWords; ++q) {
-                uint64_t m = (uint64_t)tb[r][2 * q] | ((uint64_t)tb[r][2 * q + 1] << 32);
-                dst[q] = w[q] | m;
-            }
+            for (int w = 0; w < kTileWords; ++w)
+                dst[w] = ow[w][r] | (uint64_t)tb[r][2 * w] | ((uint64_t)tb[r][2 * w + 1] << 32);
         }
     } else {
         if (i < N) {
             uint64_t *dst = rows + i * stride + K / 64;
-            reinterpret_cast<ulonglong2 *>(dst)[0] = make_ulonglong2(w[0], w[1]);
-            reinterpret_cast<ulonglong2 *>(dst)[1] = make_ulonglong2(w[2], w[3]);
+            reinterpret_cast<ulonglong2 *>(dst)[0] = make_ulonglong2(ow[0][r], ow[1][r]);
+            reinterpret_cast<ulonglong2 *>(dst)[1] = make_ulonglong2(ow[2][r], ow[3][r]);
         }
         if (kc < N) {
-            uint64_t m[kTileWords];
+            uint64_t mw[kTileWords];
 #pragma unroll
-            for (int q = 0; q < kTileWords; ++q)
-                m[q] = (uint64_t)tb[r][2 * q] | ((uint64_t)tb[r][2 * q + 1] << 32);
+            for (int w = 0; w < kTileWords; ++w)
+                mw[w] = (uint64_t)tb[r][2 * w] | ((uint64_t)tb[r][2 * w + 1] << 32);
             uint64_t *dst = rows + kc * stride + R / 64;
-            reinterpret_cast<ulonglong2 *>(dst)[0] = make_ulonglong2(m[0], m[1]);
-            reinterpret_cast<ulonglong2 *>(dst)[1] = make_ulonglong2(m[2], m[3]);
+            reinterpret_cast<ulonglong2 *>(dst)[0] = make_ulonglong2(mw[0], mw[1]);
+            reinterpret_cast<ulonglong2 *>(dst)[1] = make_ulonglong2(mw[2], mw[3]);
         }
     }
 }
@@ -281,12 +482,13 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
 LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
     LinkPlan p;
     *rc = CSG_OK;
+    int64_t nf = 0;  // floats of screen values over all sets
     // one tile space per geometry: each launch runs one instantiation of the kernel
     for (int part = 0; part < 3; ++part) {
         const int d = part == 0 ? 2 : (part == 1 ? 4 : GEOM_DS2);
         std::vector<LinkRow> rows;
-        std::vector<int64_t> starts;
-        int64_t T = 0;
+        std::vector<int64_t> starts, estarts;
+        int64_t T = 0, E = 0;
         for (int s = 0; s < n; ++s) {
             if (specs[s].d != d) continue;
             LinkRow L;
@@ -299,7 +501,11 @@ LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
             L.nb = (L.N + kTile - 1) / kTile;
             L.nbc = L.stride / kTileWords;
             L.tile_off = T;
-            L.screen = d == GEOM_DS2 ? 1e-5f : 1e-5f * (float)(specs[s].coord_scale * specs[s].coord_scale);
+            L.eoff = E;
+            L.foff = nf;
+            L.margin = d == GEOM_DS2 ? 1e-5f
+                       : d == 4     ? 4e-6f * (float)(specs[s].coord_scale * specs[s].coord_scale)
+                                    : 0.f;
             L.pad2 = 0.f;
             if (L.stride % 16 != 0 || L.nbc < L.nb) {
                 set_error("link: stride %lld does not cover N=%lld", (long long)L.stride, (long long)L.N);
@@ -307,10 +513,13 @@ LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
                 return p;
             }
             starts.push_back(T);
+            estarts.push_back(E);
             rows.push_back(L);
             T += L.nb * L.nbc - L.nb * (L.nb - 1) / 2;
+            E += L.N;
+            nf += (int64_t)screen_floats(d) * L.N;
         }
-        if (T > 0x7fffffffLL) {
+        if (T > 0x7fffffffLL || (E + 255) / 256 > 0x7fffffffLL) {
             set_error("link: %lld tiles exceed one launch", (long long)T);
             *rc = CSG_E_INVAL;
             return p;
@@ -318,23 +527,33 @@ LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
         LinkPlan::Part &P = p.part[part];
         P.n = (int)rows.size();
         P.T = T;
+        P.E = E;
         if (P.n) {
             P.t_rows = a.put(rows.data(), rows.size() * sizeof(LinkRow));
             P.t_starts = a.put(starts.data(), starts.size() * sizeof(int64_t));
+            P.t_estarts = a.put(estarts.data(), estarts.size() * sizeof(int64_t));
         }
         p.T += T;
     }
+    p.s_screen = a.reserve((size_t)nf * sizeof(float));
     return p;
+}
+
+template <int D>
+static void link_part_launch(const LinkPlan::Part &P, const Arena &a, float *F, cudaStream_t st) {
+    if (P.T == 0) return;
+    link_screen_kernel<D><<<(unsigned)((P.E + 255) / 256), 256, 0, st>>>(
+        a.tab<LinkRow>(P.t_rows), a.tab<int64_t>(P.t_estarts), P.n, P.E, F);
+    link_kernel<D><<<(unsigned)P.T, kTile, 0, st>>>(a.tab<LinkRow>(P.t_rows), a.tab<int64_t>(P.t_starts), P.n, F);
 }
 
 void link_launch(const LinkPlan &p, const Arena &a, cudaStream_t st) {
     if (p.T == 0) return;
     stage_begin(CSG_STAGE_LINK, st);
-    const LinkPlan::Part &p2 = p.part[0], &p4 = p.part[1], &p3 = p.part[2];
-    if (p2.T) link_kernel<2><<<(unsigned)p2.T, kTile, 0, st>>>(a.tab<LinkRow>(p2.t_rows), a.tab<int64_t>(p2.t_starts), p2.n);
-    if (p4.T) link_kernel<4><<<(unsigned)p4.T, kTile, 0, st>>>(a.tab<LinkRow>(p4.t_rows), a.tab<int64_t>(p4.t_starts), p4.n);
-    if (p3.T)
-        link_kernel<GEOM_DS2><<<(unsigned)p3.T, kTile, 0, st>>>(a.tab<LinkRow>(p3.t_rows), a.tab<int64_t>(p3.t_starts), p3.n);
+    float *F = a.scr<float>(p.s_screen);
+    link_part_launch<2>(p.part[0], a, F, st);
+    link_part_launch<4>(p.part[1], a, F, st);
+    link_part_launch<GEOM_DS2>(p.part[2], a, F, st);
     stage_end(CSG_STAGE_LINK, st);
 }
 

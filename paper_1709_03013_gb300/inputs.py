@@ -116,3 +116,73 @@ def pack_rows(rel: np.ndarray, stride_words: int) -> np.ndarray:
     bits[:, :N] = rel
     packed = np.packbits(bits, axis=1, bitorder="little")
     return packed.view(np.uint64).reshape(N, stride_words).copy()
+
+
+# ------------------------------------------------------- light-cone stress sets
+
+def light_cone_coords(d: int, N: int, seed: int, scale: float = 1.0) -> np.ndarray:
+    """Unsorted coordinates [4, N] crowded onto light cones, for the link's tie-breaking.
+
+    A quarter of the elements are base points on a dyadic grid (multiples of 2^-21 in
+    [-1/2, 1/2]); every other element copies a base point and moves it by an exactly null
+    displacement (d=4: along an axis, or along 3-4-5 and 1-2-2 directions; d=2: a step in
+    u or v only), after which a third of them are nudged by one unit in the last place in
+    one coordinate, and a few are exact duplicates or carry signed zeros.  Products of the
+    grid values with `scale` (1 or an integer below 2^31) stay exact.  d=4 rows are
+    t, x, y, z; d=2 rows are t, x, u, v with t = (u + v) / 2, x = (v - u) / 2.
+    """
+    rng = np.random.default_rng(seed)
+    g = 2.0 ** -21
+    nb = max(1, N // 4)
+    c = np.zeros((4, N), dtype=np.float64)
+    if d == 4:
+        c[:, :nb] = rng.integers(-2 ** 20, 2 ** 20, size=(4, nb)) * g
+        for e in range(nb, N):
+            b = int(rng.integers(0, nb))
+            p = c[:, b].copy()
+            mode = int(rng.integers(0, 4))
+            if mode == 0:                                   # along an axis
+                dt = int(rng.integers(1, 2 ** 18)) * g
+                a = 1 + int(rng.integers(0, 3))
+                p[0] += dt
+                p[a] += dt if rng.random() < 0.5 else -dt
+            elif mode == 1:                                 # 3-4-5 direction
+                dl = int(rng.integers(1, 2 ** 15)) * g
+                ax = rng.permutation(3)[:2] + 1
+                p[0] += 5 * dl
+                p[ax[0]] += 3 * dl * (1 if rng.random() < 0.5 else -1)
+                p[ax[1]] += 4 * dl * (1 if rng.random() < 0.5 else -1)
+            elif mode == 2:                                 # 1-2-2 direction
+                dl = int(rng.integers(1, 2 ** 15)) * g
+                sg = np.where(rng.random(3) < 0.5, 1.0, -1.0)
+                p[0] += 3 * dl
+                p[1:] += dl * sg * np.array([1.0, 2.0, 2.0])
+            # mode 3: exact duplicate of the base point
+            if mode != 3 and rng.random() < 1 / 3:
+                a = int(rng.integers(0, 4))
+                p[a] = np.nextafter(p[a], np.inf if rng.random() < 0.5 else -np.inf)
+            c[:, e] = p
+    else:
+        uv = rng.integers(-2 ** 20, 2 ** 20, size=(2, nb)) * g
+        c[2:, :nb] = uv
+        for e in range(nb, N):
+            b = int(rng.integers(0, nb))
+            u, v = c[2, b], c[3, b]
+            mode = int(rng.integers(0, 4))
+            step = int(rng.integers(1, 2 ** 18)) * g
+            if mode == 0:
+                v += step                                   # equal u: null, unrelated
+            elif mode == 1:
+                u += step                                   # equal v
+            elif mode == 2:                                 # u equal in float, not in double
+                u += 2.0 ** -45
+                v += step
+            if rng.random() < 1 / 3:
+                v = np.nextafter(v, np.inf if rng.random() < 0.5 else -np.inf)
+            c[2, e], c[3, e] = u, v
+        zs = rng.choice(N, size=max(1, N // 50), replace=False)
+        c[2, zs[: len(zs) // 2]] = -0.0
+        c[2, zs[len(zs) // 2:]] = 0.0
+        c[0] = (c[2] + c[3]) / 2
+        c[1] = (c[3] - c[2]) / 2
+    return c * scale

@@ -136,6 +136,22 @@ def test_set_from_host_coords(ctx, d):
     s.free()
 
 
+@pytest.mark.parametrize("d,scale", [(4, 1.0), (4, 1000.0), (2, 1.0), (2, 1000.0)])
+def test_link_on_and_near_light_cones(ctx, d, scale):
+    """Exactly null pairs, pairs one ulp off the cone, float ties, duplicates and signed
+    zeros: every pair the float screens cannot settle must still get the double decision."""
+    N = 1500
+    c = inputs.light_cone_coords(d, N, 77, scale)
+    s = ctx.set_from_coords(d, c)
+    sorted_c, _ = oracle.sort(d, c)
+    assert np.array_equal(s.coords(), sorted_c)
+    s.link()
+    rel = oracle.link(d, sorted_c)
+    assert np.array_equal(s.bitmap(), oracle.pack(rel, s.info()["stride"]))
+    _check_result(s.action(), oracle.action(rel), d, N)
+    s.free()
+
+
 @pytest.mark.parametrize("method", [0, 1])
 @pytest.mark.parametrize("d,N", [(2, 3000), (4, 4100)])
 def test_action_rows(ctx, d, N, method):

@@ -133,6 +133,29 @@ def test_link_matches_exact_light_cone(d):
         assert rel[i, j] == _exact_related(d, c, i, j)
 
 
+def test_link_light_cone_stress_set():
+    """On a set crowded onto light cones (exact nulls, one-ulp nudges, duplicates), the
+    oracle's double decision agrees with the exact rational one wherever the exact
+    interval is clearly away from zero, and exactly null pairs are unrelated (Sec. 2.2:
+    related means strictly inside the light cone)."""
+    from paper_1709_03013_gb300 import inputs
+    N = 300
+    c, _ = oracle.sort(4, inputs.light_cone_coords(4, N, 5))
+    rel = oracle.link(4, c)
+    F = [[Fraction(float(v)) for v in row] for row in c]
+    nulls = clear = 0
+    for i, j in itertools.combinations(range(N), 2):
+        dt = F[0][j] - F[0][i]
+        s2 = dt * dt - sum((F[r][j] - F[r][i]) ** 2 for r in (1, 2, 3))
+        if s2 == 0:
+            nulls += 1
+            assert rel[i, j] == 0
+        elif abs(s2) > Fraction(1, 10 ** 12):
+            clear += 1
+            assert rel[i, j] == (dt > 0 and s2 > 0)
+    assert nulls >= 50 and clear > N * (N - 1) // 2 - 2 * N
+
+
 @pytest.mark.parametrize("d", [2, 4])
 def test_link_symmetric_zero_diagonal_row_and_pair(d):
     c = oracle.sprinkle_sorted(d, 200, seed=8)
