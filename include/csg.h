@@ -147,7 +147,10 @@ int csg_set_from_bitmap(csg_ctx *ctx, int d, int64_t N, const uint64_t *dev_rows
                         int64_t stride_words, void *stream, csg_set **out);
 
 /* Interval abundances and action of one set (Alg. 5; Eq. s_local).  method is
- * CSG_POPC or CSG_TC.  Synchronises `stream`, then fills *out. */
+ * CSG_POPC, CSG_TC, CSG_TC_FP8 or CSG_TC_FP4.  The tensor methods take N^2 bytes of
+ * device scratch for their operands (fp4; 2 N^2 for fp8), allocated on `stream` and
+ * freed before return; CSG_E_NOMEM if it cannot be allocated.  Synchronises `stream`,
+ * then fills *out. */
 int csg_action(csg_ctx *ctx, csg_set *set, int method, csg_result *out, void *stream);
 
 /* The same restricted to first elements i in [row_lo, row_hi): counts only pairs

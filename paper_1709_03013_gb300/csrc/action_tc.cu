@@ -853,8 +853,10 @@ int encode_map(CUtensorMap *m, void *base, int64_t rows, int64_t kp, int box_row
 
 }  // namespace
 
-// Largest N the tensor form accepts: its fp8 operands take 2 N^2 bytes of scratch.
-static constexpr int64_t kTcMaxN = 1 << 17;
+// Largest N the tensor form accepts (every N a set can have): its operands take N^2
+// bytes of scratch in fp4 (64 GiB at N = 2^18) and 2 N^2 in fp8 (128 GiB).  The fp32
+// accumulator stays exact (m < 2^18, a 16-column sum < 2^22, both below 2^24).
+static constexpr int64_t kTcMaxN = CSG_MAX_N;
 // Operand scratch shared by the sets of one chunk (a larger single set gets its own).
 static constexpr int64_t kChunkBytes = 16ll << 30;
 

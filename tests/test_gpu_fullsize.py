@@ -131,6 +131,36 @@ def test_full_size_set(ctx, csg, d, N, seed, rows):
     s.free()
 
 
+@pytest.mark.parametrize("d,seed", [(2, 11), (4, 12)])
+def test_max_size_set(ctx, csg, d, seed):
+    """N = CSG_MAX_N (2^18): 8 GiB bitmap, 64 GiB of fp4 operands.  Bit-exact coordinates
+    and sampled bitmap rows and columns, the exact identities for R, sum m and W from the
+    whole downloaded bitmap, the oracle's matrix-free counts on late rows, and both tensor
+    formats equal (d=2 also against the popcount kernel)."""
+    N = csg.MAX_N
+    s = ctx.sprinkle(d, N, seed).link()
+    coords = oracle.sprinkle_sorted(d, N, seed)
+    assert np.array_equal(s.coords(), coords)
+    words = s.bitmap()
+    for i in (0, 7, N // 2 + 5, N - 1):
+        row = oracle.link_row(d, coords, i)
+        assert np.array_equal(words[i], _pack_row(row, words.shape[1])), i
+        col = ((words[:, i // 64] >> np.uint64(i % 64)) & np.uint64(1)).astype(np.uint8)
+        assert np.array_equal(col, row), i
+    R, sum_m, W, ins, outs = _identities(words, N)
+    del words
+    assert ins == outs == R
+    tc = s.action(csg.TC)
+    assert (tc.R, tc.sum_m, tc.W, tc.N, tc.status) == (R, sum_m, W, N, 0)
+    _same(s.action(csg.TC_FP8), tc)
+    if d == 2:
+        _same(s.action(csg.POPC), tc)
+    combo, S = oracle.finalize(d, N, tc.Nk)
+    assert tc.combo == combo and abs(tc.S - S) <= TOL_S * max(abs(S), 1.0)
+    _check_rows(s, d, coords, (N - 3000, N - 700, N - 2), csg)
+    s.free()
+
+
 def test_batch_4096_sets(ctx, csg):
     specs = inputs.batch_workload()                                # 4096 diamonds, seed 3
     assert len(specs) == 4096
