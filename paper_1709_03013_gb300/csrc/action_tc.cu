@@ -75,10 +75,10 @@ constexpr uint32_t TMEM_COLS = 2 * BN;
 constexpr uint64_t kWaitNs = 4000000000ull;
 constexpr uint8_t kOne = 0x38;   // 1.0 in fp8 e4m3
 
-struct TcTile {
-    int32_t set;     // index into the launch's set table
+struct __align__(16) TcTile {
+    int32_t set;     // index into the launch's set table (-1: no more tiles)
     int32_t ti, tj;  // rows [BM ti, BM ti + BM), columns [BN tj, BN tj + BN)
-    int32_t pad;
+    int32_t kk;      // K stages [kk & 0xFFFF, kk >> 16): the tile's first row to its last column
 };
 
 struct TcArgs {
@@ -471,14 +471,14 @@ __device__ __forceinline__ unsigned long long epi_tile_all(uint32_t tbase, const
     return packed;
 }
 
-template <int FMT>
-__device__ __forceinline__ void k_range(const TcTile &t, int64_t N, int &kt0, int &kt1) {
-    // K runs from the tile's first row to its last column (or N), in stages of KSTAGE
-    constexpr int64_t KSTAGE = FMT ? 256 : 128;
-    const int64_t I0 = (int64_t)t.ti * BM;
-    const int64_t J1 = min((int64_t)(t.tj + 1) * BN, N);
-    kt0 = (int)(I0 / KSTAGE);
-    kt1 = (int)((J1 + KSTAGE - 1) / KSTAGE);
+// K stages of a tile: from the tile's first row to its last column (or N), in stages of
+// 256 fp4 or 128 fp8 elements (at most 2^11 stages for N <= 2^18, so both fit 16 bits)
+inline int32_t k_range_packed(int ti, int tj, int64_t N, int fmt) {
+    const int64_t KSTAGE = fmt ? 256 : 128;
+    const int64_t I0 = (int64_t)ti * BM;
+    const int64_t J1 = std::min<int64_t>((int64_t)(tj + 1) * BN, N);
+    const int64_t kt0 = I0 / KSTAGE, kt1 = (J1 + KSTAGE - 1) / KSTAGE;
+    return (int32_t)(kt0 | (kt1 << 16));
 }
 
 template <int FMT>
@@ -499,8 +499,8 @@ action_tc_kernel(const TcArgs args) {
     // tile indices the leader claims and mails to the other CTA (slots in the other CTA's
     // shared memory): mail_full lives with the reader, mail_empty with the leader
     uint64_t *mail_full = rempty + RING, *mail_empty = mail_full + RING;
-    int *ring = reinterpret_cast<int *>(mail_empty + RING);
-    int *mail = ring + RING;
+    TcTile *ring = reinterpret_cast<TcTile *>(mail_empty + RING);  // 16-byte aligned (32 barriers before it)
+    TcTile *mail = ring + RING;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mail + RING);
     int *bad_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
@@ -556,24 +556,37 @@ action_tc_kernel(const TcArgs args) {
         if (lane == 0) {
             int s = 0;
             uint32_t ph = 0;
+            int cur_set = -1;
+            // the leader claims the pair's next tile one step ahead, so the atomic's round
+            // trip overlaps the current tile's loads
+            int t_next = rank == 0 ? (int)atomicAdd(args.queue, 1u) : 0;
             for (int n = 0; !bad; ++n) {
                 // the pair's next tile: the leader claims it from the global queue (in list
-                // order, so the tiles running at once stay neighbours in L2) and mails the index
-                // to the other CTA; each producer hands it to its own MMA and epilogue warps
+                // order, so the tiles running at once stay neighbours in L2) and mails the tile
+                // itself to the other CTA; each producer hands it to its own MMA and epilogue
+                // warps through the ring
                 const int slot = n % RING;
                 const uint32_t rph = (uint32_t)(n / RING) & 1u;
                 if (!ptx::mbar_wait_bounded(&rempty[slot], rph ^ 1u, kWaitNs)) {
                     bad = true;
                     break;
                 }
-                int t;
+                TcTile tile;
                 if (rank == 0) {
                     if (!mbar_wait_cl(&mail_empty[slot], rph ^ 1u, kWaitNs)) {
                         bad = true;
                         break;
                     }
-                    t = (int)atomicAdd(args.queue, 1u);
-                    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr(&mail[slot], 1)), "r"(t)
+                    const int t = t_next;
+                    if (t < args.n_tiles) {
+                        tile = args.tiles[t];
+                        t_next = (int)atomicAdd(args.queue, 1u);
+                    } else {
+                        tile.set = -1;
+                        tile.ti = tile.tj = tile.kk = 0;
+                    }
+                    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(cluster_addr(&mail[slot], 1)),
+                                 "r"(tile.set), "r"(tile.ti), "r"(tile.tj), "r"(tile.kk)
                                  : "memory");
                     mbar_arrive_cluster(cluster_addr(&mail_full[slot], 1), 1);
                 } else {
@@ -581,16 +594,20 @@ action_tc_kernel(const TcArgs args) {
                         bad = true;
                         break;
                     }
-                    t = mail[slot];
+                    tile = mail[slot];
                     mbar_arrive_cluster(cluster_addr(&mail_empty[slot], 0), 1);
                 }
-                ring[slot] = t < args.n_tiles ? t : -1;
+                ring[slot] = tile;
                 mbar_arrive(&rfull[slot]);
-                if (t >= args.n_tiles) break;
-                const TcTile tile = args.tiles[t];
-                int kt0, kt1;
-                k_range<FMT>(tile, args.sets[tile.set].N, kt0, kt1);
+                if (tile.set < 0) break;
                 const CUtensorMap *mU = args.maps + 2 * tile.set, *mP = mU + 1;
+                if (tile.set != cur_set) {
+                    // a new set's operand maps: fetch the descriptors before the first copy
+                    asm volatile("prefetch.tensormap [%0];" ::"l"(mU) : "memory");
+                    asm volatile("prefetch.tensormap [%0];" ::"l"(mP) : "memory");
+                    cur_set = tile.set;
+                }
+                const int kt0 = tile.kk & 0xFFFF, kt1 = tile.kk >> 16;
                 for (int kt = kt0; kt < kt1; ++kt) {
                     if (!mbar_wait_cl(&empty[s], ph ^ 1u, kWaitNs)) {
                         bad = true;
@@ -618,13 +635,11 @@ action_tc_kernel(const TcArgs args) {
                     bad = true;
                     break;
                 }
-                const int t = ring[slot];
+                const TcTile tile = ring[slot];
                 mbar_arrive(&rempty[slot]);
-                if (t < 0) break;
+                if (tile.set < 0) break;
                 if (rank != 0) continue;  // the leader issues the pair's MMAs
-                const TcTile tile = args.tiles[t];
-                int kt0, kt1;
-                k_range<FMT>(tile, args.sets[tile.set].N, kt0, kt1);
+                const int kt0 = tile.kk & 0xFFFF, kt1 = tile.kk >> 16;
                 // both CTAs' epilogues have drained accumulator b
                 if (!mbar_wait_cl(&tempty[b], bph ^ 1u, kWaitNs)) {
                     bad = true;
@@ -701,10 +716,9 @@ action_tc_kernel(const TcArgs args) {
                 bad = true;
                 break;
             }
-            const int t = ring[slot];
+            const TcTile tile = ring[slot];
             mbar_arrive(&rempty[slot]);
-            if (t < 0) break;
-            const TcTile tile = args.tiles[t];
+            if (tile.set < 0) break;
             if (tile.set != cur) {
                 if (cur >= 0) flush(cur);
                 cur = tile.set;
@@ -822,7 +836,7 @@ std::vector<TcTile> single_set_tiles(int64_t N, int64_t lo, int64_t hi, int supe
                     const int64_t J1 = std::min<int64_t>((int64_t)(tj + 1) * BN, N);
                     if (J1 <= I0 + 1) continue;
                     // as a pair tile: row tiles ti & ~1 and (ti & ~1) + 1 go to the two CTAs of a pair
-                    const TcTile pt{0, ti & ~1, tj, 0};
+                    const TcTile pt{0, ti & ~1, tj, 0};  // set and K range filled in per launch
                     if (tiles.empty() || tiles.back().ti != pt.ti || tiles.back().tj != pt.tj) tiles.push_back(pt);
                 }
             }
@@ -927,7 +941,10 @@ TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned
             const TcSetDesc &D = desc[c.set_lo];
             if (D.row_hi > D.row_lo) {
                 tiles = single_set_tiles(D.N, D.row_lo, D.row_hi, super);
-                for (TcTile &t : tiles) t.set = c.set_lo;
+                for (TcTile &t : tiles) {
+                    t.set = c.set_lo;
+                    t.kk = k_range_packed(t.ti, t.tj, D.N, fmt);
+                }
             }
         } else {
             // set by set, largest first: the CTAs running at any moment then work on one or
@@ -938,7 +955,10 @@ TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned
             std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return desc[x].N > desc[y].N; });
             for (int s : order) {
                 std::vector<TcTile> ts = single_set_tiles(desc[s].N, desc[s].row_lo, desc[s].row_hi, super);
-                for (TcTile &t : ts) t.set = s;
+                for (TcTile &t : ts) {
+                    t.set = s;
+                    t.kk = k_range_packed(t.ti, t.tj, desc[s].N, fmt);
+                }
                 tiles.insert(tiles.end(), ts.begin(), ts.end());
             }
         }
