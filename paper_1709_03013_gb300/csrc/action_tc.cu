@@ -83,7 +83,7 @@ struct __align__(16) TcTile {
 
 struct TcArgs {
     const TcSetDesc *sets;
-    const CUtensorMap *maps;  // 2 per set: U, P (global memory, 128-byte aligned)
+    const CUtensorMap *maps;  // 3 per set: U, P, relation bits (global memory, 128-byte aligned)
     const TcTile *tiles;
     int n_tiles;
     unsigned int *queue;       // tile counter (zeroed before the launch)
@@ -91,7 +91,10 @@ struct TcArgs {
     long long nbins;
 };
 
-constexpr int RING = 4;  // tile indices handed from the producer to the MMA and epilogue warps
+constexpr int RING = 4;  // tiles handed from the producer to the MMA and epilogue warps
+// Per ring slot, the tile's relation words for this CTA's 128 rows (4 words of 64 columns
+// each), staged by TMA so the epilogue reads them from shared memory.
+constexpr int BITS_BYTES = BM * (BN / 64) * 8;
 
 // ------------------------------------------------------------------ expand
 
@@ -219,6 +222,15 @@ __device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *m
         "cp.async.bulk.tensor.2d.shared::cta.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
         " [%0], [%1, {%2, %3}], [%4];" ::"r"(ptx::smem_addr(dst)),
         "l"(map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// TMA tile load into this CTA's shared memory completing on this CTA's barrier `bar`.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(ptx::smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(ptx::smem_addr(bar))
         : "memory");
 }
 
@@ -492,14 +504,16 @@ action_tc_kernel(const TcArgs args) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(base + STAGES * STAGE_BYTES);
+    uint64_t *sbits = reinterpret_cast<uint64_t *>(base + STAGES * STAGE_BYTES);  // [RING][BM][4]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + STAGES * STAGE_BYTES + RING * BITS_BYTES);
     uint64_t *full = bars, *empty = bars + STAGES, *tfull = bars + 2 * STAGES,
              *tempty = bars + 2 * STAGES + 2;
     uint64_t *rfull = bars + 2 * STAGES + 4, *rempty = rfull + RING;
     // tile indices the leader claims and mails to the other CTA (slots in the other CTA's
     // shared memory): mail_full lives with the reader, mail_empty with the leader
     uint64_t *mail_full = rempty + RING, *mail_empty = mail_full + RING;
-    TcTile *ring = reinterpret_cast<TcTile *>(mail_empty + RING);  // 16-byte aligned (32 barriers before it)
+    uint64_t *sfull = mail_empty + RING;  // the slot's relation words have landed
+    TcTile *ring = reinterpret_cast<TcTile *>(sfull + RING);  // 16-byte aligned (36 barriers before it)
     TcTile *mail = ring + RING;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mail + RING);
     int *bad_flag = reinterpret_cast<int *>(tmem_slot + 1);
@@ -519,6 +533,7 @@ action_tc_kernel(const TcArgs args) {
             ptx::mbar_init(&rempty[q], 1 + EPI_WARPS * 32);  // the MMA lane and every epilogue thread
             ptx::mbar_init(&mail_full[q], 1);   // other CTA: the leader's remote arrival
             ptx::mbar_init(&mail_empty[q], 1);  // leader: the other CTA's producer has read the slot
+            ptx::mbar_init(&sfull[q], 1);       // this CTA's producer: its arrival + the bits' bytes
         }
         *bad_flag = 0;
         ptx::fence_mbar_init();
@@ -597,16 +612,23 @@ action_tc_kernel(const TcArgs args) {
                     tile = mail[slot];
                     mbar_arrive_cluster(cluster_addr(&mail_empty[slot], 0), 1);
                 }
+                const CUtensorMap *mU = args.maps + 3 * (tile.set < 0 ? 0 : tile.set), *mP = mU + 1, *mS = mU + 2;
+                if (tile.set >= 0) {
+                    if (tile.set != cur_set) {
+                        // a new set's maps: fetch the descriptors before the first copy
+                        asm volatile("prefetch.tensormap [%0];" ::"l"(mU) : "memory");
+                        asm volatile("prefetch.tensormap [%0];" ::"l"(mP) : "memory");
+                        asm volatile("prefetch.tensormap [%0];" ::"l"(mS) : "memory");
+                        cur_set = tile.set;
+                    }
+                    // the relation words of this CTA's 128 rows and the tile's 256 columns
+                    ptx::mbar_arrive_expect_tx(&sfull[slot], BITS_BYTES);
+                    tma_load_2d(sbits + slot * (BITS_BYTES / 8), mS, tile.tj * (BN / 64), (tile.ti + (int)rank) * BM,
+                                &sfull[slot]);
+                }
                 ring[slot] = tile;
                 mbar_arrive(&rfull[slot]);
                 if (tile.set < 0) break;
-                const CUtensorMap *mU = args.maps + 2 * tile.set, *mP = mU + 1;
-                if (tile.set != cur_set) {
-                    // a new set's operand maps: fetch the descriptors before the first copy
-                    asm volatile("prefetch.tensormap [%0];" ::"l"(mU) : "memory");
-                    asm volatile("prefetch.tensormap [%0];" ::"l"(mP) : "memory");
-                    cur_set = tile.set;
-                }
                 const int kt0 = tile.kk & 0xFFFF, kt1 = tile.kk >> 16;
                 for (int kt = kt0; kt < kt1; ++kt) {
                     if (!mbar_wait_cl(&empty[s], ph ^ 1u, kWaitNs)) {
@@ -717,8 +739,19 @@ action_tc_kernel(const TcArgs args) {
                 break;
             }
             const TcTile tile = ring[slot];
-            mbar_arrive(&rempty[slot]);
-            if (tile.set < 0) break;
+            if (tile.set < 0) {
+                mbar_arrive(&rempty[slot]);
+                break;
+            }
+            // the row's relation words for this warp's half of the tile's columns, staged in
+            // shared memory by the producer
+            const bool staged = ptx::mbar_wait_bounded(&sfull[slot], (uint32_t)(n / RING) & 1u, kWaitNs);
+            if (!__all_sync(0xffffffffu, staged)) {
+                bad = true;
+                break;
+            }
+            const ulonglong2 wv = *reinterpret_cast<const ulonglong2 *>(sbits + slot * (BITS_BYTES / 8) + r * 4 + 2 * g);
+            mbar_arrive(&rempty[slot]);  // the slot's tile and words are read
             if (tile.set != cur) {
                 if (cur >= 0) flush(cur);
                 cur = tile.set;
@@ -727,12 +760,15 @@ action_tc_kernel(const TcArgs args) {
             const int64_t N = S.N;
             const int64_t i = (int64_t)(tile.ti + (int)rank) * BM + r;
             const int64_t J0 = (int64_t)tile.tj * BN;
-            // the row's relation bits for this warp's columns of J0..J0+255, fetched before the wait
             uint64_t w4[4] = {0, 0, 0, 0};
             if (i < N && i >= S.row_lo && i < S.row_hi) {
-                const uint64_t *src = S.rows + i * S.stride + J0 / 64;
+                w4[0] = g == 0 ? wv.x : 0ull;
+                w4[1] = g == 0 ? wv.y : 0ull;
+                w4[2] = g == 1 ? wv.x : 0ull;
+                w4[3] = g == 1 ? wv.y : 0ull;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) w4[u] = ((u >> 1) == g && J0 + 64 * u < N) ? __ldg(src + u) : 0ull;
+                for (int u = 0; u < 4; ++u)
+                    if (J0 + 64 * u >= N) w4[u] = 0;
                 // only columns j > i
                 const int64_t rel = i - J0;  // bit positions k > rel survive
 #pragma unroll
@@ -865,6 +901,32 @@ int encode_map(CUtensorMap *m, void *base, int64_t rows, int64_t kp, int box_row
     return CSG_OK;
 }
 
+// The relation words as a 2D tensor of 64-bit words (stride words x N rows); a box is the
+// 4 words of one tile's columns for one CTA's 128 rows (rows past N read as zero).
+int encode_bits_map(CUtensorMap *m, const uint64_t *rows, int64_t N, int64_t stride) {
+    auto enc = get_encoder();
+    if (!enc) {
+        set_error("action_tc: cuTensorMapEncodeTiled is unavailable");
+        return CSG_E_CUDA;
+    }
+    if ((reinterpret_cast<uintptr_t>(rows) & 15) != 0 || stride % 2 != 0) {
+        set_error("action_tc: relation rows are not 16-byte aligned");
+        return CSG_E_INVAL;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)stride, (cuuint64_t)N};
+    cuuint64_t strides[1] = {(cuuint64_t)stride * 8};
+    cuuint32_t box[2] = {(cuuint32_t)(BN / 64), (cuuint32_t)BM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<uint64_t *>(rows), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("action_tc: tensor map encoding failed (%d)", (int)r);
+        return CSG_E_CUDA;
+    }
+    return CSG_OK;
+}
+
 }  // namespace
 
 // Largest N the tensor form accepts (every N a set can have): its operands take N^2
@@ -926,7 +988,7 @@ TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned
     p.chunks.push_back(cur);
     max_chunk = std::max(max_chunk, chunk_bytes);
     p.t_sets = a.put(desc.data(), n * sizeof(TcSetDesc));
-    p.t_maps = a.put(nullptr, 2 * (size_t)n * sizeof(CUtensorMap));
+    p.t_maps = a.put(nullptr, 3 * (size_t)n * sizeof(CUtensorMap));
     p.s_ops = a.reserve((size_t)max_chunk);
     p.s_queues = a.reserve(p.chunks.size() * sizeof(unsigned int));
     for (TcPlan::Chunk &c : p.chunks) {
@@ -984,8 +1046,9 @@ int tc_patch(const TcPlan &p, Arena &a) {
         D.counters = a.scr<unsigned long long>(p.s_counters) + (size_t)(p.slot.empty() ? s : p.slot[s]) * CNT_WORDS;
         D.U = ops + reinterpret_cast<uintptr_t>(D.U);
         D.P = ops + reinterpret_cast<uintptr_t>(D.P);
-        int rc = encode_map(&maps[2 * s], D.U, D.N, D.kp, BM);
-        if (rc == CSG_OK) rc = encode_map(&maps[2 * s + 1], D.P, D.N, D.kp, BN / 2);  // each CTA's half
+        int rc = encode_map(&maps[3 * s], D.U, D.N, D.kp, BM);
+        if (rc == CSG_OK) rc = encode_map(&maps[3 * s + 1], D.P, D.N, D.kp, BN / 2);  // each CTA's half
+        if (rc == CSG_OK) rc = encode_bits_map(&maps[3 * s + 2], D.rows, D.N, D.stride);
         if (rc != CSG_OK) return rc;
     }
     return CSG_OK;
@@ -993,7 +1056,7 @@ int tc_patch(const TcPlan &p, Arena &a) {
 
 template <int FMT>
 static int tc_launch_fmt(const TcPlan &p, const Arena &a, cudaStream_t st) {
-    const size_t smem = 1024 + STAGES * STAGE_BYTES + 512;
+    const size_t smem = 1024 + STAGES * STAGE_BYTES + RING * BITS_BYTES + 512;
     CSG_CUDA_TRY(cudaFuncSetAttribute(action_tc_kernel<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // CTA pairs (clusters of two, one CTA per SM) that can be resident at once
     int clusters = 0;
