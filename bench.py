@@ -315,6 +315,39 @@ def bench_desitter(args):
     return 0
 
 
+def bench_sizes(args):
+    """Interval-count throughput against set size: K linked d=4/d=2 diamonds of one size
+    (K N^3 fixed near 2.7e11 for N <= 8192), counted in one batch launch; the stage time of the
+    counting kernel alone (operand expansion reported beside it), in algorithmic tensor
+    flops 2 C(N,3) per set.  Small sets show the per-tile cost of the tensor form: each
+    256 x 256 tile drains its accumulator and books its pairs however short its K range."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1709_03013_gb300 import csg
+    rows = []
+    with csg.Context(0) as ctx:
+        for N, K in ((512, 2048), (1024, 1024), (2048, 512), (4096, 128), (8192, 32), (16384, 8), (32768, 2)):
+            sets = [ctx.sprinkle(2 + 2 * (k % 2), N, 99, k).link() for k in range(K)]
+            torch.cuda.synchronize()
+            flops = K * 2.0 * math.comb(N, 3)
+            row = {"N": N, "sets": K}
+            for name, m in (("tc4", csg.TC_FP4), ("tc8", csg.TC_FP8), ("popc", csg.POPC)):
+                ctx.action_batch(sets, m)
+                ctx.set_timing(True)
+                ctx.action_batch(sets, m)
+                st = ctx.stage_times()
+                ctx.set_timing(False)
+                a = st.get("action") or float("nan")
+                row[name] = {"action_ms": a, "expand_ms": st.get("expand"), "tflops": flops / (a * 1e-3) / 1e12}
+            rows.append(row)
+            for x in sets:
+                x.free()
+    print(json.dumps({"experiment": "interval counts against set size (batch launches of equal sets)",
+                      "unit": "algorithmic TFLOP/s (2 C(N,3) per set)", "sizes": rows}), flush=True)
+    return 0
+
+
 def bench_dalembertian(args):
     """Cost of the discrete d'Alembertian (Eq. b_local) beside the plain interval counts on
     the d=2 N=131072 set (seed 2): the layer sums ride on the counting pass, so the extra
@@ -455,7 +488,7 @@ def main():
     ap.add_argument("--d", type=int, default=4)
     ap.add_argument("--n", type=int, default=40000)
     ap.add_argument("--reps", type=int, default=2)
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "desitter", "dalembertian"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "desitter", "dalembertian", "sizes"],
                     help="single: the d=4 N=65536 set; batch: 4096 mixed diamonds, plain vs batched; "
                          "serve: Poisson request stream through the service, p50/p99 latency")
     ap.add_argument("--n-sets", type=int, default=4096)
@@ -476,6 +509,9 @@ def main():
         return 0
     if args.workload == "dalembertian":
         bench_dalembertian(args)
+        return 0
+    if args.workload == "sizes":
+        bench_sizes(args)
         return 0
     if args.warmup < 3:
         args.warmup = 3
