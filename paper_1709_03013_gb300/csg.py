@@ -9,8 +9,8 @@ which is the only role PyTorch plays here besides device memory.
 from __future__ import annotations
 
 import ctypes
+from typing import NamedTuple
 import os
-from dataclasses import dataclass
 
 import numpy as np
 
@@ -36,8 +36,8 @@ class _Result(ctypes.Structure):
                 ("W", ctypes.c_uint64), ("combo", ctypes.c_int64), ("S", ctypes.c_double)]
 
 
-@dataclass
-class Result:
+class Result(NamedTuple):
+    """One set's counts and action (a csg_result)."""
     d: int
     N: int
     R: int
@@ -52,6 +52,31 @@ class Result:
     def of(r: _Result) -> "Result":
         return Result(d=r.d, N=r.N, R=r.R, Nk=tuple(int(x) for x in r.Nk), sum_m=r.sum_m, W=r.W,
                       combo=r.combo, S=r.S, status=r.status)
+
+
+# numpy view of a csg_result array (field offsets as laid out by ctypes)
+_RESULT_DTYPE = np.dtype({
+    "names": ["d", "status", "N", "R", "Nk", "sum_m", "W", "combo", "S"],
+    "formats": [np.int32, np.int32, np.int64, np.uint64, (np.uint64, 4), np.uint64, np.uint64, np.int64,
+                np.float64],
+    "offsets": [_Result.d.offset, _Result.status.offset, _Result.N.offset, _Result.R.offset,
+                _Result.Nk.offset, _Result.sum_m.offset, _Result.W.offset, _Result.combo.offset,
+                _Result.S.offset],
+    "itemsize": ctypes.sizeof(_Result)})
+
+
+def _results(buf, n: int) -> list:
+    """Result objects of the first n entries of a ctypes csg_result array, converted column
+    by column (one Python object per set, no per-field ctypes access)."""
+    if n == 0:
+        return []
+    a = np.frombuffer(buf, dtype=_RESULT_DTYPE, count=n)
+    k = a["Nk"]
+    nk = list(zip(k[:, 0].tolist(), k[:, 1].tolist(), k[:, 2].tolist(), k[:, 3].tolist()))
+    make = tuple.__new__
+    return [make(Result, t) for t in zip(a["d"].tolist(), a["N"].tolist(), a["R"].tolist(), nk,
+                                         a["sum_m"].tolist(), a["W"].tolist(), a["combo"].tolist(),
+                                         a["S"].tolist(), a["status"].tolist())]
 
 
 EXPORTS = [
@@ -292,7 +317,7 @@ class Context:
         res = (_Result * max(n, 1))()
         _check(load().csg_action_batch(self.handle, arr, n, method, res, _stream(stream)),
                "csg_action_batch")
-        return [Result.of(res[k]) for k in range(n)]
+        return _results(res, n)
 
     def run_batch(self, specs, method: int = POPC, stream=None) -> list[Result]:
         """specs: iterable of (d, N, seed, seq)."""
@@ -306,7 +331,7 @@ class Context:
         p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
         _check(load().csg_run_batch(self.handle, n, p(d), p(N), p(seed), p(seq), method, res,
                                     _stream(stream)), "csg_run_batch")
-        return [Result.of(res[k]) for k in range(n)]
+        return _results(res, n)
 
     def serve_submit(self, d: int, N: int, seed: int, seq: int = 0) -> int:
         t = ctypes.c_uint64()

@@ -69,3 +69,22 @@ def test_strerror_and_argument_errors_without_gpu(lib):
     assert L.csg_link(None, None, None) == csg.E_INVAL
     assert L.csg_action(None, None, 0, None, None) == csg.E_INVAL
     assert L.csg_set_info(None, None, None, None, None, None) == csg.E_INVAL
+
+
+def test_bulk_result_conversion_matches_per_field():
+    """The batch calls convert their csg_result arrays column by column through a numpy view;
+    every field of every entry must equal the field-by-field ctypes conversion."""
+    from paper_1709_03013_gb300 import csg
+    n = 37
+    res = (csg._Result * n)()
+    for k in range(n):
+        r = res[k]
+        r.d, r.status, r.N, r.R = 2 + 2 * (k % 2), -k if k % 5 == 0 else 0, 1000 + k, 3 * k
+        for q in range(4):
+            r.Nk[q] = k * 10 + q
+        r.sum_m, r.W, r.combo, r.S = 2 ** 63 + k, 2 ** 40 + k, -7 * k, 0.5 * k - 3.25
+    got = csg._results(res, n)
+    want = [csg.Result.of(res[k]) for k in range(n)]
+    assert got == want
+    assert all(isinstance(x, csg.Result) and isinstance(x.Nk, tuple) for x in got)
+    assert csg._results(res, 0) == []
