@@ -271,7 +271,7 @@ def bench_batch(args, emit=True):
     line = {"metric": METRIC, "value": R / (times["batched"] / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": times["batched"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {0: "u64", 3: "fp4"}.get(method, "fp8"), "data": "synthetic",
+            "dtype": {0: "u64", 2: "fp8"}.get(method, "fp4"), "data": "synthetic",
             "config": {"workload": f"batch: {len(specs)} flat diamonds, d alternating 2/4, N log-uniform "
                                    f"in [256, 8192], seed 3 (sprinkle+sort+link+action per set)",
                        "method": args.method, "sets": len(specs), "sum_R": R, "sum_W": W},
@@ -460,7 +460,7 @@ def bench_serve(args, emit=True):
     R = sum(r.R for r in res_b)
     line = {"metric": METRIC, "value": R / cap_s, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": cap_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "fp8", "data": "synthetic",
+            "dtype": "fp4", "data": "synthetic",
             "config": {"workload": f"serve: {len(specs)} requests, d in {{2,4}} 50/50, N log-uniform in "
                                    f"[1024, 65536], Poisson arrivals, seed 4, 160 GB admission budget",
                        "method": "tc"},
@@ -615,7 +615,7 @@ def main():
     clocks = clk.summary()
     sm_max = (clocks or {}).get("sm_max_mhz") or pk.get("sm_max_mhz") or 2070.0
     popc_peak = SMS * POPC_PER_SM_CLK * 32 * sm_max * 1e6          # bit-ops/s
-    fp4 = method == csg.TC_FP4
+    fp4 = method in (csg.TC, csg.TC_FP4)  # the tensor form's default format is fp4
     # the contraction's own dtype: measured bf16 dense burst x the nominal ratio (fp8 2, fp4 6)
     tc_peak = (6.0 if fp4 else 2.0) * pk.get("bf16_tflops", 1900.0)
     tc_flops = 2.0 * math.comb(N, 3)                                # triangle-restricted contraction
