@@ -94,80 +94,124 @@ struct Keys {
     uint32_t *idx;
 };
 
+// One attempt of element e of set S (Sec. 2.1): returns true when the element is settled
+// (accepted, a single-draw geometry, or out of attempts) with its coordinates in c.
+__device__ __forceinline__ bool sprinkle_attempt(const SetRow &S, int64_t e, int a, double (&c)[4]) {
+    if (S.d == GEOM_DS2) {
+        // 1+1 de Sitter slab (Sec. 5.1): eta by inverting the sec^2 distribution,
+        // theta uniform on the circle; rows eta, theta, 0, 0
+        U64x4 r = philox4x64_10((uint64_t)e, 0, 0, 0, S.seed, S.seq);
+        c[0] = atan(__dmul_rn(S.param, __dsub_rn(__dmul_rn(2.0, unit53(r.w[0])), 1.0)));
+        c[1] = __dmul_rn(6.283185307179586, unit53(r.w[1]));
+        c[2] = 0.0;
+        c[3] = 0.0;
+        return true;
+    }
+    if (S.d == 2) {
+        U64x4 r = philox4x64_10((uint64_t)e, 0, 0, 0, S.seed, S.seq);
+        double u = unit53(r.w[0]), v = unit53(r.w[1]);
+        c[0] = __dmul_rn(__dadd_rn(u, v), 0.5);
+        c[1] = __dmul_rn(__dsub_rn(v, u), 0.5);
+        c[2] = u;
+        c[3] = v;
+        return true;
+    }
+    U64x4 r = philox4x64_10((uint64_t)e, (uint64_t)a, 0, 0, S.seed, S.seq);
+    // fp32 screen: the top 24 bits of each word give the coordinate within 2^-23, and the
+    // screened sum is within 2e-6 of the fp64 one; attempts closer than 4e-6 to the
+    // boundary take the exact fp64 test (the decision is the fp64 one)
+    const float tf = __fmaf_rn((float)(uint32_t)(r.w[0] >> 40), 0x1.0p-23f, -1.0f);
+    const float xf = __fmaf_rn((float)(uint32_t)(r.w[1] >> 40), 0x1.0p-23f, -1.0f);
+    const float yf = __fmaf_rn((float)(uint32_t)(r.w[2] >> 40), 0x1.0p-23f, -1.0f);
+    const float zf = __fmaf_rn((float)(uint32_t)(r.w[3] >> 40), 0x1.0p-23f, -1.0f);
+    const float sf = fabsf(tf) + sqrtf(__fmaf_rn(xf, xf, __fmaf_rn(yf, yf, zf * zf)));
+    bool accept = false;
+    if (sf <= 1.0f + 4e-6f) {
+        const double t = __dsub_rn(__dmul_rn(2.0, unit53(r.w[0])), 1.0);
+        const double x = __dsub_rn(__dmul_rn(2.0, unit53(r.w[1])), 1.0);
+        const double y = __dsub_rn(__dmul_rn(2.0, unit53(r.w[2])), 1.0);
+        const double z = __dsub_rn(__dmul_rn(2.0, unit53(r.w[3])), 1.0);
+        accept = sf < 1.0f - 4e-6f;
+        if (!accept) {
+            const double rr = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+            accept = __dadd_rn(fabs(t), rr) <= 1.0;
+        }
+        if (accept) {
+            c[0] = t;
+            c[1] = x;
+            c[2] = y;
+            c[3] = z;
+            return true;
+        }
+    }
+    if (a + 1 >= 256) {  // out of attempts: the set reports CSG_E_REJECT
+        atomicExch(S.err, (unsigned long long)CNT_ERR_REJECT);
+        c[0] = c[1] = c[2] = c[3] = 0.0;
+        return true;
+    }
+    return false;
+}
+
 // Sprinkle (or take host coordinates) into the unsorted buffer and emit sort keys.
 // tmp is [4][E] (row r of set s at tmp + r*E + off).
+// Each warp takes runs of `run` elements; a lane works on one element at a time, attempt
+// after attempt (d=4 rejection sampling accepts 13 % of draws), and a lane whose element is
+// settled takes the run's next element, so the warp's lanes stay busy instead of all waiting
+// for the element that needs the most draws.  Attempt a of element e always uses the
+// same counter (e, a), so the coordinates do not depend on which lane draws them.
 __global__ void sprinkle_keys_kernel(const SetRow *__restrict__ sets, const int64_t *__restrict__ starts,
                                      int n, int64_t E, double *__restrict__ tmp, Keys keys,
-                                     int from_coords) {
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < E;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int s = find_set(starts, n, g);
-        const SetRow S = sets[s];
-        const int64_t e = g - S.off;
-        double c0, c1, c2, c3;
-        if (from_coords) {
-            c0 = tmp[g];
-            c1 = tmp[E + g];
-            c2 = tmp[2 * E + g];
-            c3 = tmp[3 * E + g];
-        } else if (S.d == GEOM_DS2) {
-            // 1+1 de Sitter slab (Sec. 5.1): eta by inverting the sec^2 distribution,
-            // theta uniform on the circle; rows eta, theta, 0, 0
-            U64x4 r = philox4x64_10((uint64_t)e, 0, 0, 0, S.seed, S.seq);
-            c0 = atan(__dmul_rn(S.param, __dsub_rn(__dmul_rn(2.0, unit53(r.w[0])), 1.0)));
-            c1 = __dmul_rn(6.283185307179586, unit53(r.w[1]));
-            c2 = 0.0;
-            c3 = 0.0;
-        } else if (S.d == 2) {
-            U64x4 r = philox4x64_10((uint64_t)e, 0, 0, 0, S.seed, S.seq);
-            double u = unit53(r.w[0]), v = unit53(r.w[1]);
-            c0 = __dmul_rn(__dadd_rn(u, v), 0.5);
-            c1 = __dmul_rn(__dsub_rn(v, u), 0.5);
-            c2 = u;
-            c3 = v;
-        } else {
-            bool found = false;
-            c0 = c1 = c2 = c3 = 0.0;
-            for (int a = 0; a < 256 && !found; ++a) {
-                U64x4 r = philox4x64_10((uint64_t)e, (uint64_t)a, 0, 0, S.seed, S.seq);
-                // fp32 screen: the top 24 bits of each word give the coordinate within 2^-23,
-                // and the screened sum is within 2e-6 of the fp64 one; attempts closer than
-                // 4e-6 to the boundary take the exact fp64 test (the decision is the fp64 one)
-                const float tf = __fmaf_rn((float)(uint32_t)(r.w[0] >> 40), 0x1.0p-23f, -1.0f);
-                const float xf = __fmaf_rn((float)(uint32_t)(r.w[1] >> 40), 0x1.0p-23f, -1.0f);
-                const float yf = __fmaf_rn((float)(uint32_t)(r.w[2] >> 40), 0x1.0p-23f, -1.0f);
-                const float zf = __fmaf_rn((float)(uint32_t)(r.w[3] >> 40), 0x1.0p-23f, -1.0f);
-                const float sf = fabsf(tf) + sqrtf(__fmaf_rn(xf, xf, __fmaf_rn(yf, yf, zf * zf)));
-                if (sf > 1.0f + 4e-6f) continue;
-                double t = __dsub_rn(__dmul_rn(2.0, unit53(r.w[0])), 1.0);
-                double x = __dsub_rn(__dmul_rn(2.0, unit53(r.w[1])), 1.0);
-                double y = __dsub_rn(__dmul_rn(2.0, unit53(r.w[2])), 1.0);
-                double z = __dsub_rn(__dmul_rn(2.0, unit53(r.w[3])), 1.0);
-                bool accept = sf < 1.0f - 4e-6f;
-                if (!accept) {
-                    double rr = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)),
-                                                     __dmul_rn(z, z)));
-                    accept = __dadd_rn(fabs(t), rr) <= 1.0;
+                                     int from_coords, int64_t run) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r0 = warp * run; r0 < E; r0 += warps * run) {
+        const int64_t r1 = r0 + run < E ? r0 + run : E;
+        int64_t g = r0 + lane;   // this lane's element (>= r1: idle)
+        int64_t next = r0 + 32;  // the run's next unassigned element
+        int a = 0;
+        int s = g < r1 ? find_set(starts, n, g) : 0;
+        SetRow S = sets[s];
+        while (__any_sync(0xffffffffu, g < r1)) {
+            bool done = false;
+            if (g < r1) {
+                const int64_t e = g - S.off;
+                double c[4];
+                if (from_coords) {
+                    c[0] = tmp[g];
+                    c[1] = tmp[E + g];
+                    c[2] = tmp[2 * E + g];
+                    c[3] = tmp[3 * E + g];
+                    done = true;
+                } else {
+                    done = sprinkle_attempt(S, e, a, c);
+                    if (done) {
+                        tmp[g] = c[0];
+                        tmp[E + g] = c[1];
+                        tmp[2 * E + g] = c[2];
+                        tmp[3 * E + g] = c[3];
+                    }
                 }
-                if (accept) {
-                    c0 = t;
-                    c1 = x;
-                    c2 = y;
-                    c3 = z;
-                    found = true;
+                if (done) {
+                    keys.k1[g] = order_key(c[0]);
+                    keys.k2[g] = (S.d == 2) ? order_key(c[2]) : 0ULL;
+                    keys.idx[g] = (uint32_t)e;
+                } else {
+                    ++a;
                 }
             }
-            if (!found) atomicExch(S.err, (unsigned long long)CNT_ERR_REJECT);
+            const uint32_t dm = __ballot_sync(0xffffffffu, done);
+            if (done) {
+                g = next + __popc(dm & below);
+                a = 0;
+                if (g < r1) {
+                    s = find_set(starts, n, g);
+                    S = sets[s];
+                }
+            }
+            next += __popc(dm);
         }
-        if (!from_coords) {
-            tmp[g] = c0;
-            tmp[E + g] = c1;
-            tmp[2 * E + g] = c2;
-            tmp[3 * E + g] = c3;
-        }
-        keys.k1[g] = order_key(c0);
-        keys.k2[g] = (S.d == 2) ? order_key(c2) : 0ULL;
-        keys.idx[g] = (uint32_t)e;
     }
 }
 
@@ -348,8 +392,13 @@ void sprinkle_launch(const SprinklePlan &p, const Arena &a, cudaStream_t st) {
     Keys ka{kb, kb + E, ib}, kb2{kb + 2 * E, kb + 3 * E, ib + E};
     const int T = 256;
     stage_begin(CSG_STAGE_SPRINKLE, st);
-    sprinkle_keys_kernel<<<grid_for(E, T), T, 0, st>>>(d_rows, d_starts, p.n, E, tmp, ka,
-                                                       p.from_coords ? 1 : 0);
+    // runs of 32 .. 1024 elements per warp: long runs keep the lanes busy through the d=4
+    // rejection draws, and about 4864 warps (32 per SM) keep the SMs busy
+    int64_t run = (E / 4864 + 31) / 32 * 32;
+    run = run < 32 ? 32 : (run > 1024 ? 1024 : run);
+    const int64_t nwarp = (E + run - 1) / run;
+    sprinkle_keys_kernel<<<(unsigned)((nwarp + T / 32 - 1) / (T / 32)), T, 0, st>>>(d_rows, d_starts, p.n, E, tmp,
+                                                                                ka, p.from_coords ? 1 : 0, run);
     chunk_sort_kernel<<<(unsigned)p.C, kSortThreads, 0, st>>>(d_rows, d_cstarts, p.n, ka, kb2);
     Keys cur = kb2, nxt = ka;
     for (int64_t w = kChunk; w < p.maxN; w *= 2) {
