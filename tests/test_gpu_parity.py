@@ -178,6 +178,25 @@ def test_batch_equals_single(ctx, csg):
         s.free()
 
 
+def test_batch_degenerate_and_empty(ctx, csg):
+    """Empty batches, and batches of the degenerate sizes N = 1, 2, 3 mixed with sets that
+    span several tiles and ragged tails, in every method: each result equals the set alone
+    and the oracle."""
+    assert ctx.run_batch([], csg.TC) == [] and ctx.action_batch([], csg.POPC) == []
+    specs = [(2, 1, 7, 0), (4, 1, 7, 1), (2, 2, 7, 2), (4, 3, 7, 3), (2, 257, 7, 4), (4, 700, 7, 5),
+             (2, 3, 7, 6), (4, 2, 7, 7), (2, 1500, 7, 8)]
+    for method in (csg.POPC, csg.TC, csg.TC_FP8):
+        got = ctx.run_batch(specs, method)
+        for (d, N, seed, seq), r in zip(specs, got):
+            want = oracle.run(d, N, seed, seq)
+            _check_result(r, want, d, N)
+    sets = [ctx.sprinkle(d, N, seed, seq).link() for d, N, seed, seq in specs]
+    for method in (csg.POPC, csg.TC_FP4):
+        assert ctx.action_batch(sets, method) == [x.action(method) for x in sets]
+    for x in sets:
+        x.free()
+
+
 def test_serve_alone_equals_in_mix(ctx, csg):
     specs = inputs.batch_workload(n_sets=40, seed=11, lo=32, hi=2500)
     alone = [ctx.run_batch([(sp.d, sp.N, sp.seed, sp.seq)])[0] for sp in specs]
