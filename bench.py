@@ -146,12 +146,13 @@ def reduce_over_ranks(dist, ms: float, units: float, device) -> tuple[float, flo
 
 
 def launches_per_step(N: int, tc: bool) -> int:
-    # sprinkle+keys, chunk ranking, merge passes, gather; link; [expand]; action; finalize
+    # sprinkle+keys, chunk sort, merge passes, gather; link screen values, link; [expand];
+    # action; finalize
     passes, w = 0, 1024
     while w < N:
         passes += 1
         w *= 2
-    return 3 + passes + 1 + (1 if tc else 0) + 2
+    return 3 + passes + 2 + (1 if tc else 0) + 2
 
 
 def cpu_baseline(threads: int = 0, rows_per_block: int = 64, blocks: int = 8):
