@@ -58,6 +58,76 @@ def peaks():
         return {}
 
 
+class NvmlClockSampler:
+    """Samples the SM clock and the clock-event (throttle) reasons through NVML every few
+    milliseconds while running (read-only queries; nothing is set).  Raises OSError when
+    NVML cannot be used, so the caller can fall back to nvidia-smi."""
+
+    # nvmlClocksEventReasons bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, cuda_index: int, period_s: float = 0.002):
+        import ctypes
+        self.period = period_s
+        try:
+            self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+        except OSError as e:
+            raise OSError(f"NVML unavailable: {e}")
+        if self.nv.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.handle = ctypes.c_void_p()
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+        target = vis[cuda_index].strip() if cuda_index < len(vis) and vis[cuda_index].strip() else str(cuda_index)
+        if target.startswith("GPU-"):
+            rc = self.nv.nvmlDeviceGetHandleByUUID(target.encode(), ctypes.byref(self.handle))
+        else:
+            rc = self.nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(int(target)), ctypes.byref(self.handle))
+        if rc != 0:
+            self.nv.nvmlShutdown()
+            raise OSError("no NVML handle for the device")
+        mx = ctypes.c_uint()
+        self.max_mhz = float(mx.value) if self.nv.nvmlDeviceGetMaxClockInfo(self.handle, 1, ctypes.byref(mx)) == 0 else None
+        self.fn_reasons = getattr(self.nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(self.nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        self.sm, self.masks = [], []
+        self._stop = threading.Event()
+
+    def _run(self):
+        import ctypes
+        mhz, mask = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if self.nv.nvmlDeviceGetClockInfo(self.handle, 1, ctypes.byref(mhz)) == 0:
+                self.sm.append(float(mhz.value))
+                self.masks.append(mask.value if self.fn_reasons(self.handle, ctypes.byref(mask)) == 0 else 0)
+            time.sleep(self.period)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=2)
+        self.nv.nvmlShutdown()
+
+    def summary(self):
+        if not self.sm:
+            return None
+        reasons = sorted({nm for m in self.masks for bit, nm in self.REASONS.items() if m & bit})
+        return {"sm_mhz": statistics.median(self.sm), "sm_max_mhz": self.max_mhz or max(self.sm),
+                "reasons": reasons, "samples": len(self.sm), "source": "nvml, 2 ms period"}
+
+
+def clock_sampler(cuda_index: int):
+    """NVML sampling when the library can be loaded, else nvidia-smi."""
+    try:
+        return NvmlClockSampler(cuda_index)
+    except (OSError, AttributeError, ValueError):
+        return ClockSampler(cuda_index)
+
+
 class ClockSampler:
     """Samples SM clocks and throttle reasons with nvidia-smi while running."""
 
@@ -223,6 +293,25 @@ def profile_action(args):
             res = s.action(method)
             print(r, res.R, res.Nk, res.W, f"{(time.perf_counter() - t0) * 1e3:.2f} ms", flush=True)
         s.free()
+    return 0
+
+
+def profile_batch(args):
+    """A fixed workload for ncu launch lists of the batch: the 4096-set batch (seed 3) built
+    into its CUDA graph with the default tuning (autotuning off, so no candidate runs), then
+    --reps replays."""
+    os.environ["CSG_AUTOTUNE"] = "0"
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1709_03013_gb300 import csg, inputs
+    method = METHODS[args.method]
+    specs = [(s.d, s.N, s.seed, s.seq) for s in inputs.batch_workload(n_sets=args.n_sets)]
+    with csg.Context(0) as ctx:
+        for r in range(args.reps + 1):
+            t0 = time.perf_counter()
+            res = ctx.run_batch(specs, method)
+            print("build" if r == 0 else f"replay {r}", sum(x.R for x in res),
+                  f"{(time.perf_counter() - t0) * 1e3:.2f} ms", flush=True)
     return 0
 
 
@@ -484,6 +573,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the batch and serve summaries of the default line")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="profiling driver: the 4096-set batch graph, then --reps replays")
     ap.add_argument("--profile-action", action="store_true",
                     help="profiling driver: one sprinkled set, then --reps action launches")
     ap.add_argument("--d", type=int, default=4)
@@ -499,6 +590,8 @@ def main():
     args = ap.parse_args()
     if args.profile_action:
         return profile_action(args)
+    if args.profile_batch:
+        return profile_batch(args)
     if args.workload == "batch":
         bench_batch(args)
         return 0
@@ -562,7 +655,7 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stage_ms = {k: 0.0 for k in csg.Context.STAGES}
     results = []
-    with ClockSampler(local) as clk:
+    with clock_sampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
             results.append(step())
