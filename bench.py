@@ -242,7 +242,25 @@ def cpu_baseline(threads: int = 0, rows_per_block: int = 64, blocks: int = 8):
         elapsed += time.perf_counter() - t0
         pairs += out["R"]
     cores = threads or os.cpu_count()
-    return {"value": pairs / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle",
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for ln in fh:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"value": pairs / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": model,
             "sample": f"{blocks} blocks of {rows_per_block} rows (first elements) spread over the N=65536 "
                       f"d=4 set; {pairs} related pairs in {elapsed:.2f} s; matrix built by the oracle's link"}
 
@@ -655,15 +673,19 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stage_ms = {k: 0.0 for k in csg.Context.STAGES}
     results = []
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with clock_sampler(local) as clk:
         ev0.record(stream)
-        for _ in range(args.steps):
+        step_ev[0].record(stream)
+        for k_step in range(args.steps):
             results.append(step())
+            step_ev[k_step + 1].record(stream)
             for k, v in ctx.stage_times().items():
                 stage_ms[k] += v or 0.0
         ev1.record(stream)
         barrier()
     ms = ev0.elapsed_time(ev1)
+    step_times = [step_ev[k].elapsed_time(step_ev[k + 1]) for k in range(args.steps)]
     R_total = sum(r.R for r in results)
     if dist is not None:
         ms, R_total = reduce_over_ranks(dist, ms, R_total, torch.device("cuda", local))
@@ -728,7 +750,9 @@ def main():
                               "(MEASURED_PEAKS.json; nominal dense ratio), of measured")}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "step_ms": {"min": min(step_times), "median": statistics.median(step_times), "max": max(step_times)},
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": ("fp4" if fp4 else "fp8") if is_tc else "u64",
         "data": "synthetic",
