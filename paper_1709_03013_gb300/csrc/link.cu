@@ -21,16 +21,20 @@
 // its expanded form,
 //     e = p - h_k - h_i = -s^2 / 2,   p = t_k t_i - x_k x_i - y_k y_i - z_k z_i,
 //     h = (t^2 - x^2 - y^2 - z^2) / 2 (formed in double, rounded once to float),
-// as one float add and four fused multiply-adds on packed pairs of columns
-// (f32x2), and takes the relation from the sign bit of e (a funnel shift packs 32
-// sign bits into a word).  With every |coordinate| <= S (S >= 1), u = 2^-24: rounding
-// the coordinates to float moves the four products by at most 2u * 4 S^2; |h| <= 1.5 S^2,
-// so rounding the two h moves e by at most 3u S^2; the first add (|sum| <= 3 S^2) rounds by
-// at most 3u S^2 and the four fused multiply-adds (partial sums below 4, 5, 6, 7 S^2) by
-// 22u S^2.  So |e + s^2/2| <= 36u S^2 < 2.2e-6 S^2 (plus terms of order u^2), the double
-// predicate is within 1e-14 S^2 of the real one, and |e| > 3e-6 S^2 fixes the double
-// decision.  A word whose smallest |e| is within that margin is redone pair by pair, and
-// only its pairs inside the margin are evaluated in double.
+// as one float add and four fused multiply-adds on packed pairs of columns (f32x2).
+// Error bound, with every |coordinate| <= S (S >= 1) and u = 2^-24: rounding the
+// coordinates to float moves the four products by at most 2u * 4 S^2; |h| <= 1.5 S^2, so
+// rounding the two h moves e by at most 3u S^2; the first add (|sum| <= 3 S^2) rounds by at
+// most 3u S^2 and the four fused multiply-adds (partial sums below 4, 5, 6, 7 S^2) by 22u S^2.
+// So |fl(e) + s^2/2| <= 36u S^2 < 2.2e-6 S^2 (plus terms of order u^2), while the double
+// predicate is within 1e-14 S^2 of the real one.  With the margin m = 4e-6 S^2 (every word
+// of a d=4 tile, words on the diagonal and ragged words included, under a column mask):
+//   * the rows carry fl(-h_i + m), so the chain gives e' ~ e + m within
+//     37.5u S^2 < 2.3e-6 S^2 (one more rounding).  A sign bit of e' (e' <= 0) means
+//     s^2 / 2 >= m - 2.3e-6 S^2 > 0: certainly related.  A clear sign bit of
+//     fl(e' - 2m) means e' >= 2m - 7u S^2, hence -s^2 / 2 >= m - 2.7e-6 S^2 > 0:
+//     certainly unrelated.  The funnel-shifted sign words give both per pair, and only the
+//     pairs between them are evaluated in double (from shared memory).
 //
 // d=2 (flat diamond): related iff u_i < u_k and v_i < v_k (light-cone coordinates) in
 // double.  Rounding to float keeps order (x <= y => fl(x) <= fl(y)) and the float
@@ -195,8 +199,9 @@ __device__ __forceinline__ bool exact_pair(const double (*rd)[kTile], const doub
 }
 
 // One 64-column word of tile row rt evaluated pair by pair: bit b set iff the row and
-// column 64 q + b are related; columns outside [c0, ncol) stay 0.  Used for the words on
-// and beside the diagonal, the ragged last column block and the de Sitter slab.  cf: the
+// column 64 q + b are related; columns outside [c0, ncol) stay 0.  Used for the de Sitter
+// slab (d=2 and d=4 words go through the packed screen); for d=4 it would decide |e| > m
+// in float (the bound above) and the rest in double.  cf: the
 // tile's column screen values (d=2 negated); Fs: the set's screen values (row i's read).
 template <int D>
 __device__ __noinline__ uint64_t word_by_pair(int q, int c0, int ncol, const float (*cf)[kTile],
