@@ -145,7 +145,8 @@ void worker_main(ServeState *S) {
             std::lock_guard<std::mutex> lk(S->mu);
             S->reserved -= bytes;
         }
-        // the tensor form is the faster one wherever its operands fit (N <= 2^17)
+        // the tensor form is the faster one; above N = 2^17 its operand scratch (N^2 bytes, 16 to
+        // 64 GiB a set) is not part of the admission budget, so such batches take the popcount form
         int method = CSG_TC;
         for (csg_set *x : sets)
             if (x->N > (1 << 17)) method = CSG_POPC;
