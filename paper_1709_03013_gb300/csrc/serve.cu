@@ -2,13 +2,15 @@
 // service built on it.
 //
 // The service does continuous batching: csg_serve_submit only queues a request.
-// A small pool of worker threads, each with its own CUDA stream, repeatedly takes
-// the queued requests that fit the context's memory budget (admission by the set's
-// footprint, N*N/8 bytes of bitmap plus coordinates), up to a work cap per batch,
-// and runs the whole path for them in shared launches.  Requests that arrive while
-// other batches are on the GPU are admitted by the next free worker as soon as
-// memory frees up, so their kernels overlap on the device.  Results are kept per
-// ticket until csg_serve_poll collects them.
+// A small pool of worker threads repeatedly takes queued requests that fit the
+// context's memory budget (admission by the set's footprint, N*N/8 bytes of bitmap plus
+// coordinates), up to a work cap per batch, and runs the whole path for them in shared
+// launches.  The oldest queued request opens each batch and only requests within a factor
+// of two of its size join it, so small requests are not held back by a large one's
+// results; batches of small sets run on a high-priority stream.  Requests that arrive
+// while other batches are on the GPU are admitted by the next free worker as soon as
+// memory frees up, so their kernels overlap on the device.  Results are kept per ticket
+// until csg_serve_poll collects them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -66,6 +68,7 @@ struct ServeState {
     size_t max_queue = 1 << 20;
     double batch_work_cap = 1e14;      // flops per batch (about 30 ms on the tensor form)
     int batch_max_sets = 4096;
+    int64_t small_n = 16384;           // batches of sets up to this size run at high priority
 };
 
 namespace {
@@ -73,8 +76,13 @@ namespace {
 void worker_main(ServeState *S) {
     csg_ctx *ctx = S->ctx;
     cudaSetDevice(ctx->device);
-    cudaStream_t st = nullptr;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    // two streams: batches of small sets go on the high-priority one, so their kernels'
+    // blocks are scheduled first whenever a large batch's short kernels leave SMs free
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    cudaStream_t st_lo = nullptr, st_hi = nullptr;
+    cudaStreamCreateWithPriority(&st_lo, cudaStreamNonBlocking, prio_lo);
+    cudaStreamCreateWithPriority(&st_hi, cudaStreamNonBlocking, prio_hi);
     std::vector<uint64_t> batch;
     for (;;) {
         batch.clear();
@@ -83,13 +91,21 @@ void worker_main(ServeState *S) {
             std::unique_lock<std::mutex> lk(S->mu);
             for (;;) {
                 if (S->stop) break;
-                // admit from the head of the queue while memory and the work cap allow
+                // The oldest queued request opens the batch; later ones join it while memory and
+                // the work cap allow, if their size is within a factor of two of the first's, so a
+                // small request never waits for a large one's results (a batch's results are
+                // ready together).  Requests passed over keep their place in the queue.
                 double work = 0.0;
-                while (!S->queue.empty() && (int)batch.size() < S->batch_max_sets) {
-                    const uint64_t t = S->queue.front();
+                int64_t n_lo = 0, n_hi = 0;
+                for (auto it = S->queue.begin(); it != S->queue.end() && (int)batch.size() < S->batch_max_sets;) {
+                    const uint64_t t = *it;
                     Req &r = S->reqs[t];
                     if (r.state == Q_CANCELLED) {
-                        S->queue.pop_front();
+                        it = S->queue.erase(it);
+                        continue;
+                    }
+                    if (!batch.empty() && (r.N < n_lo || r.N > n_hi)) {
+                        ++it;
                         continue;
                     }
                     const size_t need = footprint(r.N);
@@ -102,7 +118,11 @@ void worker_main(ServeState *S) {
                     const double w = work_of(r.d, r.N);
                     if (!fits) break;
                     if (!batch.empty() && work + w > S->batch_work_cap) break;
-                    S->queue.pop_front();
+                    if (batch.empty()) {
+                        n_lo = r.N / 2;
+                        n_hi = r.N * 2;
+                    }
+                    it = S->queue.erase(it);
                     r.state = Q_RUNNING;
                     batch.push_back(t);
                     bytes += need;
@@ -116,6 +136,12 @@ void worker_main(ServeState *S) {
         }
         // run the batch
         const int n = (int)batch.size();
+        int64_t n_max = 0;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (uint64_t t : batch) n_max = std::max<int64_t>(n_max, S->reqs[t].N);
+        }
+        cudaStream_t st = n_max <= S->small_n ? st_hi : st_lo;
         std::vector<csg_set *> sets;
         std::vector<uint64_t> seeds(n), seqs(n);
         std::vector<csg_result> res(n);
@@ -165,7 +191,8 @@ void worker_main(ServeState *S) {
         S->cv_done.notify_all();
         S->cv_work.notify_all();
     }
-    cudaStreamDestroy(st);
+    cudaStreamDestroy(st_lo);
+    cudaStreamDestroy(st_hi);
 }
 
 ServeState *ensure_serve(csg_ctx *ctx) {
