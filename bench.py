@@ -27,6 +27,7 @@ import math
 
 import numpy as np
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -195,12 +196,16 @@ def recorded_traffic(kernel: str, workload: str):
             return None
         with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
             text = fh.read()
-        # the device code: everything before the file's host-side section
+        # the device code: everything before the file's host-side section, with comments and
+        # whitespace removed (a comment edit does not change the kernel)
         marker = rec.get("device_code_ends_at", "").encode()
         if marker and marker in text:
             text = text[:text.index(marker)]
-        sha = hashlib.sha256(text).hexdigest()[:16]
-        return rec["dram_bytes_per_launch"] if sha == rec["sha256_16"] else None
+        code = re.sub(r"/\*.*?\*/", "", text.decode(), flags=re.S)
+        code = re.sub(r"//[^\n]*", "", code)
+        code = re.sub(r"\s+", " ", code)
+        sha = hashlib.sha256(code.encode()).hexdigest()[:16]
+        return rec["dram_bytes_per_launch"] if sha == rec["code_sha256_16"] else None
     except (OSError, ValueError, KeyError):
         return None
 

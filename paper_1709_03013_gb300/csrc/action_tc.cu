@@ -13,29 +13,32 @@
 // above the largest interval (N - 2 <= 2^18).  The result is converted back to an
 // integer before it is used, so the counts are bit-exact in either format.
 //
-// Pass 1 (expand): one thread per packed word writes the operand bytes of U and of P it
-// covers (64 fp8 bytes or 32 fp4 bytes each); only the column ranges the product reads
-// are written.
+// Pass 1 (expand): one warp per operand row, one lane per packed word, writes the operand
+// bytes of U and of P the word covers (64 fp8 bytes or 32 fp4 bytes each); only the column
+// ranges the product reads are written.
 // Pass 2 (product): persistent CTA pairs (clusters of two CTAs, one per SM) take pair tiles
 // (256 rows i x 256 columns j, upper triangle only, K from the first row of the tile to its
 // last column) from a global work queue: the leader CTA claims each tile with an atomic
-// counter over a tile list ordered set by set, longest first, block-rasterised, and mails the
-// index to the other CTA; claiming in list order keeps the tiles running at once on the same
-// set's operands, which then stay in L2.  The pair runs 2-SM MMAs (cta_group::2): each CTA
+// counter over a tile list ordered set by set, longest first, block-rasterised (one step ahead
+// of the tile it is loading), and mails the tile itself (set, row and column tile, K range) to
+// the other CTA; claiming in list order keeps the tiles running at once on the same set's
+// operands, which then stay in L2.  The pair runs 2-SM MMAs (cta_group::2): each CTA
 // stages its own 128 rows of U and 128 of the tile's 256 rows of P, the leader issues the
 // MMAs, and each CTA's TMEM receives the accumulator of its own 128 rows, so each SM loads
 // 32 KB per stage instead of the 48 KB a one-SM 128 x 256 tile needs.
 // Warp roles per CTA:
 //   warp 0     the tile queue (leader) or its mailbox (other CTA), handed to warps 1-9
-//              through a 4-slot shared-memory ring; TMA producer: 128-byte-swizzled K
-//              stages of 128 rows of U and 128 rows of P (16 KB each) into a 6-stage ring
-//              whose transaction bytes are counted on the leader's barrier
+//              through a 4-slot shared-memory ring together with the tile's relation words
+//              for this CTA's 128 rows (staged by TMA into the slot); TMA producer:
+//              128-byte-swizzled K stages of 128 rows of U and 128 rows of P (16 KB each)
+//              into a 6-stage ring whose transaction bytes are counted on the leader's barrier
 //   warp 1     allocates 512 TMEM columns together with the other CTA; in the leader one
 //              lane issues the MMAs (M=256, N=256, 32 bytes of K each: 32 fp8 or 64 fp4
 //              elements) and commits each stage back to both producers and each finished
 //              tile to both epilogues
 //   warps 2-9  epilogue: tcgen05.ld of the CTA's 128 rows from TMEM (each thread owns one
-//              row and half of the columns), the S bits of the row select the related pairs,
+//              row and half of the columns), the S bits of the row (from the ring slot) select
+//              the related pairs,
 //              counters, the optional full histogram and the optional d'Alembertian sums
 //              (Eq. b_local) are updated.  The fp8 form keeps two accumulators (columns 0
 //              and 256) so the epilogue of one tile overlaps the product of the next; the
