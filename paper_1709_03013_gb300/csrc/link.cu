@@ -198,44 +198,25 @@ __device__ __forceinline__ bool exact_pair(const double (*rd)[kTile], const doub
     return exact_ds(rd[0][rt], rd[1][rt], cd[0][c], cd[1][c]);
 }
 
-// One 64-column word of tile row rt evaluated pair by pair: bit b set iff the row and
-// column 64 q + b are related; columns outside [c0, ncol) stay 0.  Used for the de Sitter
-// slab (d=2 and d=4 words go through the packed screen); for d=4 it would decide |e| > m
-// in float (the bound above) and the rest in double.  cf: the
-// tile's column screen values (d=2 negated); Fs: the set's screen values (row i's read).
-template <int D>
-__device__ __noinline__ uint64_t word_by_pair(int q, int c0, int ncol, const float (*cf)[kTile],
-                                              const double (*rd)[kTile], const double (*cd)[kTile], int rt,
-                                              const float *__restrict__ Fs, int64_t N, int64_t i, float m) {
-    float f[5];
-#pragma unroll
-    for (int a = 0; a < screen_floats(D); ++a) f[a] = Fs[a * N + i];
+// One 64-column word of tile row rt of the 1+1 de Sitter slab evaluated pair by pair: bit b
+// set iff the row and column 64 q + b are related; columns outside [c0, ncol) stay 0.  The
+// float screen (|d eta| minus the shorter arc, beyond the margin m) settles almost every pair
+// and the rest are decided in double.  cf: the tile's column screen values (eta, theta); Fs:
+// the set's screen values (row i's read).
+__device__ __noinline__ uint64_t word_by_pair_ds(int q, int c0, int ncol, const float (*cf)[kTile],
+                                                 const double (*rd)[kTile], const double (*cd)[kTile], int rt,
+                                                 const float *__restrict__ Fs, int64_t N, int64_t i, float m) {
+    const float eta = Fs[i], theta = Fs[N + i];
     uint64_t acc = 0;
     for (int b = 0; b < 64; ++b) {
         const int c = q * 64 + b;
         if (c < c0 || c >= ncol) continue;
-        bool rel;
-        if (D == 2) {
-            // cf holds -U_k, -V_k
-            const float e = fmaxf(__fadd_rn(f[0], cf[0][c]), __fadd_rn(f[1], cf[1][c]));
-            rel = e < 0.f || (e == 0.f && exact_pair<D>(rd, cd, rt, c));
-        } else if (D == 4) {
-            // cf holds T_k, X_k, Y_k, Z_k, -H_k; f holds T_i, X_i, Y_i, Z_i, -H_i; e = -s^2 / 2
-            float e = __fadd_rn(cf[4][c], f[4]);
-            e = __fmaf_rn(cf[0][c], f[0], e);
-            e = __fmaf_rn(cf[1][c], -f[1], e);
-            e = __fmaf_rn(cf[2][c], -f[2], e);
-            e = __fmaf_rn(cf[3][c], -f[3], e);
-            rel = e < -m || (e <= m && exact_pair<D>(rd, cd, rt, c));
-        } else {
-            // cylinder light cone: shorter arc below |d eta|
-            const float deta = fabsf(__fsub_rn(cf[0][c], f[0]));
-            const float dth = fabsf(__fsub_rn(cf[1][c], f[1]));
-            const float ang = __fsub_rn(3.14159265f, fabsf(__fsub_rn(3.14159265f, dth)));
-            const float diff = __fsub_rn(deta, ang);
-            rel = diff > m || (diff >= -m && exact_pair<D>(rd, cd, rt, c));
-        }
-        if (rel) acc |= 1ull << b;
+        // cylinder light cone: shorter arc below |d eta|
+        const float deta = fabsf(__fsub_rn(cf[0][c], eta));
+        const float dth = fabsf(__fsub_rn(cf[1][c], theta));
+        const float ang = __fsub_rn(3.14159265f, fabsf(__fsub_rn(3.14159265f, dth)));
+        const float diff = __fsub_rn(deta, ang);
+        if (diff > m || (diff >= -m && exact_pair<GEOM_DS2>(rd, cd, rt, c))) acc |= 1ull << b;
     }
     return acc;
 }
@@ -411,12 +392,14 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
     }
 
     uint64_t A[kRowsPer] = {0, 0, 0, 0}, B[kRowsPer] = {0, 0, 0, 0};
-    if (D != GEOM_DS2 && any) {
-        const float m2 = -(m + m);
-        if (D == 2 && diag)
-            word_packed<D, true>(q, cf, a, 0, A, B);
-        else
-            word_packed<D, false>(q, cf, a, pack2(m2, m2), A, B);
+    if constexpr (D != GEOM_DS2) {
+        if (any) {
+            const float m2 = -(m + m);
+            if (D == 2 && diag)
+                word_packed<D, true>(q, cf, a, 0, A, B);
+            else
+                word_packed<D, false>(q, cf, a, pack2(m2, m2), A, B);
+        }
     }
 #pragma unroll
     for (int s = 0; s < kRowsPer; ++s) {
@@ -428,7 +411,7 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
             const int lo = diag ? max(rt + 1 - 64 * q, 0) : 0;
             const int hi = min(ncol - 64 * q, 64);
             const uint64_t mask = lo >= hi ? 0ull : ((hi == 64 ? ~0ull : (1ull << hi) - 1) & ~((1ull << lo) - 1));
-            if (D != GEOM_DS2) {
+            if constexpr (D != GEOM_DS2) {
                 // pairs the screen left open: decide them in double
                 wd = A[s] & mask;
                 uint64_t amb = B[s] & ~A[s] & mask;
@@ -441,7 +424,7 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
                         wd &= ~(1ull << b);
                 }
             } else {
-                wd = word_by_pair<D>(q, lo + 64 * q, ncol, cf, rd, cd, rt, Fs, N, i, m);
+                wd = word_by_pair_ds(q, lo + 64 * q, ncol, cf, rd, cd, rt, Fs, N, i, m);
             }
         }
         ow[q][rt] = wd;
