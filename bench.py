@@ -44,6 +44,16 @@ WORKLOAD = dict(d=4, N=65536, seed=1)
 METHODS = {"popc": 0, "tc": 1, "tc8": 2, "tc4": 3}
 WORKLOAD_NAME = "d=4 flat causal diamond, N=65536, seed 1 (sprinkle+sort+link+action)"
 
+
+def arm_config(method: str, world: int) -> dict:
+    """The default line's config (both arms report the same one)."""
+    fp4 = method in ("tc", "tc4")
+    return {"workload": WORKLOAD_NAME, "d": WORKLOAD["d"], "N": WORKLOAD["N"], "seed": WORKLOAD["seed"],
+            "method": method,
+            "l2": ("inputs larger than L2 (512 MiB bitmap, "
+                   f"{'4 GiB fp4' if fp4 else '8 GiB fp8'} operands per step)"),
+            "parallelism": "replicas" if world > 1 else "single"}
+
 # Popcount peak of the integer pipe: 32 32-bit POPC per SM per clock (a loop of
 # independent popcounts sustains 28 per SM per clock on this GB300), 32 bit-ops each.
 POPC_PER_SM_CLK = 32
@@ -293,10 +303,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME + "; each step the oracle's triple loop over 32 rows",
-                       "d": d, "N": N, "seed": seed},
+            "config": arm_config(args.method, int(os.environ.get("WORLD_SIZE", "1"))),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "per step 32 consecutive first elements, blocks spread over the set"},
+                             "sample": "per step the oracle's triple loop over 32 consecutive rows of the "
+                                       "set (its link of the whole set built once), blocks spread over the set"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -782,10 +792,7 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": ("fp4" if fp4 else "fp8") if is_tc else "u64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "d": d, "N": N, "seed": seed, "method": args.method,
-                   "l2": ("inputs larger than L2 (512 MiB bitmap, "
-                          f"{'4 GiB fp4' if fp4 else '8 GiB fp8'} operands per step)"),
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": arm_config(args.method, world),
         "gpu_launches": launches_per_step(N, is_tc) * args.steps,
         "result": {"R": res.R, "Nk": list(res.Nk), "sum_m": res.sum_m, "W": res.W, "combo": res.combo,
                    "S": res.S},
