@@ -88,3 +88,25 @@ def test_bulk_result_conversion_matches_per_field():
     assert got == want
     assert all(isinstance(x, csg.Result) and isinstance(x.Nk, tuple) for x in got)
     assert csg._results(res, 0) == []
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """A C99 program that calls every declared entry point compiles with warnings as errors
+    and links against the library (it is not run: no GPU here)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    names = _declared()
+    body = "\n".join(f"    p[{k}] = (void (*)(void))&{n};" for k, n in enumerate(names))
+    src = tmp_path / "use_csg.c"
+    src.write_text(
+        "#include <stdio.h>\n#include \"csg.h\"\n"
+        f"int main(void) {{\n    void (*p[{len(names)}])(void);\n{body}\n"
+        "    csg_result r;\n    (void)r;\n    printf(\"%p\\n\", (void *)p[0]);\n    return 0;\n}\n")
+    libdir = os.path.dirname(lib._name)
+    out = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-Wno-pedantic",
+                          "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lcsg",
+                          "-o", str(tmp_path / "use_csg")], capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
