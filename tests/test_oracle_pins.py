@@ -4,7 +4,8 @@ Each test checks the oracle against something it does not compute the same way:
 a library generator (numpy's Philox), a library sort, exact rational arithmetic,
 a graph library's reachability sets, a 2D dominance count, closed forms for
 chains and antichains, hand-worked fixtures under tests/golden, exact identities,
-and the Myrheim-Meyer ordering fraction of a flat diamond.
+the Myrheim-Meyer ordering fraction of a flat diamond, and the exact expected
+interval abundances of a sprinkled diamond (from the volume of k-chains).
 """
 import itertools
 import math
@@ -306,6 +307,78 @@ def test_2d_three_chain_expectation():
         Ns.append(oracle.action(oracle.link(2, oracle.sprinkle_sorted(2, N, 100 + s)))["sum_m"])
     want = math.comb(N, 3) / 6
     assert abs(np.mean(Ns) / want - 1) < 0.05
+
+
+def _chain_volume(k, d):
+    """chi_k of a flat Alexandrov interval: the volume of ordered k-chains x1 < ... < xk inside
+    an interval of volume V is chi_k V^k, with (Meyer's closed form)
+    chi_k = (Gamma(d+1)/2)^(k-1) Gamma(d/2) Gamma(d) / (k Gamma(kd/2) Gamma((k+1)d/2)),
+    chi_0 = 1.  Exact rational for even d (every Gamma argument is an integer)."""
+    if k == 0:
+        return Fraction(1)
+    h, fac = d // 2, math.factorial
+    return (Fraction(fac(d), 2) ** (k - 1)
+            * Fraction(fac(h - 1) * fac(d - 1), k * fac(k * h - 1) * fac((k + 1) * h - 1)))
+
+
+def _expected_abundance(d, N, m):
+    """<N_m> for N iid uniform points in a flat d-dimensional diamond (N fixed).
+
+    An ordered pair x < y holds exactly m of the other N-2 points with probability
+    C(N-2, m) E[1(x<y) p^m (1-p)^(N-2-m)], p = V(x, y)/V the fraction of the diamond inside
+    their interval.  Splitting a (j+2)-chain at its ends gives E[1(x<y) p^j] = chi_{j+2}/chi_j,
+    so the binomial expansion of (1-p)^(N-2-m) makes <N_m> an exact finite sum."""
+    n = N - 2 - m
+    s = sum(Fraction(math.comb(n, i) * (-1) ** i) * _chain_volume(m + i + 2, d) / _chain_volume(m + i, d)
+            for i in range(n + 1))
+    return N * (N - 1) * math.comb(N - 2, m) * s
+
+
+def test_chain_volume_closed_form():
+    # chi_k: 1/(k!)^2 in 1+1 (two random orders agree), the ordering probability f(d)/2 for k = 2,
+    # and in 3+1 the recursion chi_{k+1} V^{k+1} = chi_k int_I V(x, top)^k dx over the diamond
+    # (every chain's later part lies in the interval from its first element to the top vertex),
+    # integrated numerically with V(x, top) = (pi/24) tau^4.
+    from scipy import integrate
+    for k in range(1, 7):
+        assert _chain_volume(k, 2) == Fraction(1, math.factorial(k) ** 2)
+    assert _chain_volume(2, 4) == Fraction(1, 20) and _chain_volume(3, 4) == Fraction(1, 2100)
+    V = math.pi / 24    # unit-height diamond: bottom (-1/2, 0), top (1/2, 0)
+
+    def tau_moment(a):
+        f = lambda r, t: 4 * math.pi * r * r * ((0.5 - t) ** 2 - r * r) ** (a / 2)
+        return integrate.dblquad(f, -0.5, 0.5, lambda t: 0.0, lambda t: 0.5 - abs(t),
+                                 epsabs=1e-15, epsrel=1e-11)[0]
+
+    assert abs(tau_moment(0) / V - 1) < 1e-10
+    for k in (1, 2, 3):
+        lhs = float(_chain_volume(k + 1, 4)) * V ** (k + 1)
+        rhs = float(_chain_volume(k, 4)) * (math.pi / 24) ** k * tau_moment(4 * k)
+        assert abs(lhs / rhs - 1) < 1e-9
+
+
+@pytest.mark.parametrize("d,N", [(2, 24), (2, 40), (4, 24), (4, 40)])
+def test_mean_abundances_and_action_exact(d, N):
+    # Means over 20000 sprinkled sets against the exact expectations of N_0..N_3, of the related
+    # pairs R = sum_m N_m, of the 3-chains sum_m m N_m, and of the action (linear in the N_k).
+    E = [_expected_abundance(d, N, m) for m in range(N - 1)]
+    assert sum(E) == Fraction(N * (N - 1), 2) * 2 * _chain_volume(2, d)
+    assert sum(m * e for m, e in enumerate(E)) == N * (N - 1) * (N - 2) * _chain_volume(3, d)
+    if d == 2:
+        ES = 2 * (N - 2 * E[0] + 4 * E[1] - 2 * E[2])
+        assert ES == 2    # the mean 1+1 action of a flat diamond is 2 at every N
+    else:
+        ES = (N - E[0] + 9 * E[1] - 16 * E[2] + 8 * E[3]) * 4 / SQ6
+    want = np.array([float(x) for x in E[:4]] + [float(sum(E)),
+                    float(sum(m * e for m, e in enumerate(E))), float(ES)])
+    T = 20000
+    X = np.empty((T, 7))
+    for s in range(T):
+        r = oracle.run(d, N, seed=s, seq=7, threads=1)
+        X[s, :4] = r["Nk"]
+        X[s, 4:] = r["R"], r["sum_m"], r["S"]
+    z = (X.mean(0) - want) / (X.std(0, ddof=1) / math.sqrt(T))
+    assert np.all(np.abs(z) < 5), z
 
 
 def test_rows_partition():
