@@ -627,9 +627,9 @@ def main():
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the batch and serve summaries of the default line")
     ap.add_argument("--profile-batch", action="store_true",
-                    help="profiling driver: the 4096-set batch graph, then --reps replays")
+                    help="profiling mode: the 4096-set batch graph, then --reps replays")
     ap.add_argument("--profile-action", action="store_true",
-                    help="profiling driver: one sprinkled set, then --reps action launches")
+                    help="profiling mode: one sprinkled set, then --reps action launches")
     ap.add_argument("--d", type=int, default=4)
     ap.add_argument("--n", type=int, default=40000)
     ap.add_argument("--reps", type=int, default=2)
