@@ -206,7 +206,10 @@ int csg_run_batch(csg_ctx *ctx, int n, const int32_t *d, const int64_t *N, const
  * while their bitmaps (N*N/8 bytes each) fit the context's budget, runs sprinkle,
  * link and action for every admitted request in shared launches, and retires them.
  * poll waits up to timeout_ms (0 = no wait, <0 = forever) and returns CSG_OK with
- * *out filled, CSG_PENDING, or an error; a collected ticket is forgotten. */
+ * *out filled, CSG_PENDING, or an error; a collected ticket is forgotten.  cancel
+ * drops a request that is still queued (CSG_E_BUSY once it is admitted; its poll
+ * then returns CSG_E_CANCELLED).  Both return CSG_E_NOTFOUND for a ticket the
+ * context never issued or already forgot; neither starts the service. */
 int csg_serve_submit(csg_ctx *ctx, int d, int64_t N, uint64_t seed, uint64_t seq,
                      uint64_t *ticket);
 int csg_serve_poll(csg_ctx *ctx, uint64_t ticket, csg_result *out, int timeout_ms);

@@ -78,11 +78,17 @@ void worker_main(ServeState *S) {
     cudaSetDevice(ctx->device);
     // two streams: batches of small sets go on the high-priority one, so their kernels'
     // blocks are scheduled first whenever a large batch's short kernels leave SMs free
+    // (if only one stream can be made, both classes share it; with none, every batch this
+    // worker takes fails with CSG_E_CUDA, so its requests still complete)
     int prio_lo = 0, prio_hi = 0;
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     cudaStream_t st_lo = nullptr, st_hi = nullptr;
-    cudaStreamCreateWithPriority(&st_lo, cudaStreamNonBlocking, prio_lo);
-    cudaStreamCreateWithPriority(&st_hi, cudaStreamNonBlocking, prio_hi);
+    const bool own_lo = cudaStreamCreateWithPriority(&st_lo, cudaStreamNonBlocking, prio_lo) == cudaSuccess;
+    const bool own_hi = cudaStreamCreateWithPriority(&st_hi, cudaStreamNonBlocking, prio_hi) == cudaSuccess;
+    if (!own_lo) st_lo = own_hi ? st_hi : nullptr;
+    if (!own_hi) st_hi = own_lo ? st_lo : nullptr;
+    const int stream_rc = own_lo || own_hi ? CSG_OK : CSG_E_CUDA;
+    cudaGetLastError();  // a failed creation leaves no sticky error behind
     std::vector<uint64_t> batch;
     for (;;) {
         batch.clear();
@@ -145,7 +151,7 @@ void worker_main(ServeState *S) {
         std::vector<csg_set *> sets;
         std::vector<uint64_t> seeds(n), seqs(n);
         std::vector<csg_result> res(n);
-        int rc = CSG_OK;
+        int rc = stream_rc;
         {
             std::lock_guard<std::mutex> lk(S->mu);
             for (int q = 0; q < n; ++q) {
@@ -191,8 +197,14 @@ void worker_main(ServeState *S) {
         S->cv_done.notify_all();
         S->cv_work.notify_all();
     }
-    cudaStreamDestroy(st_lo);
-    cudaStreamDestroy(st_hi);
+    if (own_lo) cudaStreamDestroy(st_lo);
+    if (own_hi) cudaStreamDestroy(st_hi);
+}
+
+// the running service, or null before the first request (polls and cancels do not start it)
+ServeState *find_serve(csg_ctx *ctx) {
+    std::lock_guard<std::mutex> g(ctx->serve_mu);
+    return ctx->serve;
 }
 
 ServeState *ensure_serve(csg_ctx *ctx) {
@@ -266,7 +278,8 @@ int csg_serve_submit(csg_ctx *ctx, int d, int64_t N, uint64_t seed, uint64_t seq
 
 int csg_serve_poll(csg_ctx *ctx, uint64_t ticket, csg_result *out, int timeout_ms) {
     if (!ctx || !out) return CSG_E_INVAL;
-    ServeState *S = ensure_serve(ctx);
+    ServeState *S = find_serve(ctx);
+    if (!S) return CSG_E_NOTFOUND;
     std::unique_lock<std::mutex> lk(S->mu);
     auto it = S->reqs.find(ticket);
     if (it == S->reqs.end()) return CSG_E_NOTFOUND;
@@ -295,7 +308,8 @@ int csg_serve_poll(csg_ctx *ctx, uint64_t ticket, csg_result *out, int timeout_m
 
 int csg_serve_cancel(csg_ctx *ctx, uint64_t ticket) {
     if (!ctx) return CSG_E_INVAL;
-    ServeState *S = ensure_serve(ctx);
+    ServeState *S = find_serve(ctx);
+    if (!S) return CSG_E_NOTFOUND;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         auto it = S->reqs.find(ticket);

@@ -249,6 +249,23 @@ def test_cancel_and_unknown_ticket(ctx, csg):
         assert ctx.serve_poll(b, 120000) is not None
 
 
+def test_serve_calls_on_a_fresh_context(csg):
+    # polls and cancels before any submission find no ticket (and start no service);
+    # the first submission then starts it
+    with csg.Context(0) as c:
+        with pytest.raises(csg.CsgError) as e:
+            c.serve_poll(1, 0)
+        assert e.value.code == csg.E_NOTFOUND
+        assert c.serve_cancel(1) == csg.E_NOTFOUND
+        t = c.serve_submit(2, 300, 7, 0)
+        r = c.serve_poll(t, 60000)
+        want = oracle.run(2, 300, 7, 0)
+        _check_result(r, want, 2, 300)
+        with pytest.raises(csg.CsgError) as e:
+            c.serve_poll(t, 0)
+        assert e.value.code == csg.E_NOTFOUND
+
+
 def test_batch_autotune_records_choice(csg, tmp_path, monkeypatch):
     # the first batch of a shape times candidate tunings and records the winner; every
     # candidate gives the same counts, so the results stay exact whichever wins
