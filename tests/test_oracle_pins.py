@@ -433,6 +433,51 @@ def test_smeared_tends_to_local_action():
         assert abs(S - S2) <= 1e-5 * max(abs(S2), N)
 
 
+@pytest.mark.parametrize("d,N,seed", [(2, 11, 21), (4, 12, 22), (2, 12, 23)])
+def test_smeared_is_mean_local_action_of_thinnings(d, N, seed):
+    # Keeping each element independently with probability e, a pair with m elements between
+    # them survives as a pair with k between with probability e^2 P(Binomial(m, e) = k), so the
+    # mean local 1+1 action (Eq. s_local) of the kept subset is the smeared action S_e.  Brute
+    # force over all 2^N subsets of a small sprinkled set, each subset counted by the pinned
+    # interval counter and action.
+    rel = oracle.link(d, oracle.sprinkle_sorted(d, N, seed))
+    hist = oracle.action(rel)["hist"]
+    S_sub = {}
+    for mask in range(1 << N):
+        keep = [e for e in range(N) if mask >> e & 1]
+        if keep:
+            sub = rel[np.ix_(keep, keep)]
+            S_sub[mask] = (len(keep), oracle.finalize(2, len(keep), oracle.action(sub)["Nk"])[1])
+        else:
+            S_sub[mask] = (0, 0.0)
+    for eps in (0.5, 0.25, 0.1, 0.9):
+        want = math.fsum(eps ** n * (1 - eps) ** (N - n) * S for n, S in S_sub.values())
+        got = oracle.smeared(N, hist, eps)
+        assert abs(got - want) <= 1e-12 * max(1.0, math.fsum(
+            eps ** n * (1 - eps) ** (N - n) * abs(S) for n, S in S_sub.values())), (eps, got, want)
+
+
+@pytest.mark.parametrize("N", [24, 40])
+def test_mean_smeared_action_2d_exact(N):
+    # With the thinning reading above, a thinned uniform sprinkle of N elements is a uniform
+    # sprinkle of Binomial(N, e) elements, whose mean 1+1 action is 2 at every size >= 1 (and
+    # 0 for the empty set): E[S_e] = 2 (1 - (1 - e)^N).  Checked exactly against the expected
+    # abundances, then against the oracle's mean over 20000 sets.
+    E = [_expected_abundance(2, N, m) for m in range(N - 1)]
+    for e in (Fraction(1, 2), Fraction(1, 4), Fraction(1, 10)):
+        w = [sum(c * math.comb(m, k) * e ** k * (1 - e) ** (m - k) for k, c in ((0, 1), (1, -2), (2, 1)) if k <= m)
+             for m in range(N - 1)]
+        assert 2 * e * (N - 2 * e * sum(a * b for a, b in zip(E, w))) == 2 * (1 - (1 - e) ** N)
+    T = 20000
+    X = np.empty((T, 3))
+    for s in range(T):
+        h = oracle.run(2, N, seed=s, seq=9, threads=1)["hist"]
+        X[s] = [oracle.smeared(N, h, eps) for eps in (0.5, 0.25, 0.1)]
+    want = np.array([2 * (1 - (1 - eps) ** N) for eps in (0.5, 0.25, 0.1)])
+    z = (X.mean(0) - want) / (X.std(0, ddof=1) / math.sqrt(T))
+    assert np.all(np.abs(z) < 5), z
+
+
 @pytest.mark.parametrize("N", [1, 50])
 def test_smeared_antichain(N):
     assert oracle.smeared(N, np.zeros(N, np.uint64), 0.2) == 2 * 0.2 * N
