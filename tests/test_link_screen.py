@@ -1,0 +1,108 @@
+"""The link kernel's float screens, checked on the CPU against their error analysis.
+
+The d=4 link settles each pair by the sign of the expanded interval
+    e = t_k t_i - x_k x_i - y_k y_i - z_k z_i - h_k - h_i = -s^2 / 2,   h = (t^2 - |x|^2) / 2,
+evaluated in float (one add, then four fused multiply-adds) with the margin m = 4e-6 S^2
+folded into the row value: a set sign bit of e' = fl(e + m) means certainly related, a clear
+sign bit of fl(e' - 2m) certainly unrelated, and the pairs in between are decided in double.
+The argument rests on |e' - (e + m)| <= 37.5 u S^2 (u = 2^-24, S = max(1, max |coordinate|)).
+
+These tests replay that arithmetic operation by operation in numpy float32 (a fused
+multiply-add as the exact double product plus the addend, rounded to float) and check, on
+sprinkles, boxes and light-cone stress sets at scales 1 to 1e15, that no certain bit
+contradicts the double predicate (the oracle's link), that the error stays inside the bound,
+and that the pairs left to double are few.  The d=2 screen (float light-cone coordinates,
+ties to double) is checked the same way.  No GPU is involved: the kernel itself is compared
+with the oracle bit for bit by the GPU tests.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_03013_gb300 import inputs
+
+f32 = np.float32
+U = 2.0 ** -24
+
+
+def _fma(a, b, c):
+    # float32 fused multiply-add: the product of two floats is exact in double
+    return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(f32)
+
+
+def _screen_d4(c, S):
+    """Certain-related bits A, not-certainly-unrelated bits B (upper triangle, k > i) and the
+    largest |e' - (e + m)| / (u S^2) over the pairs."""
+    t, x, y, z = c
+    T, X, Y, Z = (v.astype(f32) for v in (t, x, y, z))
+    Hn = (-(0.5 * (t * t - ((x * x + y * y) + z * z)))).astype(f32)   # -h, formed in double
+    m = f32(4e-6) * f32(S * S)
+    aH = (Hn + m).astype(f32)                                          # row value fl(-h_i + m)
+    m2 = -(m + m)
+    N = t.shape[0]
+    A = np.zeros((N, N), bool)
+    B = np.zeros((N, N), bool)
+    worst = 0.0
+    for i in range(N - 1):
+        k = np.arange(i + 1, N)
+        e = (Hn[k] + aH[i]).astype(f32)
+        e = _fma(T[k], np.full(k.size, T[i]), e)
+        e = _fma(X[k], np.full(k.size, -X[i]), e)
+        e = _fma(Y[k], np.full(k.size, -Y[i]), e)
+        e = _fma(Z[k], np.full(k.size, -Z[i]), e)
+        A[i, k] = np.signbit(e)
+        B[i, k] = np.signbit((e + m2).astype(f32))
+        dt = t[k] - t[i]
+        s2 = dt * dt - ((x[k] - x[i]) ** 2 + (y[k] - y[i]) ** 2 + (z[k] - z[i]) ** 2)
+        worst = max(worst, float(np.max(np.abs(e.astype(np.float64) - (-0.5 * s2 + float(m))))))
+    return A, B, worst / (S * S * U)
+
+
+def _box(N, seed, scale):
+    # coordinates anywhere in [-scale, scale]^4 (the bound assumes only |coordinate| <= S)
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-scale, scale, size=(4, N))
+    return oracle.sort(4, c)[0]
+
+
+def _cases():
+    out = []
+    for sc in (1.0, 1e3, 1e15):
+        out.append((f"sprinkle x{sc:g}", lambda sc=sc: oracle.sprinkle_sorted(4, 1200, 3) * sc))
+        out.append((f"light cones x{sc:g}", lambda sc=sc: oracle.sort(4, inputs.light_cone_coords(4, 1200, 5, scale=sc))[0]))
+        out.append((f"box x{sc:g}", lambda sc=sc: _box(1200, 7, sc)))
+    return out
+
+
+@pytest.mark.parametrize("name,make", _cases(), ids=[n for n, _ in _cases()])
+def test_d4_screen_never_contradicts_double_predicate(name, make):
+    c = np.ascontiguousarray(make())
+    S = max(1.0, float(np.abs(c).max()))
+    rel = oracle.link(4, c).astype(bool)
+    A, B, worst = _screen_d4(c, S)
+    iu = np.triu_indices(c.shape[1], 1)
+    a, b, r = A[iu], B[iu], rel[iu]
+    assert not (a & ~r).any()          # certainly related => related in double
+    assert not (~b & r).any()          # certainly unrelated => unrelated in double
+    assert not (a & ~b).any()          # the two sign words are nested
+    assert worst <= 37.5, worst        # the error bound the margin is built on
+    assert (b & ~a).sum() <= max(8, 0.01 * r.size)   # few pairs go to double
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e3, 1e15])
+def test_d2_screen_order_and_ties(scale):
+    # d=2: related iff u_i < u_k and v_i < v_k in double.  In float, e = max(U_i - U_k,
+    # V_i - V_k) < 0 must mean related and e > 0 unrelated; e == 0 goes to double.
+    N = 1500
+    c = oracle.sort(2, inputs.light_cone_coords(2, N, 4, scale=scale))[0]
+    rel = oracle.link(2, c).astype(bool)
+    Uf, Vf = c[2].astype(f32), c[3].astype(f32)
+    Uf = np.where(Uf == 0, f32(0), Uf)   # -0 folded onto +0
+    Vf = np.where(Vf == 0, f32(0), Vf)
+    i, k = np.triu_indices(N, 1)
+    e = np.maximum((Uf[i] - Uf[k]).astype(f32), (Vf[i] - Vf[k]).astype(f32))
+    r = rel[i, k]
+    assert not ((e < 0) & ~r).any()
+    assert not ((e > 0) & r).any()
+    assert not np.signbit(e[e == 0]).any()   # ties are +0, not -0
+    assert (e == 0).any()                    # the stress set does hold float ties
