@@ -12,7 +12,8 @@ multiply-add as the exact double product plus the addend, rounded to float) and 
 sprinkles, boxes and light-cone stress sets at scales 1 to 1e15, that no certain bit
 contradicts the double predicate (the oracle's link), that the error stays inside the bound,
 and that the pairs left to double are few.  The d=2 screen (float light-cone coordinates,
-ties to double) is checked the same way.  No GPU is involved: the kernel itself is compared
+ties to double) and the de Sitter slab's screen (arc against |d eta|, margin 1e-5) are
+checked the same way.  No GPU is involved: the kernel itself is compared
 with the oracle bit for bit by the GPU tests.
 """
 import numpy as np
@@ -106,3 +107,24 @@ def test_d2_screen_order_and_ties(scale):
     assert not ((e > 0) & r).any()
     assert not np.signbit(e[e == 0]).any()   # ties are +0, not -0
     assert (e == 0).any()                    # the stress set does hold float ties
+
+
+@pytest.mark.parametrize("eta0,seed", [(0.5, 1), (1.2, 2), (1.5, 3)])
+def test_desitter_screen_margin(eta0, seed):
+    # 1+1 de Sitter slab: related iff the shorter arc pi - |pi - |d theta|| is below |d eta|
+    # (in double).  The float form diff = |d eta| - arc (pi rounded to float) is within
+    # 2.6e-6 of the real value, so diff > 1e-5 must mean related and diff < -1e-5 unrelated.
+    N = 1500
+    c = oracle.sprinkle_desitter(N, eta0, seed)
+    rel = oracle.link(oracle.DS2, c).astype(bool)
+    eta, th = c[0].astype(f32), c[1].astype(f32)
+    pi_f, m = f32(3.14159265), f32(1e-5)
+    i, k = np.triu_indices(N, 1)
+    deta = np.abs((eta[k] - eta[i]).astype(f32))
+    dth = np.abs((th[k] - th[i]).astype(f32))
+    ang = (pi_f - np.abs((pi_f - dth).astype(f32))).astype(f32)
+    diff = (deta - ang).astype(f32)
+    r = rel[i, k]
+    assert not ((diff > m) & ~r).any()
+    assert not ((diff < -m) & r).any()
+    assert (np.abs(diff) <= m).sum() <= 0.01 * r.size
