@@ -40,3 +40,20 @@ def test_light_cone_stress_d2_contains_float_ties_and_signed_zeros():
     assert same_float.sum() >= 10 and same_double.sum() >= 10
     assert np.any((u == 0) & np.signbit(u)) and np.any((u == 0) & ~np.signbit(u))
     assert np.allclose(c[0], (u + v) / 2) and np.allclose(c[1], (v - u) / 2)
+
+
+def test_workload_distributions():
+    # the batch and serve recipes draw what they state: N log-uniform on [lo, hi], d 50/50
+    # (alternating in a batch, Bernoulli(1/2) in the stream), exponential gaps at the rate
+    from scipy import stats
+    b = inputs.batch_workload()
+    lnN = np.log([s.N for s in b])
+    assert stats.kstest(lnN, "uniform", args=(np.log(256), np.log(8192) - np.log(256))).pvalue > 1e-4
+    reqs = inputs.serve_workload(n_req=20000, rate_per_s=90.0)
+    lnN = np.log([r.spec.N for r in reqs])
+    assert stats.kstest(lnN, "uniform", args=(np.log(1024), np.log(65536) - np.log(1024))).pvalue > 1e-4
+    d4 = np.mean([r.spec.d == 4 for r in reqs])
+    assert abs(d4 - 0.5) < 5 * np.sqrt(0.25 / len(reqs))
+    gaps = np.diff([r.arrival_s for r in reqs])
+    assert stats.kstest(gaps, "expon", args=(0, 1 / 90.0)).pvalue > 1e-4
+    assert len({(r.spec.seed, r.spec.seq) for r in reqs}) == len(reqs)   # every request its own stream
