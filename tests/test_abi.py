@@ -110,3 +110,22 @@ def test_header_is_plain_c_and_links(lib, tmp_path):
                           "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lcsg",
                           "-o", str(tmp_path / "use_csg")], capture_output=True, text=True)
     assert out.returncode == 0, out.stderr
+
+
+def test_no_fallback_without_library_or_device(lib, tmp_path):
+    """The binding has no CPU path: a missing library is an ImportError that says how to build
+    it, and without a usable GPU the context cannot be made (the failure is an error code, not
+    a silent substitute)."""
+    from paper_1709_03013_gb300 import csg
+    saved, csg._lib = csg._lib, None   # as if nothing had been loaded yet
+    try:
+        with pytest.raises(ImportError, match="no CPU fallback"):
+            csg.load(str(tmp_path / "libcsg.so"))
+    finally:
+        csg._lib = saved
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(csg.CsgError) as e:
+        csg.Context(0)
+    assert e.value.code in (csg.E_CUDA, csg.E_INVAL)
