@@ -497,6 +497,23 @@ def test_desitter_sampler_distribution():
     assert stats.kstest(theta, "uniform", args=(0, 2 * math.pi)).pvalue > 1e-4
 
 
+@pytest.mark.parametrize("eta0", [0.5, 1.2])
+def test_desitter_ordering_fraction(eta0):
+    # For two iid elements of the slab the shorter arc between their angles is uniform on
+    # [0, pi], so they are related with probability P = E|eta_1 - eta_2| / pi (|d eta| < pi),
+    # eta with density sec^2(eta) / (2 tan eta0).  The related fraction of a set is a
+    # U-statistic: variance 4 var(g)/N + 2 P(1-P)/N^2 with g(a) = E|a - eta| / pi.
+    from scipy import integrate
+    f = lambda a: 1.0 / (math.cos(a) ** 2 * 2.0 * math.tan(eta0))
+    g = lambda a: integrate.quad(lambda b: abs(a - b) * f(b), -eta0, eta0, points=[a])[0] / math.pi
+    P = integrate.quad(lambda a: g(a) * f(a), -eta0, eta0)[0]
+    var_g = integrate.quad(lambda a: g(a) ** 2 * f(a), -eta0, eta0)[0] - P * P
+    N, sets = 3000, 6
+    frac = [oracle.link(oracle.DS2, oracle.sprinkle_desitter(N, eta0, s)).sum() / (N * (N - 1)) for s in range(sets)]
+    sd = math.sqrt((4 * var_g / N + 2 * P * (1 - P) / N ** 2) / sets)
+    assert abs(np.mean(frac) - P) < 5 * sd
+
+
 def test_desitter_relation_is_cylinder_light_cone():
     # timelike iff the shorter arc between the angles is below |d eta| (Eq. ds_metric),
     # decided here in exact rationals with the min(|dth|, 2 pi - |dth|) form of the arc
