@@ -37,10 +37,9 @@
 //              elements) and commits each stage back to both producers and each finished
 //              tile to both epilogues
 //   warps 2-9  epilogue: tcgen05.ld of the CTA's 128 rows from TMEM (each thread owns one
-//              row and half of the columns), the S bits of the row (from the ring slot) select
-//              the related pairs,
-//              counters, the optional full histogram and the optional d'Alembertian sums
-//              (Eq. b_local) are updated.  The fp8 form keeps two accumulators (columns 0
+//              row and half of the columns); the S bits of the row (from the ring slot) select
+//              the related pairs, whose counts update the counters, the optional full
+//              histogram and the optional d'Alembertian sums (Eq. b_local).  The fp8 form keeps two accumulators (columns 0
 //              and 256) so the epilogue of one tile overlaps the product of the next; the
 //              fp4 form keeps one accumulator at column 0 and its scale factors in columns
 //              256..511, and releases the accumulator as soon as the last columns are in
