@@ -66,7 +66,7 @@ struct ServeState {
     size_t reserved = 0;               // bytes admitted by running batches
     std::vector<std::thread> workers;
     size_t max_queue = 1 << 20;
-    double batch_work_cap = 1e14;      // flops per batch (about 30 ms on the tensor form)
+    double batch_work_cap = 1e14;      // flops per batch (12 ms at the tensor form's large-set rate)
     int batch_max_sets = 4096;
     int64_t small_n = 16384;           // batches of sets up to this size run at high priority
 };
