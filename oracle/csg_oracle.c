@@ -324,7 +324,8 @@ int orc_action_rows(int64_t N, const uint8_t *rel, int64_t row_lo, int64_t row_h
             for (int64_t j = i + 1; j < N; ++j) {
                 if (!ri[j]) continue;
                 const uint8_t *rj = rel + j * N;
-                int64_t m = 0;
+                /* m <= N - 2 < 2^31 (the largest interval, Sec. 4.1): a 32-bit count is exact */
+                uint32_t m = 0;
                 for (int64_t k = i + 1; k < j; ++k) m += ri[k] & rj[k];
                 h[m] += 1;
                 tR += 1;
