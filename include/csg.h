@@ -237,7 +237,7 @@ void csg_set_free(csg_set *set);
  * stage not run since timing was switched on). */
 #define CSG_STAGE_SPRINKLE 0 /* sprinkle + time order */
 #define CSG_STAGE_LINK 1     /* causal matrix */
-#define CSG_STAGE_EXPAND 2   /* fp8 operand expansion of the tensor form */
+#define CSG_STAGE_EXPAND 2   /* 0/1 operand expansion of the tensor form (fp4, or fp8) */
 #define CSG_STAGE_ACTION 3   /* the interval-count kernel itself */
 #define CSG_STAGE_FINALIZE 4 /* counters -> action */
 #define CSG_STAGE_COUNT 5
@@ -264,9 +264,28 @@ int csg_stage_times(csg_ctx *ctx, double *ms, int n);
  * and caches it, so make that first call before any stream capture.  All calls on a
  * device share the array and each call clears the parts that must start at zero;
  * calls whose kernels overlap on the GPU (different streams, no ordering between
- * them) race on it and must not be issued. */
+ * them) race on it and must not be issued.  If a bounded wait of the call's kernel runs
+ * out, *dev_out gets status CSG_E_TIMEOUT with every count (and combo and S) zero. */
 int csg_action_noalloc(int d, int64_t N, const uint64_t *dev_rows, int64_t stride_words,
                        csg_result *dev_out, void *stream);
+
+/* Failure injection for tests of the error paths (not for production use; process-wide,
+ * off by default).  No GPU faults, traps or hangs in either: the failures are made on the
+ * host or by a wait that nothing completes, and every device wait is bounded.
+ *
+ * csg_test_wait_expiry(limit_ns, starve): every bounded wait of the interval-count kernels
+ * (csg_action and its variants with CSG_POPC or a tensor method) gives up after limit_ns
+ * nanoseconds (0 restores the built-in limits of 2-4 s).  With starve nonzero (limit_ns must
+ * then be nonzero), the producer of every CTA skips the bulk copies of its first stage: the
+ * stage's barrier never completes, the first wait on it runs out with no copy in flight, the
+ * kernel records the expiry in the set's error word and returns, and the call returns
+ * CSG_E_TIMEOUT.  The context stays usable; csg_test_wait_expiry(0, 0) switches it off.
+ *
+ * csg_test_fail_alloc(n): the next n device allocations the library makes (set memory,
+ * stream-ordered scratch, batch arenas) fail as if the allocator were out of memory, so the
+ * calls that needed them return CSG_E_NOMEM.  n = 0 clears the count. */
+int csg_test_wait_expiry(uint64_t limit_ns, int starve);
+int csg_test_fail_alloc(int n);
 
 #ifdef __cplusplus
 }

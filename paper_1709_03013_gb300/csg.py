@@ -85,7 +85,7 @@ EXPORTS = [
     "csg_action_hist", "csg_action_batch", "csg_run_batch", "csg_serve_submit", "csg_serve_poll",
     "csg_serve_cancel", "csg_export_coords", "csg_export_bitmap", "csg_set_info", "csg_set_free",
     "csg_action_noalloc", "csg_set_timing", "csg_stage_times", "csg_action_smeared",
-    "csg_sprinkle_desitter", "csg_dalembertian",
+    "csg_sprinkle_desitter", "csg_dalembertian", "csg_test_wait_expiry", "csg_test_fail_alloc",
 ]
 
 _lib = None
@@ -130,6 +130,8 @@ def load(path: str = LIB_PATH):
         "csg_action_smeared": (i32, [vp, vp, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_double), R, vp]),
         "csg_dalembertian": (i32, [vp, vp, i32, vp, ctypes.c_double, vp, R, vp]),
         "csg_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_double), i32]),
+        "csg_test_wait_expiry": (i32, [u64, i32]),
+        "csg_test_fail_alloc": (i32, [i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -177,6 +179,18 @@ def action_noalloc(d: int, N: int, dev_rows_ptr: int, stride_words: int, dev_out
     after synchronising the stream, e.g. with result_from_bytes()."""
     _check(load().csg_action_noalloc(d, N, ctypes.c_void_p(dev_rows_ptr), stride_words,
                                      ctypes.c_void_p(dev_out_ptr), _stream(stream)), "csg_action_noalloc")
+
+
+def inject_wait_expiry(limit_ns: int, starve: bool) -> None:
+    """Failure injection (tests only): every bounded device wait of the interval-count kernels
+    gives up after limit_ns (0: built-in limits); with starve, each CTA's first stage gets no
+    copies, so its wait runs out and the call returns E_TIMEOUT.  See include/csg.h."""
+    _check(load().csg_test_wait_expiry(limit_ns, int(bool(starve))), "csg_test_wait_expiry")
+
+
+def inject_alloc_failures(n: int) -> None:
+    """Failure injection (tests only): the next n device allocations of the library fail."""
+    _check(load().csg_test_fail_alloc(n), "csg_test_fail_alloc")
 
 
 def result_from_bytes(buf: bytes) -> Result:

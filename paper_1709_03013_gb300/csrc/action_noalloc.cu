@@ -194,8 +194,12 @@ __global__ void noalloc_finalize_kernel(int d, int64_t N, int n_items,
     if (threadIdx.x == 0) {
         csg_result r;
         r.d = d;
-        r.status = scratch[1] ? CSG_E_TIMEOUT : CSG_OK;
+        const bool failed = scratch[1] != 0;
+        r.status = failed ? CSG_E_TIMEOUT : CSG_OK;
         r.N = N;
+        // after a timed-out wait some slots hold an earlier call's counts: report zeros
+        if (failed)
+            for (int k = 0; k < 7; ++k) tot[k] = 0;
         for (int k = 0; k < 4; ++k) r.Nk[k] = tot[k];
         r.R = tot[4];
         r.sum_m = tot[5];

@@ -140,7 +140,8 @@ template <int G, bool PHI>
 __global__ void __launch_bounds__(kThreads, 1)
 action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict__ items,
                    int n_items, int pitch, unsigned int *__restrict__ queue,
-                   unsigned long long *__restrict__ hist, long long nbins) {
+                   unsigned long long *__restrict__ hist, long long nbins, unsigned long long wait_ns,
+                   int starve) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem *ctl = reinterpret_cast<Smem *>(smem_raw);
     uint64_t *A = reinterpret_cast<uint64_t *>(smem_raw + 128);  // G rows x pitch words, then a zero row
@@ -154,6 +155,7 @@ action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict_
     __syncthreads();
 
     uint32_t phase = 0;
+    bool first = true;  // this CTA's first item (the one a failure-handling test starves)
     for (;;) {
         if (threadIdx.x == 0) ctl->item = (int)atomicAdd(queue, 1u);
         __syncthreads();
@@ -179,27 +181,31 @@ action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict_
             continue;
         }
 
-        // ---- stage the group's rows with bulk copies
+        // ---- stage the group's rows with bulk copies (a failure-handling test starves the
+        // first item: its barrier then gets no arrival and nothing is in flight)
         if (threadIdx.x == 0) {
             if (PHI) {
                 ctl->phi = S.phi;
                 ctl->acc = S.acc;
             }
-            ptx::fence_proxy_async_smem();
-            const uint32_t bytes = (uint32_t)nwa * 8u;
-            ptx::mbar_arrive_expect_tx(&ctl->bar, bytes * (uint32_t)__popc(gmask));
-            for (int r = 0; r < G; ++r)
-                if (gmask >> r & 1u)
-                    ptx::bulk_g2s(A + (size_t)r * pitch, rows + (i0 + r) * stride + w0a, bytes,
-                                  &ctl->bar);
+            if (!(starve && first)) {
+                ptx::fence_proxy_async_smem();
+                const uint32_t bytes = (uint32_t)nwa * 8u;
+                ptx::mbar_arrive_expect_tx(&ctl->bar, bytes * (uint32_t)__popc(gmask));
+                for (int r = 0; r < G; ++r)
+                    if (gmask >> r & 1u)
+                        ptx::bulk_g2s(A + (size_t)r * pitch, rows + (i0 + r) * stride + w0a, bytes,
+                                      &ctl->bar);
+            }
         }
-        const bool landed = ptx::mbar_wait_bounded(&ctl->bar, phase, kWaitLimitNs);
+        first = false;
+        const bool landed = ptx::mbar_wait_bounded(&ctl->bar, phase, wait_ns);
         if (__syncthreads_or(!landed)) {
             // a copy did not land in time: record it, keep the CTA alive until the
             // copy lands (bounded again), then stop
             if (threadIdx.x == 0) {
                 atomicExch(&S.counters[CNT_ERR], 1ull);
-                ptx::mbar_wait_bounded(&ctl->bar, phase, kWaitLimitNs);
+                ptx::mbar_wait_bounded(&ctl->bar, phase, wait_ns);
             }
             __syncthreads();
             break;
@@ -286,7 +292,8 @@ int launch_g(const PopcPlan &p, const Arena &a, cudaStream_t st) {
     CSG_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned int), st));
     stage_begin(CSG_STAGE_ACTION, st);
     kern<<<grid, kThreads, smem, st>>>(a.tab<SetDesc>(p.t_sets), a.tab<WorkItem>(p.t_items), p.n_items,
-                                       p.pitch, queue, p.hist, (long long)p.nbins);
+                                       p.pitch, queue, p.hist, (long long)p.nbins, wait_limit_ns(kWaitLimitNs),
+                                       starve_first_stage());
     stage_end(CSG_STAGE_ACTION, st);
     CSG_CUDA_TRY(cudaGetLastError());
     return CSG_OK;

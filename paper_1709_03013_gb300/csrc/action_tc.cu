@@ -91,6 +91,8 @@ struct TcArgs {
     unsigned int *queue;       // tile counter (zeroed before the launch)
     unsigned long long *hist;  // optional full histogram (single-set launches)
     long long nbins;
+    unsigned long long wait_ns;  // limit of every bounded wait (kWaitNs unless a test shortens it)
+    int starve;                  // test only: the producers skip the loads of their first stage
 };
 
 constexpr int RING = 4;  // tiles handed from the producer to the MMA and epilogue warps
@@ -584,13 +586,13 @@ action_tc_kernel(const TcArgs args) {
                 // warps through the ring
                 const int slot = n % RING;
                 const uint32_t rph = (uint32_t)(n / RING) & 1u;
-                if (!ptx::mbar_wait_bounded(&rempty[slot], rph ^ 1u, kWaitNs)) {
+                if (!ptx::mbar_wait_bounded(&rempty[slot], rph ^ 1u, args.wait_ns)) {
                     bad = true;
                     break;
                 }
                 TcTile tile;
                 if (rank == 0) {
-                    if (!mbar_wait_cl(&mail_empty[slot], rph ^ 1u, kWaitNs)) {
+                    if (!mbar_wait_cl(&mail_empty[slot], rph ^ 1u, args.wait_ns)) {
                         bad = true;
                         break;
                     }
@@ -607,7 +609,7 @@ action_tc_kernel(const TcArgs args) {
                                  : "memory");
                     mbar_arrive_cluster(cluster_addr(&mail_full[slot], 1), 1);
                 } else {
-                    if (!mbar_wait_cl(&mail_full[slot], rph, kWaitNs)) {
+                    if (!mbar_wait_cl(&mail_full[slot], rph, args.wait_ns)) {
                         bad = true;
                         break;
                     }
@@ -633,15 +635,20 @@ action_tc_kernel(const TcArgs args) {
                 if (tile.set < 0) break;
                 const int kt0 = tile.kk & 0xFFFF, kt1 = tile.kk >> 16;
                 for (int kt = kt0; kt < kt1; ++kt) {
-                    if (!mbar_wait_cl(&empty[s], ph ^ 1u, kWaitNs)) {
+                    if (!mbar_wait_cl(&empty[s], ph ^ 1u, args.wait_ns)) {
                         bad = true;
                         break;
                     }
                     if (rank == 0) ptx::mbar_arrive_expect_tx(&full[s], 2 * STAGE_BYTES);
                     unsigned char *st = base + s * STAGE_BYTES;
                     const uint32_t lead_full = cluster_addr(&full[s], 0);
-                    tma_load_2d_pair(st, mU, kt * BKB, (tile.ti + (int)rank) * BM, lead_full);
-                    tma_load_2d_pair(st + A_BYTES, mP, kt * BKB, tile.tj * BN + (int)rank * (BN / 2), lead_full);
+                    // (a failure-handling test starves the first stage: its barrier then waits for
+                    // bytes that never come, and nothing is in flight when the waits run out)
+                    if (!(args.starve && n == 0 && kt == kt0)) {
+                        tma_load_2d_pair(st, mU, kt * BKB, (tile.ti + (int)rank) * BM, lead_full);
+                        tma_load_2d_pair(st + A_BYTES, mP, kt * BKB, tile.tj * BN + (int)rank * (BN / 2),
+                                         lead_full);
+                    }
                     if (++s == STAGES) {
                         s = 0;
                         ph ^= 1u;
@@ -655,7 +662,7 @@ action_tc_kernel(const TcArgs args) {
             uint32_t ph = 0, b = 0, bph = 0;
             for (int n = 0; !bad; ++n) {
                 const int slot = n % RING;
-                if (!ptx::mbar_wait_bounded(&rfull[slot], (uint32_t)(n / RING) & 1u, kWaitNs)) {
+                if (!ptx::mbar_wait_bounded(&rfull[slot], (uint32_t)(n / RING) & 1u, args.wait_ns)) {
                     bad = true;
                     break;
                 }
@@ -665,14 +672,14 @@ action_tc_kernel(const TcArgs args) {
                 if (rank != 0) continue;  // the leader issues the pair's MMAs
                 const int kt0 = tile.kk & 0xFFFF, kt1 = tile.kk >> 16;
                 // both CTAs' epilogues have drained accumulator b
-                if (!mbar_wait_cl(&tempty[b], bph ^ 1u, kWaitNs)) {
+                if (!mbar_wait_cl(&tempty[b], bph ^ 1u, args.wait_ns)) {
                     bad = true;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t dt = tmem + b * BN;
                 for (int kt = kt0; kt < kt1; ++kt) {
-                    if (!mbar_wait_cl(&full[s], ph, kWaitNs)) {
+                    if (!mbar_wait_cl(&full[s], ph, args.wait_ns)) {
                         bad = true;
                         break;
                     }
@@ -735,7 +742,7 @@ action_tc_kernel(const TcArgs args) {
         uint32_t b = 0, bph = 0;
         for (int n = 0;; ++n) {
             const int slot = n % RING;
-            const bool got = ptx::mbar_wait_bounded(&rfull[slot], (uint32_t)(n / RING) & 1u, kWaitNs);
+            const bool got = ptx::mbar_wait_bounded(&rfull[slot], (uint32_t)(n / RING) & 1u, args.wait_ns);
             if (!__all_sync(0xffffffffu, got)) {
                 bad = true;
                 break;
@@ -747,7 +754,7 @@ action_tc_kernel(const TcArgs args) {
             }
             // the row's relation words for this warp's half of the tile's columns, staged in
             // shared memory by the producer
-            const bool staged = ptx::mbar_wait_bounded(&sfull[slot], (uint32_t)(n / RING) & 1u, kWaitNs);
+            const bool staged = ptx::mbar_wait_bounded(&sfull[slot], (uint32_t)(n / RING) & 1u, args.wait_ns);
             if (!__all_sync(0xffffffffu, staged)) {
                 bad = true;
                 break;
@@ -783,7 +790,7 @@ action_tc_kernel(const TcArgs args) {
                 }
             }
             const double phi_i = (S.acc != nullptr && i < N) ? S.phi[i] : 0.0;
-            const bool ok = mbar_wait_cl(&tfull[b], bph, kWaitNs);
+            const bool ok = mbar_wait_cl(&tfull[b], bph, args.wait_ns);
             if (!__all_sync(0xffffffffu, ok)) {
                 bad = true;
                 break;
@@ -1097,6 +1104,8 @@ static int tc_launch_fmt(const TcPlan &p, const Arena &a, cudaStream_t st) {
             args.queue = queues + ci;
             args.hist = p.hist;
             args.nbins = (long long)p.nbins;
+            args.wait_ns = wait_limit_ns(kWaitNs);
+            args.starve = starve_first_stage();
             stage_begin(CSG_STAGE_ACTION, st);
             const int pairs = std::min(clusters > 0 ? clusters : sms / 2, c.n_tiles);
             action_tc_kernel<FMT><<<2 * pairs, THREADS, smem, st>>>(args);

@@ -15,6 +15,35 @@ namespace csg {
 
 static thread_local char g_last_error[512];
 
+TestHooks &test_hooks() {
+    static TestHooks h;
+    return h;
+}
+
+static bool injected_alloc_failure() {
+    std::atomic<int> &n = test_hooks().fail_alloc;
+    int v = n.load();
+    while (v > 0)
+        if (n.compare_exchange_weak(v, v - 1)) return true;
+    return false;
+}
+
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st) {
+    if (injected_alloc_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, st);
+}
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    if (injected_alloc_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 void set_error(const char *fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
@@ -47,8 +76,8 @@ int alloc_set(csg_ctx *ctx, int d, int64_t N, csg_set **out, cudaStream_t st) {
         ctx->used += s->bytes;
     }
     s->stream = st;
-    cudaError_t e1 = cudaMallocAsync((void **)&s->coords, (size_t)N * 4 * sizeof(double) + 256, st);
-    cudaError_t e2 = cudaMallocAsync((void **)&s->rows, (size_t)N * s->stride * sizeof(uint64_t), st);
+    cudaError_t e1 = dev_malloc_async((void **)&s->coords, (size_t)N * 4 * sizeof(double) + 256, st);
+    cudaError_t e2 = dev_malloc_async((void **)&s->rows, (size_t)N * s->stride * sizeof(uint64_t), st);
     if (e1 == cudaSuccess && e2 == cudaSuccess) {
         s->err = reinterpret_cast<unsigned long long *>(s->coords + (size_t)N * 4);
         e1 = cudaMemsetAsync(s->err, 0, sizeof(unsigned long long), st);
@@ -454,5 +483,24 @@ int csg_set_info(const csg_set *set, int *d, int64_t *N, int64_t *stride_words,
 }
 
 void csg_set_free(csg_set *set) { free_set(set); }
+
+int csg_test_wait_expiry(uint64_t limit_ns, int starve) {
+    if (starve && limit_ns == 0) {
+        set_error("csg_test_wait_expiry: starving a stage needs a wait limit");
+        return CSG_E_INVAL;
+    }
+    test_hooks().wait_ns.store(limit_ns);
+    test_hooks().starve.store(starve ? 1 : 0);
+    return CSG_OK;
+}
+
+int csg_test_fail_alloc(int n) {
+    if (n < 0) {
+        set_error("csg_test_fail_alloc: n < 0");
+        return CSG_E_INVAL;
+    }
+    test_hooks().fail_alloc.store(n);
+    return CSG_OK;
+}
 
 }  // extern "C"

@@ -172,6 +172,24 @@ int tc_launch(const TcPlan &p, const Arena &a, cudaStream_t st);
 
 void set_error(const char *fmt, ...);
 
+// Failure injection for the library's own tests (csg_test_wait_expiry, csg_test_fail_alloc);
+// process-wide and off by default.
+struct TestHooks {
+    std::atomic<unsigned long long> wait_ns{0};  // nonzero: limit of every bounded device wait
+    std::atomic<int> starve{0};                  // producers skip the copies of their first stage
+    std::atomic<int> fail_alloc{0};              // the next n device allocations fail
+};
+TestHooks &test_hooks();
+// The wait limit a kernel launch gets: the test setting, else the kernel's own default.
+inline unsigned long long wait_limit_ns(unsigned long long dflt) {
+    const unsigned long long t = test_hooks().wait_ns.load(std::memory_order_relaxed);
+    return t ? t : dflt;
+}
+inline int starve_first_stage() { return test_hooks().starve.load(std::memory_order_relaxed); }
+// cudaMallocAsync / cudaMalloc, or cudaErrorMemoryAllocation while an injected failure count lasts.
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st);
+cudaError_t dev_malloc(void **p, size_t bytes);
+
 // Stage timing hooks (no-ops unless a TimerScope with timing on is active).
 void stage_begin(int stage, cudaStream_t st);
 void stage_end(int stage, cudaStream_t st);
@@ -189,7 +207,7 @@ void stage_end(int stage, cudaStream_t st);
 // with the stream-ordered allocator.
 template <typename T>
 inline cudaError_t stream_alloc(T **p, size_t count, cudaStream_t st) {
-    return cudaMallocAsync((void **)p, count * sizeof(T), st);
+    return dev_malloc_async((void **)p, count * sizeof(T), st);
 }
 
 }  // namespace csg

@@ -20,7 +20,7 @@
 namespace csg {
 
 int arena_alloc(Arena &a, cudaStream_t st) {
-    if (cudaMallocAsync((void **)&a.dev, a.bytes(), st) != cudaSuccess) {
+    if (dev_malloc_async((void **)&a.dev, a.bytes(), st) != cudaSuccess) {
         cudaGetLastError();
         a.dev = nullptr;
         set_error("scratch allocation of %zu bytes failed", a.bytes());
@@ -265,20 +265,28 @@ int run_smeared(csg_set *set, int method, double eps, double *S_eps, csg_result 
     const int64_t N = set->N;
     unsigned long long *hist = nullptr;
     double *d_S = nullptr;
-    CSG_CUDA_TRY(cudaMallocAsync((void **)&hist, (size_t)N * sizeof(unsigned long long) + 256, st));
+    if (dev_malloc_async((void **)&hist, (size_t)N * sizeof(unsigned long long) + 256, st) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("smeared: histogram allocation of %lld words failed", (long long)N);
+        return CSG_E_NOMEM;
+    }
     d_S = reinterpret_cast<double *>(reinterpret_cast<char *>(hist) + (size_t)N * sizeof(unsigned long long));
-    cudaMemsetAsync(hist, 0, (size_t)N * sizeof(unsigned long long), st);
     csg_result res;
     csg_set *one[1] = {set};
-    int rc = run_actions(one, 1, method, -1, -1, hist, N, &res, st);  // synchronises st
+    int rc = CSG_OK;
+    cudaError_t me = cudaMemsetAsync(hist, 0, (size_t)N * sizeof(unsigned long long), st);
+    if (me != cudaSuccess) {
+        set_error("smeared: histogram clear: %s", cudaGetErrorString(me));
+        rc = CSG_E_CUDA;
+    }
+    if (rc == CSG_OK) rc = run_actions(one, 1, method, -1, -1, hist, N, &res, st);  // synchronises st
     if (rc == CSG_OK) {
         smeared_kernel<<<1, 1024, 0, st>>>(hist, N, eps, d_S);
         cudaError_t le = cudaGetLastError();
+        if (le == cudaSuccess) le = cudaMemcpyAsync(S_eps, d_S, sizeof(double), cudaMemcpyDeviceToHost, st);
         if (le != cudaSuccess) {
-            set_error("smeared launch: %s", cudaGetErrorString(le));
+            set_error("smeared: %s", cudaGetErrorString(le));
             rc = CSG_E_CUDA;
-        } else {
-            cudaMemcpyAsync(S_eps, d_S, sizeof(double), cudaMemcpyDeviceToHost, st);
         }
     }
     cudaFreeAsync(hist, st);
@@ -497,7 +505,7 @@ static int build_batch_graph(csg_ctx *ctx, int n, const int32_t *d, const int64_
     Tune tune;
     if (rc == CSG_OK && method != CSG_POPC) rc = autotune(ctx, g->sets.data(), n, d, N, seed, seq, method, &tune);
     if (rc == CSG_OK) rc = build_seq(g->q, g->sets.data(), n, method, -1, -1, nullptr, 0, seed, seq, tune);
-    if (rc == CSG_OK && cudaMalloc((void **)&g->q.a.dev, g->q.a.bytes()) != cudaSuccess) {
+    if (rc == CSG_OK && dev_malloc((void **)&g->q.a.dev, g->q.a.bytes()) != cudaSuccess) {
         cudaGetLastError();
         g->q.a.dev = nullptr;
         set_error("batch: scratch allocation of %zu bytes failed", g->q.a.bytes());
