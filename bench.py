@@ -10,12 +10,14 @@ bitmap is 512 MiB, larger than the 129 MB L2, so no flush is needed between step
 Prints ONE JSON line (rank 0).  `value` is related-pair interval counts per second
 (R / step time) with the set generated on the device; `e2e` is the same metric
 through the public API from host coordinates (copied in every step) to the host
-result.  `roofline` is the action kernel of the chosen method (default: the fp8
-tensor-core form, against the fp8 tensor peak; the popcount form against the
-integer-pipe popcount peak is reported beside it); `cpu_baseline` is the CPU oracle
-on a bounded sample of the same workload.  `batch` compares the batched (CUDA-graph)
-path with one-set-at-a-time calls on 4096 mixed diamonds, and `serve` gives p50/p99
-latency of a Poisson request stream through the service (--no-workloads skips both).
+result.  `roofline` is the action kernel of the chosen method (default: the tensor-core
+form with fp4 operands, against the fp4 tensor peak; the popcount form against the
+integer-pipe popcount peak is reported beside it, and the link kernel against the fp32
+pipe for d=4 and HBM write bandwidth for d=2); `cpu_baseline` is the CPU oracle on a
+bounded, stratified sample of the same workload (the same measurement as
+`--impl reference`).  `batch` compares the batched (CUDA-graph) path with
+one-set-at-a-time calls on 4096 mixed diamonds, and `serve` gives p50/p99 latency of the
+20000-request Poisson stream through the service (--no-workloads skips both).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -206,11 +208,8 @@ def recorded_traffic(kernel: str, workload: str):
             return None
         with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
             text = fh.read()
-        # the device code: everything before the file's host-side section, with comments and
-        # whitespace removed (a comment edit does not change the kernel)
-        marker = rec.get("device_code_ends_at", "").encode()
-        if marker and marker in text:
-            text = text[:text.index(marker)]
+        # the whole source file (kernels and the host code that orders their work), with
+        # comments and whitespace removed (a comment edit does not change the kernel)
         code = re.sub(r"/\*.*?\*/", "", text.decode(), flags=re.S)
         code = re.sub(r"//[^\n]*", "", code)
         code = re.sub(r"\s+", " ", code)
@@ -240,73 +239,90 @@ def launches_per_step(N: int, tc: bool) -> int:
     return 3 + passes + 2 + (1 if tc else 0) + 2
 
 
-def cpu_baseline(threads: int = 0, rows_per_block: int = 64, blocks: int = 8):
-    """The oracle as it stands on a bounded sample: its link of the full set, then its
-    triple loop over `blocks` stratified blocks of rows."""
-    import numpy as np  # noqa: F401
+STRATA = 16  # equal row strata of the bench set; one block of rows is drawn from each in turn
 
-    import oracle
-    d, N, seed = WORKLOAD["d"], WORKLOAD["N"], WORKLOAD["seed"]
-    c = oracle.sprinkle_sorted(d, N, seed, 0)
-    rel = oracle.link(d, c, threads)
-    pairs, elapsed = 0, 0.0
-    for b in range(blocks):
-        lo = (N * b) // blocks
-        t0 = time.perf_counter()
-        out = oracle.action(rel, threads, rows=(lo, lo + rows_per_block))
-        elapsed += time.perf_counter() - t0
-        pairs += out["R"]
-    cores = threads or os.cpu_count()
-    model = None
+
+def cpu_model():
     try:
         out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
         for ln in out.splitlines():
             if ln.lower().startswith("model name"):
-                model = ln.split(":", 1)[1].strip()
-                break
+                return ln.split(":", 1)[1].strip()
     except (OSError, subprocess.SubprocessError):
         pass
-    if model is None:
-        try:
-            with open("/proc/cpuinfo") as fh:
-                for ln in fh:
-                    if ln.lower().startswith(("model name", "cpu part")):
-                        model = ln.split(":", 1)[1].strip()
-                        break
-        except OSError:
-            pass
-    return {"value": pairs / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": model,
-            "sample": f"{blocks} blocks of {rows_per_block} rows (first elements) spread over the N=65536 "
-                      f"d=4 set; {pairs} related pairs in {elapsed:.2f} s; matrix built by the oracle's link"}
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def oracle_sample(steps: int, warmup: int):
+    """The oracle as it stands on a bounded, stratified sample of the bench set (d=4,
+    N=65536, seed 1): its link of the whole set (built once, not timed), then, per step,
+    its triple loop over one block of 16 rows per thread (so every thread gets several
+    dynamic chunks), centred in stratum k mod 16 of 16 equal row strata (strata visited in
+    an interleaved order).  Returns the timed steps' pairs, bit tests and seconds."""
+    import oracle
+    d, N, seed = WORKLOAD["d"], WORKLOAD["N"], WORKLOAD["seed"]
+    threads = os.cpu_count() or 1
+    rows = 16 * threads
+    c = oracle.sprinkle_sorted(d, N, seed, 0)
+    rel = oracle.link(d, c, threads)
+    order = [0, 8, 4, 12, 2, 10, 6, 14, 1, 9, 5, 13, 3, 11, 7, 15]
+    per = {}  # stratum -> [(pairs, bit tests, seconds)] of its timed blocks
+    for k in range(warmup + steps):
+        st = order[k % STRATA]
+        mid = (2 * st + 1) * N // (2 * STRATA)
+        lo = max(0, min(N - rows, mid - rows // 2))
+        t0 = time.perf_counter()
+        out = oracle.action(rel, threads, rows=(lo, lo + rows))
+        dt = time.perf_counter() - t0
+        if k >= warmup:
+            per.setdefault(st, []).append((out["R"], out["W"], dt))
+    # stratified estimate of the whole set's rates: each visited stratum's mean block counts
+    mean = lambda v, i: sum(x[i] for x in v) / len(v)
+    P = sum(mean(v, 0) for v in per.values())
+    B = sum(mean(v, 1) for v in per.values())
+    T = sum(mean(v, 2) for v in per.values())
+    allb = [x for v in per.values() for x in v]
+    return {"pairs_per_s": P / T, "bits_per_s": B / T, "pairs": sum(x[0] for x in allb),
+            "bits": sum(x[1] for x in allb), "seconds": sum(x[2] for x in allb), "threads": threads,
+            "rows": rows, "steps": steps, "strata": len(per)}
+
+
+def sample_description(m: dict) -> str:
+    return (f"{m['steps']} blocks of {m['rows']} consecutive first elements (16 per thread), each centred in "
+            f"one of 16 equal row strata in turn ({m['strata']} strata visited), of the d=4 N=65536 set "
+            f"(seed 1); the oracle's own link of the whole set built first (not timed); {m['pairs']} related "
+            f"pairs and {m['bits']:.3e} bit tests in {m['seconds']:.2f} s; value = the strata's summed mean "
+            f"pairs per block over their summed mean seconds per block")
+
+
+def cpu_baseline():
+    """One stratum each: the same measurement as the reference arm with 16 steps."""
+    m = oracle_sample(steps=STRATA, warmup=1)
+    return {"value": m["pairs_per_s"], "unit": UNIT, "cores": m["threads"], "kind": "oracle",
+            "cpu": cpu_model(), "bit_tests_per_s": m["bits_per_s"], "sample": sample_description(m)}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    import oracle
-    d, N, seed = WORKLOAD["d"], WORKLOAD["N"], WORKLOAD["seed"]
-    c = oracle.sprinkle_sorted(d, N, seed, 0)
-    rel = oracle.link(d, c)
-    times, pairs = [], []
-    nblk = args.warmup + args.steps
-    for k in range(nblk):
-        lo = (N * (k % 8)) // 8
-        t0 = time.perf_counter()
-        out = oracle.action(rel, rows=(lo, lo + 32))
-        dt = time.perf_counter() - t0
-        if k >= args.warmup:
-            times.append(dt)
-            pairs.append(out["R"])
-    value = sum(pairs) / sum(times)
+    m = oracle_sample(steps=args.steps, warmup=args.warmup)
+    value = m["pairs_per_s"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * m["seconds"] / m["steps"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
             "config": arm_config(args.method, int(os.environ.get("WORLD_SIZE", "1"))),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "per step the oracle's triple loop over 32 consecutive rows of the "
-                                       "set (its link of the whole set built once), blocks spread over the set"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": m["threads"], "kind": "oracle",
+                             "cpu": cpu_model(), "bit_tests_per_s": m["bits_per_s"],
+                             "sample": sample_description(m)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -418,6 +434,7 @@ def bench_desitter(args):
     eta0, eps, graphs = 0.5, 2.0 ** -6, 10
     S_EH = 4 * math.pi * math.tan(eta0)
     rows = []
+    hists = []  # interval abundances of the N = 2^15 slabs (the left panel of the paper's figure)
     with csg.Context(0) as ctx:
         for p in range(10, 18):
             N = 1 << p
@@ -426,15 +443,35 @@ def bench_desitter(args):
                 s = ctx.sprinkle_desitter(N, eta0, seed=5, seq=g)
                 s.link()
                 S, _ = s.action_smeared(eps, csg.TC)
-                s.free()
                 vals.append(S)
+                if p == 15:
+                    dev = torch.zeros(N, dtype=torch.int64, device="cuda")
+                    s.action_hist(dev.data_ptr(), N, csg.TC)
+                    torch.cuda.synchronize()
+                    hists.append(dev.cpu().numpy().astype(np.float64))
+                s.free()
             torch.cuda.synchronize()
             ms = (time.perf_counter() - t0) * 1e3 / graphs
             v = np.array(vals)
             rows.append({"N": N, "mean": float(v.mean()), "std": float(v.std(ddof=1)),
                          "sem": float(v.std(ddof=1) / math.sqrt(graphs)), "ms_per_set": ms})
+    # n_i (1-based: pairs whose interval holds i - 1 elements) of the paper's figure: every i up
+    # to 64, then sums over octaves [2^k, 2^(k+1)) of i
+    H = np.array(hists)
+    top = int(np.nonzero(H.sum(axis=0))[0].max()) + 1
+    single = [{"i": m + 1, "mean": float(H[:, m].mean()), "std": float(H[:, m].std(ddof=1))} for m in range(min(64, top))]
+    octaves = []
+    lo = 64
+    while lo < top:
+        hi = min(top, 2 * lo)
+        blk = H[:, lo:hi].sum(axis=1)
+        octaves.append({"i_from": lo + 1, "i_to": hi, "mean": float(blk.mean()), "std": float(blk.std(ddof=1))})
+        lo = hi
+    abundance = {"N": 1 << 15, "sets": len(hists), "largest_i": top, "mean_pairs": float(H.sum(axis=1).mean()),
+                 "n_i": single, "octaves": octaves}
     print(json.dumps({"experiment": "smeared action in the 1+1 de Sitter slab (Sec. 5.2)", "eta0": eta0,
-                      "eps": eps, "sets_per_size": graphs, "S_EH": S_EH, "sizes": rows}), flush=True)
+                      "eps": eps, "sets_per_size": graphs, "S_EH": S_EH, "sizes": rows,
+                      "interval_abundances": abundance}), flush=True)
     return 0
 
 
@@ -740,6 +777,14 @@ def main():
     coords_host = s.coords()
     s.free()
 
+    # ---- the link kernel of the d=2 N=131072 set (seed 2), whose 2 GiB bitmap write is its bound
+    s2 = ctx.sprinkle(2, 131072, 2, seq)
+    s2.link()
+    s2.link()
+    link2_ms = ctx.stage_times()["link"]
+    link2_bytes = 131072 * s2.info()["stride"] * 8
+    s2.free()
+
     # ---- end to end through the public API from pinned host coordinates to the host result
     pinned = torch.from_numpy(coords_host).pin_memory()
     host_np = pinned.numpy()
@@ -774,7 +819,8 @@ def main():
     popc_ms = act_ms if method == csg.POPC else other_ms
     tc_ms = act_ms if is_tc else other_ms
     popc_roof = {"bound": "alu", "achieved": res.W / (popc_ms / 1e3), "peak": popc_peak,
-                 "unit": "bit-ops/s", "frac": res.W / (popc_ms / 1e3) / popc_peak, "traffic": None,
+                 "unit": "bit-ops/s", "frac": res.W / (popc_ms / 1e3) / popc_peak,
+                 "traffic": recorded_traffic("action_popc_kernel<16, 0>", f"d={d} N={N} seed {seed}"),
                  "kernel_ms": popc_ms,
                  "peak_basis": f"{SMS} SMs x {POPC_PER_SM_CLK} POPC/clk x 32 bits x {sm_max:.0f} MHz"}
     tc_ach = tc_flops / (tc_ms / 1e3) / 1e12
@@ -784,6 +830,23 @@ def main():
                "kernel_ms": tc_ms,
                "peak_basis": (f"{'fp4 = 6' if fp4 else 'fp8 = 2'} x measured bf16 dense burst "
                               "(MEASURED_PEAKS.json; nominal dense ratio), of measured")}
+    # link: d=4 against the fp32 pipe its screen runs on (the expanded interval of each pair
+    # i < k as one add and four fused multiply-adds, and the margin's second sign: 10 flops a
+    # pair), d=2 against HBM bandwidth for the bitmap it writes (every word once)
+    fp32_peak = SMS * 128 * 2 * sm_max * 1e6 / 1e12                # TFLOP/s, non-tensor
+    link4_ms = stage_avg["link"]
+    link4_flops = 10.0 * N * (N - 1) / 2
+    hbm = pk.get("hbm_gbs", 6687.1)
+    link_roof = {
+        "d4": {"bound": "fp32", "achieved": link4_flops / (link4_ms / 1e3) / 1e12, "peak": fp32_peak,
+               "unit": "TFLOP/s", "frac": link4_flops / (link4_ms / 1e3) / 1e12 / fp32_peak, "kernel_ms": link4_ms,
+               "workload": f"d=4 N={N} seed {seed}",
+               "peak_basis": f"{SMS} SMs x 128 fp32 lanes x 2 flops x {sm_max:.0f} MHz (nominal)"},
+        "d2": {"bound": "hbm", "achieved": link2_bytes / (link2_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+               "frac": link2_bytes / (link2_ms / 1e3) / 1e9 / hbm, "kernel_ms": link2_ms,
+               "workload": "d=2 N=131072 seed 2 (2 GiB bitmap written)",
+               "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), of measured"},
+    }
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -800,6 +863,7 @@ def main():
         "bitops_per_s": res.W / (act_ms / 1e3),
         "roofline": tc_roof if is_tc else popc_roof,
         "roofline_other_method": popc_roof if is_tc else tc_roof,
+        "roofline_link": link_roof,
         "e2e": {"value": e_pairs / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(host_np.nbytes),
                 "d2h_bytes_per_step": 88},
     }
@@ -807,7 +871,8 @@ def main():
         line["clocks"] = clocks
     if not args.no_workloads and world == 1:
         # the metric's other halves: batched vs plain on the 4096-set mixed workload, and
-        # served p50/p99 latency on a Poisson stream (a 300-request sample of it)
+        # served p50/p99 latency on the whole 20000-request Poisson stream at half and 0.9 of
+        # the service's capacity
         ctx.close()
         ctx = None
         ns = argparse.Namespace(**vars(args))
@@ -816,14 +881,14 @@ def main():
         line["batch"] = {"workload": b["config"]["workload"], "value": b["value"], "unit": UNIT,
                          "batched_ms": b["ms_per_step"], "plain_ms": b["plain"]["ms"],
                          "batched_over_plain": b["batched_over_plain"]}
-        ns.n_req, ns.rates = 300, "0.5,0.9"
+        ns.n_req, ns.rates = 20000, "0.5,0.9"
         v = bench_serve(ns, emit=False)
         line["serve"] = {"workload": v["config"]["workload"], "capacity_req_s": v["capacity_req_s"],
                          "plain_req_s": v["plain_req_s"],
                          "served_capacity_over_plain": v["served_capacity_over_plain"],
                          "capacity_results_equal_alone": v["capacity_results_equal_alone"],
-                         "sweep": [{k: x[k] for k in ("rate_frac", "throughput_req_s", "p50_ms", "p99_ms",
-                                                      "results_equal_alone")} for x in v["sweep"]]}
+                         "sweep": [{k: x[k] for k in ("rate_frac", "throughput_req_s", "pairs_per_s", "p50_ms",
+                                                      "p99_ms", "results_equal_alone")} for x in v["sweep"]]}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

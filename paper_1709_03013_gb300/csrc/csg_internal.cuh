@@ -164,7 +164,7 @@ struct TcPlan {
 };
 // super: side of the square blocks (in elements) in which output tiles are rasterised
 TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned long long *hist,
-               int64_t nbins, int *rc, const int *slots = nullptr, int super = 2048, int fmt = 0);
+               int64_t nbins, int *rc, const int *slots = nullptr, int super = 4096, int fmt = 0);
 int tc_patch(const TcPlan &p, Arena &a);
 int tc_launch(const TcPlan &p, const Arena &a, cudaStream_t st);
 

@@ -80,7 +80,7 @@ __global__ void finalize_kernel(const FinRow *__restrict__ rows, int n, csg_resu
 // Tunable choices of a launch sequence.
 struct Tune {
     int64_t popc_below = 0;  // with the tensor method, sets with N below this use the popcount kernel
-    int super = 2048;        // rasterisation block of the tensor kernel's output tiles
+    int super = 4096;        // rasterisation block of the tensor kernel's output tiles
 };
 
 namespace {
@@ -436,7 +436,7 @@ static int autotune(csg_ctx *ctx, csg_set *const *sets, int n, const int32_t *d,
     if (n < 16) return CSG_OK;  // small batches keep the defaults
     const std::string key = tune_key(n, d, N, method);
     if (tune_lookup(key, best)) return CSG_OK;
-    const Tune cands[] = {{0, 2048}, {1024, 2048}, {2048, 2048}, {0, 1024}};
+    const Tune cands[] = {{0, 4096}, {1024, 4096}, {2048, 4096}, {0, 2048}, {0, 1024}};
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||

@@ -5,9 +5,12 @@
 // A small pool of worker threads repeatedly takes queued requests that fit the
 // context's memory budget (admission by the set's footprint, N*N/8 bytes of bitmap plus
 // coordinates), up to a work cap per batch, and runs the whole path for them in shared
-// launches.  The oldest queued request opens each batch and only requests within a factor
-// of two of its size join it, so small requests are not held back by a large one's
-// results; batches of small sets run on a high-priority stream.  Requests that arrive
+// launches.  The smallest queued request opens each batch (shortest job first, which keeps
+// the many small requests from queueing behind a few large ones), unless a request has
+// waited longer than the age limit, in which case the oldest such request opens it (no
+// request starves, even above capacity); only requests within a factor of two of the
+// opener's size join it, so small requests are not held back by a large one's results;
+// batches of small sets run on a high-priority stream.  Requests that arrive
 // while other batches are on the GPU are admitted by the next free worker as soon as
 // memory frees up, so their kernels overlap on the device.  Results are kept per ticket
 // until csg_serve_poll collects them.
@@ -39,6 +42,7 @@ struct Req {
     ReqState state;
     int rc;
     csg_result res;
+    std::chrono::steady_clock::time_point submitted;
 };
 
 size_t footprint(int64_t N) {
@@ -69,6 +73,7 @@ struct ServeState {
     double batch_work_cap = 1e14;      // flops per batch (12 ms at the tensor form's large-set rate)
     int batch_max_sets = 4096;
     int64_t small_n = 16384;           // batches of sets up to this size run at high priority
+    std::chrono::milliseconds max_age{250};  // a request waiting longer opens the next batch
 };
 
 namespace {
@@ -97,42 +102,57 @@ void worker_main(ServeState *S) {
             std::unique_lock<std::mutex> lk(S->mu);
             for (;;) {
                 if (S->stop) break;
-                // The oldest queued request opens the batch; later ones join it while memory and
-                // the work cap allow, if their size is within a factor of two of the first's, so a
+                // The opener: the oldest request past the age limit, else the smallest (the
+                // oldest of equal size).  Others join it while memory and the work cap allow, in
+                // arrival order, if their size is within a factor of two of the opener's, so a
                 // small request never waits for a large one's results (a batch's results are
                 // ready together).  Requests passed over keep their place in the queue.
-                double work = 0.0;
-                int64_t n_lo = 0, n_hi = 0;
-                for (auto it = S->queue.begin(); it != S->queue.end() && (int)batch.size() < S->batch_max_sets;) {
-                    const uint64_t t = *it;
-                    Req &r = S->reqs[t];
+                const auto now = std::chrono::steady_clock::now();
+                auto opener = S->queue.end();
+                for (auto it = S->queue.begin(); it != S->queue.end();) {
+                    Req &r = S->reqs[*it];
                     if (r.state == Q_CANCELLED) {
                         it = S->queue.erase(it);
                         continue;
                     }
-                    if (!batch.empty() && (r.N < n_lo || r.N > n_hi)) {
-                        ++it;
-                        continue;
+                    if (now - r.submitted > S->max_age) {  // the queue is in arrival order
+                        opener = it;
+                        break;
                     }
-                    const size_t need = footprint(r.N);
+                    if (opener == S->queue.end() || r.N < S->reqs[*opener].N) opener = it;
+                    ++it;
+                }
+                double work = 0.0;
+                int64_t n_lo = 0, n_hi = 0;
+                auto fits = [&](const Req &r) {
                     size_t used;
                     {
                         std::lock_guard<std::mutex> g(ctx->mu);
                         used = ctx->used;
                     }
-                    const bool fits = ctx->budget == 0 || used + S->reserved + bytes + need <= ctx->budget;
-                    const double w = work_of(r.d, r.N);
-                    if (!fits) break;
-                    if (!batch.empty() && work + w > S->batch_work_cap) break;
-                    if (batch.empty()) {
-                        n_lo = r.N / 2;
-                        n_hi = r.N * 2;
-                    }
-                    it = S->queue.erase(it);
+                    return ctx->budget == 0 || used + S->reserved + bytes + footprint(r.N) <= ctx->budget;
+                };
+                auto take = [&](std::deque<uint64_t>::iterator it) {
+                    Req &r = S->reqs[*it];
                     r.state = Q_RUNNING;
-                    batch.push_back(t);
-                    bytes += need;
-                    work += w;
+                    batch.push_back(*it);
+                    bytes += footprint(r.N);
+                    work += work_of(r.d, r.N);
+                    return S->queue.erase(it);
+                };
+                if (opener != S->queue.end() && fits(S->reqs[*opener])) {
+                    n_lo = S->reqs[*opener].N / 2;
+                    n_hi = S->reqs[*opener].N * 2;
+                    take(opener);
+                    for (auto it = S->queue.begin(); it != S->queue.end() && (int)batch.size() < S->batch_max_sets;) {
+                        const Req &r = S->reqs[*it];
+                        if (r.state == Q_CANCELLED || r.N < n_lo || r.N > n_hi) {
+                            ++it;
+                            continue;
+                        }
+                        if (!fits(r) || work + work_of(r.d, r.N) > S->batch_work_cap) break;
+                        it = take(it);
+                    }
                 }
                 if (!batch.empty()) break;
                 S->cv_work.wait(lk);
@@ -268,6 +288,7 @@ int csg_serve_submit(csg_ctx *ctx, int d, int64_t N, uint64_t seed, uint64_t seq
         r.seq = seq;
         r.state = Q_QUEUED;
         r.rc = CSG_PENDING;
+        r.submitted = std::chrono::steady_clock::now();
         S->reqs[t] = r;
         S->queue.push_back(t);
         *ticket = t;

@@ -129,3 +129,37 @@ def test_no_fallback_without_library_or_device(lib, tmp_path):
     with pytest.raises(csg.CsgError) as e:
         csg.Context(0)
     assert e.value.code in (csg.E_CUDA, csg.E_INVAL)
+
+
+def _nvcc():
+    import shutil
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    pytest.skip("nvcc not found")
+
+
+_MMA_KERNEL = r"""
+#include <cstdint>
+__global__ void k(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+    if (threadIdx.x == 0)
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                     "tcgen05.mma.cta_group::1.kind::KIND [%0], %1, %2, %3, p;\n}\n"
+                     :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+"""
+
+
+@pytest.mark.parametrize("kind,arch,ok", [("i8", "103a", False), ("i8", "100a", True),
+                                          ("f8f6f4", "103a", True), ("f16", "103a", True)])
+def test_which_tensor_mma_kinds_exist_on_sm103a(tmp_path, kind, arch, ok):
+    """Why the tensor form uses 0/1 operands in fp8/fp4 rather than int8: ptxas has no
+    tcgen05 int8 MMA (kind::i8) for sm_103a, although it assembles one for sm_100a."""
+    import subprocess
+    src = tmp_path / "mma.cu"
+    src.write_text(_MMA_KERNEL.replace("KIND", kind))
+    r = subprocess.run([_nvcc(), "-gencode", f"arch=compute_{arch},code=sm_{arch}", "-c", str(src),
+                        "-o", str(tmp_path / "mma.o")], capture_output=True, text=True)
+    assert (r.returncode == 0) == ok, r.stderr
+    if not ok:
+        assert "kind::i8" in r.stderr and "not supported" in r.stderr

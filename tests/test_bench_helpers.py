@@ -1,5 +1,5 @@
 """Host logic of the benchmark (no GPU): the recorded ncu traffic is found for the committed
-tensor kernel and dropped when its device code changes, the launch count per step, and the
+action kernels and dropped when their source changes, the launch count per step, and the
 clock sampler's fallback when NVML cannot be loaded."""
 import importlib.util
 import os
@@ -27,6 +27,7 @@ def test_recorded_traffic_matches_committed_kernel(bench):
     fp4 = bench.recorded_traffic("action_tc_kernel<1>", "d=4 N=65536 seed 1")
     fp8 = bench.recorded_traffic("action_tc_kernel<0>", "d=4 N=65536 seed 1")
     assert fp4 is not None and fp8 is not None and fp8 > fp4 > 0
+    assert bench.recorded_traffic("action_popc_kernel<16, 0>", "d=4 N=65536 seed 1") is not None
     assert bench.recorded_traffic("action_tc_kernel<1>", "d=4 N=40000 seed 1") is None
     assert bench.recorded_traffic("no_such_kernel", "d=4 N=65536 seed 1") is None
 
@@ -50,6 +51,9 @@ def test_recorded_traffic_dropped_when_device_code_changes(bench, tmp_path, monk
     dst.write_text(text[:i] + "// a comment only\n" + text[i:])          # comments do not count
     assert bench.recorded_traffic("action_tc_kernel<1>", "d=4 N=65536 seed 1") is not None
     dst.write_text(text[:i] + "static int changed_device_code = 1;\n" + text[i:])
+    assert bench.recorded_traffic("action_tc_kernel<1>", "d=4 N=65536 seed 1") is None
+    # the host code that orders the kernel's tiles counts too (it changes the traffic)
+    dst.write_text(text + "\nstatic int changed_host_code = 1;\n")
     assert bench.recorded_traffic("action_tc_kernel<1>", "d=4 N=65536 seed 1") is None
 
 
