@@ -56,9 +56,10 @@ def arm_config(method: str, world: int) -> dict:
                    f"{'4 GiB fp4' if fp4 else '8 GiB fp8'} operands per step)"),
             "parallelism": "replicas" if world > 1 else "single"}
 
-# Popcount peak of the integer pipe: 32 32-bit POPC per SM per clock (a loop of
-# independent popcounts sustains 28 per SM per clock on this GB300), 32 bit-ops each.
-POPC_PER_SM_CLK = 32
+# Popcount peak: 16 32-bit POPC results per SM per clock (the CUDA programming guide's
+# throughput table; csg_measure_popc_rate's loop of independent popcounts sustains 15.2 on
+# this GB300, measured live in every run), 32 bit-ops each.
+POPC_PER_SM_CLK = 16
 SMS = 152
 
 
@@ -810,6 +811,7 @@ def main():
 
     pk = peaks()
     clocks = clk.summary()
+    popc_rate = csg.measure_popc_rate(local)  # popcounts per second, measured live
     sm_max = (clocks or {}).get("sm_max_mhz") or pk.get("sm_max_mhz") or 2070.0
     popc_peak = SMS * POPC_PER_SM_CLK * 32 * sm_max * 1e6          # bit-ops/s
     fp4 = method in (csg.TC, csg.TC_FP4)  # the tensor form's default format is fp4
@@ -822,7 +824,9 @@ def main():
                  "unit": "bit-ops/s", "frac": res.W / (popc_ms / 1e3) / popc_peak,
                  "traffic": recorded_traffic("action_popc_kernel<16, 0>", f"d={d} N={N} seed {seed}"),
                  "kernel_ms": popc_ms,
-                 "peak_basis": f"{SMS} SMs x {POPC_PER_SM_CLK} POPC/clk x 32 bits x {sm_max:.0f} MHz"}
+                 "peak_basis": (f"{SMS} SMs x {POPC_PER_SM_CLK} POPC/clk (CUDA guide throughput table) x 32 bits x "
+                                f"{sm_max:.0f} MHz"),
+                 "popc_probe_per_sm_clk": popc_rate / SMS / (sm_max * 1e6)}
     tc_ach = tc_flops / (tc_ms / 1e3) / 1e12
     tc_roof = {"bound": "tensor", "achieved": tc_ach, "peak": tc_peak, "unit": "TFLOP/s",
                "frac": tc_ach / tc_peak,

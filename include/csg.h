@@ -269,6 +269,14 @@ int csg_stage_times(csg_ctx *ctx, double *ms, int n);
 int csg_action_noalloc(int d, int64_t N, const uint64_t *dev_rows, int64_t stride_words,
                        csg_result *dev_out, void *stream);
 
+/* Measurement aid for the roofline of CSG_POPC: the sustained throughput of this GPU's
+ * 32-bit population-count pipe, in popcounts per second over the whole device, from a
+ * dedicated loop of independent popcounts (two 1024-thread CTAs per SM, about 50 ms).
+ * Divided by the SM count and the SM clock it gives results per SM per clock; the CUDA
+ * programming guide lists 16.  Allocates and frees a small output buffer; synchronises the
+ * device. */
+int csg_measure_popc_rate(int device, double *popc_per_second);
+
 /* Failure injection for tests of the error paths (not for production use; process-wide,
  * off by default).  No GPU faults, traps or hangs in either: the failures are made on the
  * host or by a wait that nothing completes, and every device wait is bounded.

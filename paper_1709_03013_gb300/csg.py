@@ -86,6 +86,7 @@ EXPORTS = [
     "csg_serve_cancel", "csg_export_coords", "csg_export_bitmap", "csg_set_info", "csg_set_free",
     "csg_action_noalloc", "csg_set_timing", "csg_stage_times", "csg_action_smeared",
     "csg_sprinkle_desitter", "csg_dalembertian", "csg_test_wait_expiry", "csg_test_fail_alloc",
+    "csg_measure_popc_rate",
 ]
 
 _lib = None
@@ -132,6 +133,7 @@ def load(path: str = LIB_PATH):
         "csg_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_double), i32]),
         "csg_test_wait_expiry": (i32, [u64, i32]),
         "csg_test_fail_alloc": (i32, [i32]),
+        "csg_measure_popc_rate": (i32, [i32, ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -191,6 +193,13 @@ def inject_wait_expiry(limit_ns: int, starve: bool) -> None:
 def inject_alloc_failures(n: int) -> None:
     """Failure injection (tests only): the next n device allocations of the library fail."""
     _check(load().csg_test_fail_alloc(n), "csg_test_fail_alloc")
+
+
+def measure_popc_rate(device: int = 0) -> float:
+    """Sustained 32-bit popcounts per second of the whole GPU (csg_measure_popc_rate)."""
+    v = ctypes.c_double()
+    _check(load().csg_measure_popc_rate(device, ctypes.byref(v)), "csg_measure_popc_rate")
+    return v.value
 
 
 def result_from_bytes(buf: bytes) -> Result:

@@ -506,3 +506,14 @@ def test_sets_on_side_streams(ctx, csg):
                   oracle.action(oracle.link(4, oracle.sprinkle_sorted(4, 2000, 9, 0))), 4, 2000)
     torch.cuda.synchronize()
     s.free()
+
+
+def test_popc_pipe_probe_rate(csg):
+    """The roofline of the popcount method takes 16 32-bit popcounts per SM per clock (the
+    CUDA guide's throughput table); the probe's sustained rate must agree with it."""
+    import torch
+    rate = csg.measure_popc_rate(0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    per_sm = rate / sms
+    # 12 to 17 results per SM per clock at a clock between 1.4 and 2.1 GHz
+    assert 12 * 1.4e9 < per_sm < 17 * 2.1e9, per_sm
