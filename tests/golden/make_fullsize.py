@@ -27,6 +27,11 @@ go into each file's header.
 
   python tests/golden/make_fullsize.py [--only single1,single2,single3,batch,serve]
                                        [--threads T] [--ckpt DIR]
+  python tests/golden/make_fullsize.py --verify single1,single2,batch [--threads T]
+
+--verify reruns the named parts with the oracle, compares every value with the stored files
+(writing nothing) and prints one JSON line of timings per part: how long the oracle takes on
+this machine's cores, and that it gives the same results here as where the files were written.
 """
 from __future__ import annotations
 
@@ -247,12 +252,93 @@ def run_serve(threads: int, ckpt: str) -> None:
         fh.writelines(head + body)
 
 
+def _stored_single(name: str) -> dict:
+    g = {"digests": []}
+    with open(os.path.join(HERE, name)) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            key, val = (x.strip() for x in line.split(":", 1))
+            if key == "digest":
+                g["digests"].append(tuple(val.split()))
+            elif key == "Nk":
+                g["Nk"] = [int(x) for x in val.split()]
+            elif key == "S":
+                g["S"] = float(val)
+            elif key != "hist":
+                g[key] = int(val)
+    return g
+
+
+def verify(parts: list, threads: int) -> int:
+    """Reruns the named parts with the oracle and compares them with the stored files."""
+    T = threads or os.cpu_count()
+    ok = True
+    for name in parts:
+        if name in SINGLES:
+            d, N, seed = SINGLES[name]
+            g = _stored_single(f"full_d{d}_n{N}_seed{seed}.txt")
+            t0 = time.perf_counter()
+            coords = oracle.sprinkle_sorted(d, N, seed, 0)
+            rel = oracle.link(d, coords, threads)
+            t1 = time.perf_counter()
+            out = oracle.action(rel, threads)
+            t2 = time.perf_counter()
+            f = counts_fields(d, N, out)
+            same = (f[:8] == [g["R"], *g["Nk"], g["sum_m"], g["W"], g["combo"]] and float(f[8]) == g["S"] and
+                    [(str(lo), h) for lo, h in bitmap_digests(oracle.pack(rel))] == g["digests"])
+            rec = {"part": name, "workload": f"d={d} N={N} seed {seed}", "threads": T, "cpu": cpu_model(),
+                   "link_s": t1 - t0, "count_s": t2 - t1, "pairs_per_s": out["R"] / (t2 - t1),
+                   "bit_tests_per_s": out["W"] / (t2 - t1), "equal_to_stored": bool(same)}
+            if name == "single1":
+                t3 = time.perf_counter()
+                oracle.action(rel, 1)
+                rec["count_s_1_thread"] = time.perf_counter() - t3
+            print(json.dumps(rec), flush=True)
+            ok = ok and same
+        elif name == "batch":
+            rows = {}
+            with open(os.path.join(HERE, "batch_4096_seed3.txt")) as fh:
+                for ln in fh:
+                    if not ln.startswith("#") and ln.strip():
+                        v = ln.split()
+                        rows[int(v[0])] = v
+            t_link = t_count = 0.0
+            R = W = 0
+            bad = []
+            for k, sp in enumerate(inputs.batch_workload()):
+                t0 = time.perf_counter()
+                rel = oracle.link(sp.d, oracle.sprinkle_sorted(sp.d, sp.N, sp.seed, sp.seq), threads)
+                t1 = time.perf_counter()
+                out = oracle.action(rel, threads)
+                t2 = time.perf_counter()
+                t_link += t1 - t0
+                t_count += t2 - t1
+                R += out["R"]
+                W += out["W"]
+                f = [str(x) for x in counts_fields(sp.d, sp.N, out)] + [set_digest16(oracle.pack(rel))]
+                if f != rows[k][5:]:
+                    bad.append(k)
+            print(json.dumps({"part": "batch", "workload": "4096 diamonds, seed 3", "threads": T,
+                              "cpu": cpu_model(), "link_s": t_link, "count_s": t_count, "pairs_per_s": R / t_count,
+                              "bit_tests_per_s": W / t_count, "equal_to_stored": not bad,
+                              "differing_sets": bad[:16]}), flush=True)
+            ok = ok and not bad
+        else:
+            raise SystemExit(f"--verify: unknown part {name}")
+    return 0 if ok else 1
+
+
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", default="single1,single2,batch,serve,single3")
+    ap.add_argument("--verify", default=None)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--ckpt", default=os.path.join(tempfile.gettempdir(), "csg_golden_ckpt"))
     args = ap.parse_args()
+    if args.verify:
+        return verify(args.verify.split(","), args.threads)
     os.makedirs(args.ckpt, exist_ok=True)
     for name in args.only.split(","):
         if name in SINGLES:
