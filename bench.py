@@ -198,6 +198,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+TRAFFIC_BASIS = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on this workload, recorded in "
+                 "profiles/traffic.json for this exact kernel source (hash of the whole file); null once it changed")
+
+
 def recorded_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from the committed ncu record, or None when the kernel's
     source has changed since the counters were taken (or no record exists)."""
@@ -823,6 +827,7 @@ def main():
     popc_roof = {"bound": "alu", "achieved": res.W / (popc_ms / 1e3), "peak": popc_peak,
                  "unit": "bit-ops/s", "frac": res.W / (popc_ms / 1e3) / popc_peak,
                  "traffic": recorded_traffic("action_popc_kernel<16, 0>", f"d={d} N={N} seed {seed}"),
+                 "traffic_basis": TRAFFIC_BASIS,
                  "kernel_ms": popc_ms,
                  "peak_basis": (f"{SMS} SMs x {POPC_PER_SM_CLK} POPC/clk (CUDA guide throughput table) x 32 bits x "
                                 f"{sm_max:.0f} MHz"),
@@ -831,6 +836,7 @@ def main():
     tc_roof = {"bound": "tensor", "achieved": tc_ach, "peak": tc_peak, "unit": "TFLOP/s",
                "frac": tc_ach / tc_peak,
                "traffic": recorded_traffic(f"action_tc_kernel<{1 if fp4 else 0}>", f"d={d} N={N} seed {seed}"),
+               "traffic_basis": TRAFFIC_BASIS,
                "kernel_ms": tc_ms,
                "peak_basis": (f"{'fp4 = 6' if fp4 else 'fp8 = 2'} x measured bf16 dense burst "
                               "(MEASURED_PEAKS.json; nominal dense ratio), of measured")}
