@@ -269,6 +269,17 @@ int csg_stage_times(csg_ctx *ctx, double *ms, int n);
 int csg_action_noalloc(int d, int64_t N, const uint64_t *dev_rows, int64_t stride_words,
                        csg_result *dev_out, void *stream);
 
+/* Bounds checks (the library built with CSG_CHECKED defined, e.g. by
+ * paper_1709_03013_gb300/_build.py's build(checked=True) into libcsg_checked.so): the kernels
+ * test the indices they compute before each guarded access, skip an access that would leave
+ * its buffer, and record the first such failure of each kernel group -- the check site in the
+ * top 16 bits, the low 48 bits of the offending index below -- in a device word.
+ * csg_check_words synchronises the device, copies up to n of the words (sprinkle/sort, link,
+ * popcount, tensor, pipeline, allocation-free, in that order) to words[], clears them and
+ * returns how many it wrote; 0 means no failure.  The normal build compiles no checks and
+ * returns 0. */
+int csg_check_words(uint64_t *words, int n);
+
 /* Measurement aid for the roofline of CSG_POPC: the sustained throughput of this GPU's
  * 32-bit population-count pipe, in popcounts per second over the whole device, from a
  * dedicated loop of independent popcounts (two 1024-thread CTAs per SM, about 50 ms).

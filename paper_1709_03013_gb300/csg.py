@@ -86,7 +86,7 @@ EXPORTS = [
     "csg_serve_cancel", "csg_export_coords", "csg_export_bitmap", "csg_set_info", "csg_set_free",
     "csg_action_noalloc", "csg_set_timing", "csg_stage_times", "csg_action_smeared",
     "csg_sprinkle_desitter", "csg_dalembertian", "csg_test_wait_expiry", "csg_test_fail_alloc",
-    "csg_measure_popc_rate",
+    "csg_measure_popc_rate", "csg_check_words",
 ]
 
 _lib = None
@@ -134,6 +134,7 @@ def load(path: str = LIB_PATH):
         "csg_test_wait_expiry": (i32, [u64, i32]),
         "csg_test_fail_alloc": (i32, [i32]),
         "csg_measure_popc_rate": (i32, [i32, ctypes.POINTER(ctypes.c_double)]),
+        "csg_check_words": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -193,6 +194,14 @@ def inject_wait_expiry(limit_ns: int, starve: bool) -> None:
 def inject_alloc_failures(n: int) -> None:
     """Failure injection (tests only): the next n device allocations of the library fail."""
     _check(load().csg_test_fail_alloc(n), "csg_test_fail_alloc")
+
+
+def check_words() -> list:
+    """The bounds-check words of a library built with CSG_CHECKED (read and cleared; all 0 when no
+    access left its buffer); an empty list for the normal build."""
+    arr = (ctypes.c_uint64 * 8)()
+    n = _check(load().csg_check_words(ctypes.cast(arr, ctypes.c_void_p), 8), "csg_check_words")
+    return [int(arr[k]) for k in range(n)]
 
 
 def measure_popc_rate(device: int = 0) -> float:

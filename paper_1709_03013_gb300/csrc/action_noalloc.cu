@@ -86,7 +86,7 @@ noalloc_popc_kernel(const NaSet S, int n_items, int pitch, unsigned long long *s
             const uint32_t bytes = (uint32_t)nwa * 8u;
             ptx::mbar_arrive_expect_tx(bar, bytes * (uint32_t)__popc(gmask));
             for (int r = 0; r < kG; ++r)
-                if (gmask >> r & 1u)
+                if ((gmask >> r & 1u) && CSG_IN_BOUNDS(nwa <= pitch && w0a + nwa <= stride, 0x60, i0 + r))
                     ptx::bulk_g2s(A + (size_t)r * pitch, rows + (i0 + r) * stride + w0a, bytes, bar);
         }
         const bool landed = ptx::mbar_wait_bounded(bar, phase, kWaitLimitNs);
@@ -133,11 +133,12 @@ noalloc_popc_kernel(const NaSet S, int n_items, int pitch, unsigned long long *s
 #pragma unroll
                 for (int r = 0; r < kG; ++r) acc[r] = 0;
                 for (int w = lane; w <= wj; w += 32) {
-                    uint64_t b = __ldg(bj + w);
+                    uint64_t b = CSG_IN_BOUNDS(w0a + w < stride, 0x61, j) ? __ldg(bj + w) : 0ull;
                     if (w == wj) b &= lastmask;
 #pragma unroll
                     for (int r = 0; r < kG; ++r)
-                        if (mask >> r & 1u) acc[r] += __popcll(A[(size_t)r * pitch + w] & b);
+                        if ((mask >> r & 1u) && CSG_IN_BOUNDS(w < pitch, 0x62, w))
+                            acc[r] += __popcll(A[(size_t)r * pitch + w] & b);
                 }
 #pragma unroll
                 for (int r = 0; r < kG; ++r) {
@@ -169,7 +170,7 @@ noalloc_popc_kernel(const NaSet S, int n_items, int pitch, unsigned long long *s
         }
         __syncthreads();
         // every item overwrites its whole slot, so no slot needs clearing between calls
-        if (threadIdx.x < 7) {
+        if (threadIdx.x < 7 && CSG_IN_BOUNDS(k < kMaxItems, 0x63, k)) {
             unsigned long long s = 0;
             for (int w = 0; w < kWarps; ++w) s += wsum[w][threadIdx.x];
             part[(size_t)k * kSlot + threadIdx.x] = s;
@@ -223,6 +224,8 @@ std::mutex g_setup_mu;
 unsigned long long *g_scratch_addr[kMaxDevices] = {nullptr};
 
 }  // namespace
+
+unsigned long long check_word_noalloc() { return take_check_word(); }
 }  // namespace csg
 
 using namespace csg;

@@ -69,7 +69,7 @@ __device__ __forceinline__ void sweep_rows(uint32_t mask, int cnt, int zoff, con
                                            const uint64_t *__restrict__ bj, int wj, uint64_t lastmask,
                                            int lane, int64_t j, int64_t i0, Counters &c,
                                            unsigned long long *__restrict__ hist, long long nbins,
-                                           const Smem *ctl) {
+                                           const Smem *ctl, int blim, int alim, int64_t N) {
     int off[K];
     uint32_t m = mask;
     int rsum = 0;
@@ -87,20 +87,22 @@ __device__ __forceinline__ void sweep_rows(uint32_t mask, int cnt, int zoff, con
     // through a full adder (sum and majority words) and one is counted directly, so four words
     // cost three 64-bit popcounts instead of four
     int w = 2 * lane;
+    const ulonglong2 z2 = make_ulonglong2(0ull, 0ull);
     for (; w + 65 < wj; w += 128) {  // all four words lie before row j's last word
-        const ulonglong2 b0 = __ldg(reinterpret_cast<const ulonglong2 *>(bj + w));
-        const ulonglong2 b1 = __ldg(reinterpret_cast<const ulonglong2 *>(bj + w + 64));
+        const ulonglong2 b0 = CSG_IN_BOUNDS(w + 65 < blim, 0x11, j) ? __ldg(reinterpret_cast<const ulonglong2 *>(bj + w)) : z2;
+        const ulonglong2 b1 = CSG_IN_BOUNDS(w + 65 < blim, 0x11, j) ? __ldg(reinterpret_cast<const ulonglong2 *>(bj + w + 64)) : z2;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const ulonglong2 a0 = *reinterpret_cast<const ulonglong2 *>(A + off[k] + w);
-            const ulonglong2 a1 = *reinterpret_cast<const ulonglong2 *>(A + off[k] + w + 64);
+            const bool ain = CSG_IN_BOUNDS(off[k] + w + 65 < alim, 0x12, off[k] + w);
+            const ulonglong2 a0 = ain ? *reinterpret_cast<const ulonglong2 *>(A + off[k] + w) : z2;
+            const ulonglong2 a1 = ain ? *reinterpret_cast<const ulonglong2 *>(A + off[k] + w + 64) : z2;
             const uint64_t x = a0.x & b0.x, y = a0.y & b0.y, z = a1.x & b1.x;
             const uint64_t sum = x ^ y ^ z, carry = (x & y) | (x & z) | (y & z);
             acc[k] += __popcll(sum) + 2 * __popcll(carry) + __popcll(a1.y & b1.y);
         }
     }
     for (; w <= wj; w += 64) {  // the rest, one pair per lane, the last word masked
-        ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2 *>(bj + w));
+        ulonglong2 b = CSG_IN_BOUNDS(w + 1 < blim, 0x11, j) ? __ldg(reinterpret_cast<const ulonglong2 *>(bj + w)) : z2;
         if (w + 1 >= wj) {
             if (w == wj) {
                 b.x &= lastmask;
@@ -111,7 +113,9 @@ __device__ __forceinline__ void sweep_rows(uint32_t mask, int cnt, int zoff, con
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(A + off[k] + w);
+            const ulonglong2 a = CSG_IN_BOUNDS(off[k] + w + 1 < alim, 0x12, off[k] + w)
+                                     ? *reinterpret_cast<const ulonglong2 *>(A + off[k] + w)
+                                     : z2;
             acc[k] += __popcll(a.x & b.x) + __popcll(a.y & b.y);
         }
     }
@@ -128,7 +132,8 @@ __device__ __forceinline__ void sweep_rows(uint32_t mask, int cnt, int zoff, con
             uint32_t mm = mask;  // k < cnt = popc(mask), so mm keeps a set bit
             for (int t = 0; t < k; ++t) mm &= mm - 1;
             const int r = __ffs(mm) - 1;
-            atomicAdd(&acc_phi[j], (v == 1u ? -2.0 : 1.0) * ctl->phi[i0 + r]);
+            if (CSG_IN_BOUNDS(j < N && i0 + r < N, 0x13, j))
+                atomicAdd(&acc_phi[j], (v == 1u ? -2.0 : 1.0) * ctl->phi[i0 + r]);
         }
     }
     c.R += (unsigned long long)cnt;
@@ -141,18 +146,19 @@ __device__ __forceinline__ void dispatch_rows(int cnt, uint32_t mask, const uint
                                               int pitch, const uint64_t *__restrict__ bj, int wj,
                                               uint64_t lastmask, int lane, int64_t j, int64_t i0,
                                               Counters &c, unsigned long long *__restrict__ hist,
-                                              long long nbins, const Smem *ctl) {
+                                              long long nbins, const Smem *ctl, int blim, int64_t N) {
+    const int alim = (G + 1) * pitch;  // the staged rows and the zero row after them
     const int zoff = G * pitch;  // the zero row after the G staged rows
     if (cnt <= 1)
-        sweep_rows<1, PHI>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins, ctl);
+        sweep_rows<1, PHI>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins, ctl, blim, alim, N);
     else if (cnt <= 2)
-        sweep_rows<2, PHI>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins, ctl);
+        sweep_rows<2, PHI>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins, ctl, blim, alim, N);
     else if (cnt <= 4 || G <= 4 || kMaxK <= 4) {
         if constexpr (G >= 4)
-            sweep_rows<4, PHI>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins, ctl);
+            sweep_rows<4, PHI>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins, ctl, blim, alim, N);
     } else {
         if constexpr (G >= 8 && kMaxK >= 8)
-            sweep_rows<8, PHI>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins, ctl);
+            sweep_rows<8, PHI>(mask, cnt, zoff, A, pitch, bj, wj, lastmask, lane, j, i0, c, hist, nbins, ctl, blim, alim, N);
     }
 }
 
@@ -213,7 +219,8 @@ action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict_
                 const uint32_t bytes = (uint32_t)nwa * 8u;
                 ptx::mbar_arrive_expect_tx(&ctl->bar, bytes * (uint32_t)__popc(gmask));
                 for (int r = 0; r < G; ++r)
-                    if (gmask >> r & 1u)
+                    if ((gmask >> r & 1u) &&
+                        CSG_IN_BOUNDS(nwa <= pitch && i0 + r < N && w0a + nwa <= stride, 0x10, i0 + r))
                         ptx::bulk_g2s(A + (size_t)r * pitch, rows + (i0 + r) * stride + w0a, bytes,
                                       &ctl->bar);
             }
@@ -250,7 +257,7 @@ action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict_
             const int64_t jl = jb + lane;
             uint32_t my = 0;
             if (jl < N) {
-                const uint64_t word = __ldg(rows + jl * stride + w0);
+                const uint64_t word = CSG_IN_BOUNDS(w0 < stride, 0x14, jl) ? __ldg(rows + jl * stride + w0) : 0ull;
                 my = (uint32_t)(word >> gshift) & Gbits & gmask;
                 const int64_t off = jl - i0;  // elements of the group after j do not precede it
                 if (off < G) my &= (1u << off) - 1u;
@@ -264,6 +271,7 @@ action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict_
                 const int wj = (int)((j >> 6) - w0a);                 // last word, relative
                 const uint64_t lastmask = (1ull << (j & 63)) - 1ull;  // bits k < j
                 const uint64_t *__restrict__ bj = rows + j * stride + w0a;
+                const int blim = (int)(stride - w0a);  // words of row j from w0a on
                 // at most kMaxK rows per pass keeps the row slots and sums in registers
                 uint32_t rest = mask;
                 while (rest) {
@@ -276,7 +284,7 @@ action_popc_kernel(const SetDesc *__restrict__ sets, const WorkItem *__restrict_
                     }
                     rest &= ~part;
                     dispatch_rows<G, PHI>(__popc(part), part, A, pitch, bj, wj, lastmask, lane, j, i0, cnt, hist, nbins,
-                                     ctl);
+                                          ctl, blim, N);
                 }
             }
         }
@@ -320,6 +328,8 @@ int launch_g(const PopcPlan &p, const Arena &a, cudaStream_t st) {
 }
 
 }  // namespace
+
+unsigned long long check_word_popc() { return take_check_word(); }
 
 // Shared-memory budget for the staged rows of one CTA.
 static constexpr size_t kRowBudget = 200 * 1024;

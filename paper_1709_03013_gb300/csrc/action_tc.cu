@@ -171,11 +171,12 @@ __global__ void expand_kernel(const TcSetDesc *__restrict__ sets, const int64_t 
         const int64_t p1 = min(wpr, (i / BN + 1) * BN / 64);                // P words read: [0, p1)
         for (int64_t w = u0 + lane; w < wpr; w += 32) {
             const int64_t k0 = w * 64;
-            uint64_t m = __ldg(row + w);
+            uint64_t m = CSG_IN_BOUNDS(w < S.stride, 0x20, w) ? __ldg(row + w) : 0ull;
             if (k0 + 63 <= i)
                 m = 0;
             else if (k0 <= i)
                 m &= ~((2ull << (i - k0)) - 1ull);  // keep k > i
+            if (!CSG_IN_BOUNDS(i < S.N && (FMT ? k0 / 2 + 32 : k0 + 64) <= S.kp, 0x21, w)) continue;
             if (FMT)
                 put64_fp4(urow + k0 / 2, m);
             else
@@ -183,11 +184,12 @@ __global__ void expand_kernel(const TcSetDesc *__restrict__ sets, const int64_t 
         }
         for (int64_t w = lane; w < p1; w += 32) {
             const int64_t k0 = w * 64;
-            uint64_t m = __ldg(row + w);
+            uint64_t m = CSG_IN_BOUNDS(w < S.stride, 0x20, w) ? __ldg(row + w) : 0ull;
             if (k0 >= i)
                 m = 0;
             else if (k0 + 63 >= i)
                 m &= (1ull << (i - k0)) - 1ull;  // keep k < i
+            if (!CSG_IN_BOUNDS(i < S.N && (FMT ? k0 / 2 + 32 : k0 + 64) <= S.kp, 0x21, w)) continue;
             if (FMT)
                 put64_fp4(prow + k0 / 2, m);
             else
@@ -634,6 +636,14 @@ action_tc_kernel(const TcArgs args) {
                 mbar_arrive(&rfull[slot]);
                 if (tile.set < 0) break;
                 const int kt0 = tile.kk & 0xFFFF, kt1 = tile.kk >> 16;
+#ifdef CSG_CHECKED
+                {  // the tile lies in its set and its K range in the set's operand rows
+                    const TcSetDesc &TS = args.sets[tile.set];
+                    CSG_IN_BOUNDS((int64_t)tile.ti * BM < TS.N && (int64_t)tile.tj * BN < TS.N &&
+                                      (int64_t)kt1 * BKB <= TS.kp && kt0 <= kt1,
+                                  0x22, tile.ti);
+                }
+#endif
                 for (int kt = kt0; kt < kt1; ++kt) {
                     if (!mbar_wait_cl(&empty[s], ph ^ 1u, args.wait_ns)) {
                         bad = true;
@@ -759,7 +769,10 @@ action_tc_kernel(const TcArgs args) {
                 bad = true;
                 break;
             }
-            const ulonglong2 wv = *reinterpret_cast<const ulonglong2 *>(sbits + slot * (BITS_BYTES / 8) + r * 4 + 2 * g);
+            const int bidx = slot * (BITS_BYTES / 8) + r * 4 + 2 * g;
+            const ulonglong2 wv = CSG_IN_BOUNDS(bidx + 1 < RING * (BITS_BYTES / 8), 0x23, bidx)
+                                      ? *reinterpret_cast<const ulonglong2 *>(sbits + bidx)
+                                      : make_ulonglong2(0ull, 0ull);
             mbar_arrive(&rempty[slot]);  // the slot's tile and words are read
             if (tile.set != cur) {
                 if (cur >= 0) flush(cur);
@@ -938,6 +951,8 @@ int encode_bits_map(CUtensorMap *m, const uint64_t *rows, int64_t N, int64_t str
 }
 
 }  // namespace
+
+unsigned long long check_word_tc() { return take_check_word(); }
 
 // Largest N the tensor form accepts (every N a set can have): its operands take N^2
 // bytes of scratch in fp4 (64 GiB at N = 2^18) and 2 N^2 in fp8 (128 GiB).  The fp32

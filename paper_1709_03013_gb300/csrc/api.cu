@@ -484,6 +484,24 @@ int csg_set_info(const csg_set *set, int *d, int64_t *N, int64_t *stride_words,
 
 void csg_set_free(csg_set *set) { free_set(set); }
 
+int csg_check_words(uint64_t *words, int n) {
+    if (!words || n < 0) {
+        set_error("csg_check_words: bad arguments");
+        return CSG_E_INVAL;
+    }
+#ifdef CSG_CHECKED
+    cudaDeviceSynchronize();
+    const unsigned long long w[6] = {check_word_sprinkle(), check_word_link(), check_word_popc(),
+                                     check_word_tc(), check_word_pipeline(), check_word_noalloc()};
+    const int k = n < 6 ? n : 6;
+    for (int q = 0; q < k; ++q) words[q] = w[q];
+    return k;
+#else
+    (void)words;
+    return 0;  // the normal build compiles no checks
+#endif
+}
+
 int csg_test_wait_expiry(uint64_t limit_ns, int starve) {
     if (starve && limit_ns == 0) {
         set_error("csg_test_wait_expiry: starving a stage needs a wait limit");

@@ -168,6 +168,43 @@ TcPlan tc_plan(const SetDesc *sets, int n, Arena &a, size_t s_counters, unsigned
 int tc_patch(const TcPlan &p, Arena &a);
 int tc_launch(const TcPlan &p, const Arena &a, cudaStream_t st);
 
+// ---------------------------------------------------------------- checked build
+//
+// The bounds-checked build (compiled with -DCSG_CHECKED; compute-sanitizer is not available
+// to this project): CSG_IN_BOUNDS(cond, site, value) guards a memory access whose index the
+// kernel computed.  In the checked build a false condition records the first failure of this
+// translation unit -- the site number in the top 16 bits, the low 48 bits of the offending
+// value below -- in a device word, and the access it guards is skipped; the host reads and
+// clears the words with csg_check_words.  In the normal build the macro is `true` and
+// compiles away.
+#ifdef CSG_CHECKED
+static __device__ unsigned long long g_csg_check;
+__device__ __forceinline__ bool csg_in_bounds(bool ok, unsigned site, long long v) {
+    if (!ok)
+        atomicCAS(&g_csg_check, 0ull,
+                  ((unsigned long long)site << 48) | ((unsigned long long)v & 0xFFFFFFFFFFFFull));
+    return ok;
+}
+#define CSG_IN_BOUNDS(cond, site, v) ::csg::csg_in_bounds((cond), (site), (long long)(v))
+// this translation unit's check word, read and cleared (host side)
+static inline unsigned long long take_check_word() {
+    unsigned long long v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_csg_check, sizeof v) != cudaSuccess) v = ~0ull;
+    cudaMemcpyToSymbol(g_csg_check, &z, sizeof z);
+    return v;
+}
+#else
+#define CSG_IN_BOUNDS(cond, site, v) true
+static inline unsigned long long take_check_word() { return 0; }
+#endif
+// Check words of the kernel groups, one per translation unit (0: no failure).
+unsigned long long check_word_sprinkle();
+unsigned long long check_word_link();
+unsigned long long check_word_popc();
+unsigned long long check_word_tc();
+unsigned long long check_word_pipeline();
+unsigned long long check_word_noalloc();
+
 // ---------------------------------------------------------------- errors
 
 void set_error(const char *fmt, ...);

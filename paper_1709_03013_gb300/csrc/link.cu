@@ -441,19 +441,19 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
     const int64_t kc = K + r;
     if (diag) {
         // both halves land in the same words: OR them
-        if (i < N) {
+        if (i < N && CSG_IN_BOUNDS(K / 64 + kTileWords <= stride, 0x30, i)) {
             uint64_t *dst = rows + i * stride + K / 64;
 #pragma unroll
             for (int w = 0; w < kTileWords; ++w)
                 dst[w] = ow[w][r] | (uint64_t)tb[r][2 * w] | ((uint64_t)tb[r][2 * w + 1] << 32);
         }
     } else {
-        if (i < N) {
+        if (i < N && CSG_IN_BOUNDS(K / 64 + kTileWords <= stride, 0x30, i)) {
             uint64_t *dst = rows + i * stride + K / 64;
             reinterpret_cast<ulonglong2 *>(dst)[0] = make_ulonglong2(ow[0][r], ow[1][r]);
             reinterpret_cast<ulonglong2 *>(dst)[1] = make_ulonglong2(ow[2][r], ow[3][r]);
         }
-        if (kc < N) {
+        if (kc < N && CSG_IN_BOUNDS(R / 64 + kTileWords <= stride, 0x31, kc)) {
             uint64_t mw[kTileWords];
 #pragma unroll
             for (int w = 0; w < kTileWords; ++w)
@@ -466,6 +466,8 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
 }
 
 }  // namespace
+
+unsigned long long check_word_link() { return take_check_word(); }
 
 LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
     LinkPlan p;

@@ -572,4 +572,6 @@ int run_batch_graph(csg_ctx *ctx, int n, const int32_t *d, const int64_t *N, con
     return collect(out, n);
 }
 
+unsigned long long check_word_pipeline() { return take_check_word(); }
+
 }  // namespace csg

@@ -107,20 +107,27 @@ void worker_main(ServeState *S) {
                 // arrival order, if their size is within a factor of two of the opener's, so a
                 // small request never waits for a large one's results (a batch's results are
                 // ready together).  Requests passed over keep their place in the queue.
+                // tickets that were cancelled (or cancelled and already collected) leave the queue
+                // first, in a pass of their own: erasing from the deque invalidates its iterators
+                S->queue.erase(std::remove_if(S->queue.begin(), S->queue.end(),
+                                              [&](uint64_t t) {
+                                                  auto f = S->reqs.find(t);
+                                                  return f == S->reqs.end() || f->second.state == Q_CANCELLED;
+                                              }),
+                               S->queue.end());
                 const auto now = std::chrono::steady_clock::now();
-                auto opener = S->queue.end();
-                for (auto it = S->queue.begin(); it != S->queue.end();) {
-                    Req &r = S->reqs[*it];
-                    if (r.state == Q_CANCELLED) {
-                        it = S->queue.erase(it);
-                        continue;
-                    }
+                uint64_t opener = 0;
+                int64_t opener_n = 0;
+                for (uint64_t t : S->queue) {
+                    const Req &r = S->reqs.find(t)->second;
                     if (now - r.submitted > S->max_age) {  // the queue is in arrival order
-                        opener = it;
+                        opener = t;
                         break;
                     }
-                    if (opener == S->queue.end() || r.N < S->reqs[*opener].N) opener = it;
-                    ++it;
+                    if (opener == 0 || r.N < opener_n) {
+                        opener = t;
+                        opener_n = r.N;
+                    }
                 }
                 double work = 0.0;
                 int64_t n_lo = 0, n_hi = 0;
@@ -133,20 +140,20 @@ void worker_main(ServeState *S) {
                     return ctx->budget == 0 || used + S->reserved + bytes + footprint(r.N) <= ctx->budget;
                 };
                 auto take = [&](std::deque<uint64_t>::iterator it) {
-                    Req &r = S->reqs[*it];
+                    Req &r = S->reqs.find(*it)->second;
                     r.state = Q_RUNNING;
                     batch.push_back(*it);
                     bytes += footprint(r.N);
                     work += work_of(r.d, r.N);
                     return S->queue.erase(it);
                 };
-                if (opener != S->queue.end() && fits(S->reqs[*opener])) {
-                    n_lo = S->reqs[*opener].N / 2;
-                    n_hi = S->reqs[*opener].N * 2;
-                    take(opener);
+                if (opener != 0 && fits(S->reqs.find(opener)->second)) {
+                    n_lo = S->reqs.find(opener)->second.N / 2;
+                    n_hi = S->reqs.find(opener)->second.N * 2;
+                    take(std::find(S->queue.begin(), S->queue.end(), opener));
                     for (auto it = S->queue.begin(); it != S->queue.end() && (int)batch.size() < S->batch_max_sets;) {
-                        const Req &r = S->reqs[*it];
-                        if (r.state == Q_CANCELLED || r.N < n_lo || r.N > n_hi) {
+                        const Req &r = S->reqs.find(*it)->second;
+                        if (r.N < n_lo || r.N > n_hi) {
                             ++it;
                             continue;
                         }

@@ -266,6 +266,7 @@ chunk_sort_kernel(const SetRow *__restrict__ sets, const int64_t *__restrict__ c
         }
     }
     for (int t = threadIdx.x; t < len; t += kSortThreads) {
+        if (!CSG_IN_BOUNDS(c * kChunk + t < S.N, 0x42, base + t)) continue;
         out.k1[base + t] = s1[t];
         out.k2[base + t] = s2[t];
         out.idx[base + t] = si[t];
@@ -303,6 +304,7 @@ __global__ void merge_pass_kernel(const SetRow *__restrict__ sets, const int64_t
                 dst = pair_lo + (p - run * w) + (lo - sib_lo);
             }
         }
+        if (!CSG_IN_BOUNDS(dst >= 0 && dst < S.N, 0x40, g)) continue;
         out.k1[S.off + dst] = a1;
         out.k2[S.off + dst] = a2;
         out.idx[S.off + dst] = ai;
@@ -319,6 +321,7 @@ __global__ void gather_kernel(const SetRow *__restrict__ sets, const int64_t *__
         const SetRow S = sets[s];
         const int64_t p = g - S.off;
         const int64_t src = S.off + idx[g];
+        if (!CSG_IN_BOUNDS(idx[g] < (uint64_t)S.N && p < S.N, 0x41, g)) continue;
 #pragma unroll
         for (int r = 0; r < 4; ++r) S.coords[r * S.N + p] = tmp[r * E + src];
     }
@@ -331,6 +334,8 @@ int grid_for(int64_t E, int threads) {
 }
 
 }  // namespace
+
+unsigned long long check_word_sprinkle() { return take_check_word(); }
 
 SprinklePlan sprinkle_plan(const SprinkleSpec *specs, int n, Arena &a, bool from_coords,
                            size_t s_counters) {

@@ -163,3 +163,9 @@ def test_which_tensor_mma_kinds_exist_on_sm103a(tmp_path, kind, arch, ok):
     assert (r.returncode == 0) == ok, r.stderr
     if not ok:
         assert "kind::i8" in r.stderr and "not supported" in r.stderr
+
+
+def test_normal_build_compiles_no_bounds_checks(lib):
+    words = (ctypes.c_uint64 * 8)()
+    lib.csg_check_words.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.csg_check_words(ctypes.cast(words, ctypes.c_void_p), 8) == 0
