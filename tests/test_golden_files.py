@@ -92,3 +92,24 @@ def test_batch_file_matches_its_workload_and_fresh_oracle_runs():
             tuple(_fields(row)[x] for x in ("R", "Nk", "sum_m", "W", "combo"))
         words = np.ascontiguousarray(oracle.pack(want["rel"])).astype("<u8")
         assert hashlib.sha256(words.tobytes()).hexdigest()[:16] == row["bitmap_sha256_16"]
+def test_serve_file_matches_its_sample_and_fresh_oracle_runs():
+    mk = _load("make_fullsize")
+    rows = _read_table("serve_20000_seed4_sample.txt")
+    reqs = inputs.serve_workload(n_req=20000)
+    keys = [int(r["key"]) for r in rows]
+    assert keys == mk.serve_sample(reqs)
+    assert sum(reqs[k].spec.N > 4096 for k in keys) == 64
+    kset = set(keys)
+    assert all(k in kset for k in range(20000) if reqs[k].spec.N <= 4096)
+    for row in rows:
+        sp = reqs[int(row["key"])].spec
+        assert (int(row["d"]), int(row["N"]), int(row["seed"]), int(row["seq"])) == (sp.d, sp.N, sp.seed, sp.seq)
+        _check_finalize(sp.d, sp.N, _fields(row))
+    for k in np.random.default_rng(12).choice(len(rows), 4, replace=False):
+        row = rows[k]
+        if int(row["N"]) > 1500:
+            continue
+        sp = reqs[int(row["key"])].spec
+        want = oracle.run(sp.d, sp.N, sp.seed, sp.seq)
+        assert (want["R"], [int(x) for x in want["Nk"]], want["sum_m"], want["W"], want["combo"]) == \
+            tuple(_fields(row)[x] for x in ("R", "Nk", "sum_m", "W", "combo"))

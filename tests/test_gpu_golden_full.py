@@ -110,3 +110,19 @@ def test_batch_of_4096_against_full_oracle_runs(csg):
             if hashlib.sha256(w.tobytes()).hexdigest()[:16] != row["bitmap_sha256_16"]:
                 bad.append(k)
         assert not bad, f"bitmaps of sets {bad[:16]} differ"
+
+
+def test_served_sample_against_full_oracle_runs(csg):
+    rows = read_table("serve_20000_seed4_sample.txt")
+    reqs = inputs.serve_workload(n_req=20000)
+    assert len(rows) > 6000 and sum(int(r["N"]) > 4096 for r in rows) == 64
+    with csg.Context(0, budget_bytes=160 * 10 ** 9) as ctx:
+        tickets = []
+        for row in rows:
+            sp = reqs[int(row["key"])].spec
+            assert (sp.d, sp.N, sp.seed, sp.seq) == (int(row["d"]), int(row["N"]), int(row["seed"]), int(row["seq"]))
+            tickets.append(ctx.serve_submit(sp.d, sp.N, sp.seed, sp.seq))
+        for row, t in zip(rows, tickets):
+            r = ctx.serve_poll(t, timeout_ms=600000)
+            assert r.d == int(row["d"]) and r.N == int(row["N"])
+            _same_counts(r, _row_fields(row), ("request", row["key"]))
