@@ -92,6 +92,8 @@ def test_batch_file_matches_its_workload_and_fresh_oracle_runs():
             tuple(_fields(row)[x] for x in ("R", "Nk", "sum_m", "W", "combo"))
         words = np.ascontiguousarray(oracle.pack(want["rel"])).astype("<u8")
         assert hashlib.sha256(words.tobytes()).hexdigest()[:16] == row["bitmap_sha256_16"]
+
+
 def test_serve_file_matches_its_sample_and_fresh_oracle_runs():
     mk = _load("make_fullsize")
     rows = _read_table("serve_20000_seed4_sample.txt")
