@@ -40,7 +40,7 @@ def _check_finalize(d, N, fields):
     assert combo == fields["combo"] and S == fields["S"]
 
 
-SINGLES = ["full_d2_n2048_seed0.txt", "full_d4_n65536_seed1.txt"]
+SINGLES = ["full_d2_n2048_seed0.txt", "full_d4_n65536_seed1.txt", "full_d2_n131072_seed2.txt"]
 
 
 @pytest.mark.parametrize("name", SINGLES)

@@ -57,7 +57,8 @@ def _block_digests(words, rows_per):
     return out
 
 
-@pytest.mark.parametrize("name", ["full_d2_n2048_seed0.txt", "full_d4_n65536_seed1.txt"])
+@pytest.mark.parametrize("name", ["full_d2_n2048_seed0.txt", "full_d4_n65536_seed1.txt",
+                                  "full_d2_n131072_seed2.txt"])
 def test_single_set_against_full_oracle_run(csg, name):
     import torch
     g = read_full(name)
