@@ -2,9 +2,9 @@
 // "Optimized GPU Linking Algorithm": tiles of the adjacency matrix, coordinates
 // staged in shared memory, dense output).
 //
-// A CTA owns a 256 x 256 tile (row block bi <= column block bj) of the upper
-// triangle.  Warp w computes the 64-column word q = w / 2 of the tile for 4 x 32 rows
-// (rows 32 (w & 1) + 64 s + lane, s = 0..3), so the column coordinates it reads from
+// d=4 and the de Sitter slab: a CTA owns a 256 x 256 tile (row block bi <= column block
+// bj) of the upper triangle.  Warp w computes the 64-column word q = w / 2 of the tile for
+// 4 x 32 rows (rows 32 (w & 1) + 64 s + lane, s = 0..3), so the column coordinates it reads from
 // shared memory are the same for all of its lanes (broadcast 16-byte loads, one load
 // per coordinate for four columns, used for four rows).  Row words are staged in shared
 // memory and written as 32-byte row segments.  The lower triangle is the same tile
@@ -37,10 +37,7 @@
 //     pairs between them are evaluated in double (from shared memory).
 //
 // d=2 (flat diamond): related iff u_i < u_k and v_i < v_k (light-cone coordinates) in
-// double.  Rounding to float keeps order (x <= y => fl(x) <= fl(y)) and the float
-// difference of two floats is zero only if they are equal, so e = max(U_i - U_k,
-// V_i - V_k) < 0 means related, e > 0 unrelated, and e == 0 (a float tie) is decided
-// in double.  -0 is folded onto +0 first, so that equal values give e = +0.
+// double; this product order is settled without a pair-by-pair test (link_d2_kernel below).
 //
 // 1+1 de Sitter slab (Sec. 5.1): related when the shorter arc between the angles is below
 // |d eta|, i.e. pi - |pi - |d theta|| < |d eta| in double.  With |eta| < pi/2 and theta in
@@ -69,15 +66,15 @@ struct LinkRow {
     int64_t N, stride;
     const double *coords;
     uint64_t *rows;
-    int64_t tile_off;
-    int64_t nb, nbc;  // row blocks, column blocks
+    int64_t tile_off;  // first CTA of the set (d=4, de Sitter: one per tile; d=2: per row-block chunk)
+    int64_t nb, nbc;   // row blocks, column blocks
     int64_t eoff;     // first element of the set within its geometry's elements
-    int64_t foff;     // first float of the set's screen values (kFloats[D] rows of N)
-    float margin;     // float-screen margin: d=4 4e-6 S^2 on e, de Sitter 1e-5, d=2 0
+    int64_t foff;     // first float of the set's screen values (screen_floats(d) rows of N)
+    float margin;     // float-screen margin: d=4 4e-6 S^2 on e, de Sitter 1e-5
     float pad2;
 };
 
-// float screen values per element: d=4 T, X, Y, Z, -H; d=2 U, V; de Sitter eta, theta
+// float screen values per element: d=4 T, X, Y, Z, -H; de Sitter eta, theta
 __host__ __device__ constexpr int screen_floats(int d) { return d == 4 ? 5 : 2; }
 
 __device__ __forceinline__ int find_set(const int64_t *__restrict__ starts, int n, int64_t g) {
@@ -120,7 +117,6 @@ __device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
 __device__ __forceinline__ uint32_t push_sign(float e, uint32_t acc) {
     return __funnelshift_l(__float_as_uint(e), acc, 1);
 }
-__device__ __forceinline__ float fold_zero(float x) { return x == 0.f ? 0.f : x; }
 
 // 1+1 de Sitter slab (Sec. 5.1): related iff pi - |pi - |d theta|| < |d eta| in double
 __device__ __forceinline__ bool exact_ds(double ei, double thi, double ek, double thk) {
@@ -153,13 +149,10 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
 
 // Screen values of one element from its double coordinates (rounded once to float):
 // d=4 T, X, Y, Z, -H with H = fl(h), h = (t^2 - x^2 - y^2 - z^2) / 2 formed in double;
-// d=2 U, V with -0 folded onto +0; de Sitter eta, theta.
+// de Sitter eta, theta.
 template <int D>
 __device__ __forceinline__ void screen_values(const double *v, float *f) {
-    if (D == 2) {
-        f[0] = fold_zero(__double2float_rn(v[2]));
-        f[1] = fold_zero(__double2float_rn(v[3]));
-    } else if (D == 4) {
+    if (D == 4) {
 #pragma unroll
         for (int a = 0; a < 4; ++a) f[a] = __double2float_rn(v[a]);
         f[4] = -__double2float_rn(0.5 * (v[0] * v[0] - ((v[1] * v[1] + v[2] * v[2]) + v[3] * v[3])));
@@ -188,12 +181,11 @@ link_screen_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__
     for (int a = 0; a < screen_floats(D); ++a) F[S.foff + a * N + e] = f[a];
 }
 
-// The double decision for tile row rt and tile column c (Sec. 2.2; d=4 and d=2 in the
-// time order of the set, de Sitter on the cylinder).  rd, cd: the tile's row and column
-// coordinates in double (d=4 t, x, y, z; d=2 u, v; de Sitter eta, theta).
+// The double decision for tile row rt and tile column c (Sec. 2.2; d=4 in the time order of
+// the set, de Sitter on the cylinder).  rd, cd: the tile's row and column coordinates in
+// double (d=4 t, x, y, z; de Sitter eta, theta).
 template <int D>
 __device__ __forceinline__ bool exact_pair(const double (*rd)[kTile], const double (*cd)[kTile], int rt, int c) {
-    if (D == 2) return rd[0][rt] < cd[0][c] && rd[1][rt] < cd[1][c];
     if (D == 4) return exact4(rd[0][rt], rd[1][rt], rd[2][rt], rd[3][rt], cd[0][c], cd[1][c], cd[2][c], cd[3][c]);
     return exact_ds(rd[0][rt], rd[1][rt], cd[0][c], cd[1][c]);
 }
@@ -221,23 +213,15 @@ __device__ __noinline__ uint64_t word_by_pair_ds(int q, int c0, int ncol, const 
     return acc;
 }
 
-// The packed screen over one full 64-column word for the thread's four rows (d=2 and
-// d=4).  a[s][0..4]: row s's screen values, each duplicated into both halves of a
-// packed pair.  Bit b of a word stands for column 64 q + b.
-//   d=4: a[s][4] is fl(-H_i + m), so the chain gives e' ~ e + m; A[s] holds the sign
-//        bits of e' (certainly related) and B[s] those of e' - 2m (related, or inside
-//        the margin): B & ~A are the pairs to decide in double.
-//   d=2: A[s] holds the sign bits of e (related unless a float tie).  TIES: B[s] holds
-//        the sign bits of e - 2^-149, i.e. e <= 0 (ties and related; denormals are kept);
-//        otherwise B[s] is all-ones when some |e| of the word is 0 (cheaper, for words
-//        off the diagonal, where ties are rare: the whole word is then decided in double).
-template <int D, bool TIES>
+// The packed d=4 screen over one full 64-column word for the thread's four rows.
+// a[s][0..4]: row s's screen values, each duplicated into both halves of a packed pair;
+// a[s][4] is fl(-H_i + m), so the chain gives e' ~ e + m.  A[s] holds the sign bits of e'
+// (certainly related) and B[s] those of e' - 2m (related, or inside the margin): B & ~A are
+// the pairs to decide in double.  Bit b of a word stands for column 64 q + b.
 __device__ __forceinline__ void word_packed(int q, const float (*cf)[kTile], const uint64_t (*a)[5],
                                             uint64_t m2n, uint64_t *A, uint64_t *B) {
-    float mn[kRowsPer];
 #pragma unroll
     for (int s = 0; s < kRowsPer; ++s) {
-        mn[s] = __int_as_float(0x7f800000);  // +inf
         A[s] = 0;
         B[s] = 0;
     }
@@ -248,64 +232,37 @@ __device__ __forceinline__ void word_packed(int q, const float (*cf)[kTile], con
 #pragma unroll 1
         for (int j = 7; j >= 0; --j) {
             const int c = 64 * q + 32 * h + 4 * j;
-            if (D == 4) {
-                const ulonglong2 cT = *reinterpret_cast<const ulonglong2 *>(&cf[0][c]);
-                const ulonglong2 cX = *reinterpret_cast<const ulonglong2 *>(&cf[1][c]);
-                const ulonglong2 cY = *reinterpret_cast<const ulonglong2 *>(&cf[2][c]);
-                const ulonglong2 cZ = *reinterpret_cast<const ulonglong2 *>(&cf[3][c]);
-                const ulonglong2 cH = *reinterpret_cast<const ulonglong2 *>(&cf[4][c]);
+            const ulonglong2 cT = *reinterpret_cast<const ulonglong2 *>(&cf[0][c]);
+            const ulonglong2 cX = *reinterpret_cast<const ulonglong2 *>(&cf[1][c]);
+            const ulonglong2 cY = *reinterpret_cast<const ulonglong2 *>(&cf[2][c]);
+            const ulonglong2 cZ = *reinterpret_cast<const ulonglong2 *>(&cf[3][c]);
+            const ulonglong2 cH = *reinterpret_cast<const ulonglong2 *>(&cf[4][c]);
 #pragma unroll
-                for (int s = 0; s < kRowsPer; ++s) {
-                    uint64_t e01 = fadd2(cH.x, a[s][4]);
-                    uint64_t e23 = fadd2(cH.y, a[s][4]);
-                    e01 = ffma2(cT.x, a[s][0], e01);
-                    e23 = ffma2(cT.y, a[s][0], e23);
-                    e01 = ffma2(cX.x, a[s][1], e01);
-                    e23 = ffma2(cX.y, a[s][1], e23);
-                    e01 = ffma2(cY.x, a[s][2], e01);
-                    e23 = ffma2(cY.y, a[s][2], e23);
-                    e01 = ffma2(cZ.x, a[s][3], e01);
-                    e23 = ffma2(cZ.y, a[s][3], e23);
-                    float e0, e1, e2, e3, f0, f1, f2, f3;
-                    unpack2(e01, e0, e1);
-                    unpack2(e23, e2, e3);
-                    unpack2(fadd2(e01, m2n), f0, f1);
-                    unpack2(fadd2(e23, m2n), f2, f3);
-                    acc[s] = push_sign(e0, push_sign(e1, push_sign(e2, push_sign(e3, acc[s]))));
-                    bcc[s] = push_sign(f0, push_sign(f1, push_sign(f2, push_sign(f3, bcc[s]))));
-                }
-            } else {
-                const ulonglong2 cU = *reinterpret_cast<const ulonglong2 *>(&cf[0][c]);
-                const ulonglong2 cV = *reinterpret_cast<const ulonglong2 *>(&cf[1][c]);
-#pragma unroll
-                for (int s = 0; s < kRowsPer; ++s) {
-                    float u0, u1, u2, u3, w0, w1, w2, w3;
-                    unpack2(fadd2(cU.x, a[s][0]), u0, u1);
-                    unpack2(fadd2(cU.y, a[s][0]), u2, u3);
-                    unpack2(fadd2(cV.x, a[s][1]), w0, w1);
-                    unpack2(fadd2(cV.y, a[s][1]), w2, w3);
-                    const float e0 = fmaxf(u0, w0), e1 = fmaxf(u1, w1), e2 = fmaxf(u2, w2), e3 = fmaxf(u3, w3);
-                    acc[s] = push_sign(e0, push_sign(e1, push_sign(e2, push_sign(e3, acc[s]))));
-                    if (TIES) {
-                        const float dn = -0x1p-149f;
-                        bcc[s] = push_sign(__fadd_rn(e0, dn),
-                                           push_sign(__fadd_rn(e1, dn),
-                                                     push_sign(__fadd_rn(e2, dn), push_sign(__fadd_rn(e3, dn), bcc[s]))));
-                    } else {
-                        mn[s] = fminf(mn[s], fminf(fminf(fabsf(e0), fabsf(e1)), fminf(fabsf(e2), fabsf(e3))));
-                    }
-                }
+            for (int s = 0; s < kRowsPer; ++s) {
+                uint64_t e01 = fadd2(cH.x, a[s][4]);
+                uint64_t e23 = fadd2(cH.y, a[s][4]);
+                e01 = ffma2(cT.x, a[s][0], e01);
+                e23 = ffma2(cT.y, a[s][0], e23);
+                e01 = ffma2(cX.x, a[s][1], e01);
+                e23 = ffma2(cX.y, a[s][1], e23);
+                e01 = ffma2(cY.x, a[s][2], e01);
+                e23 = ffma2(cY.y, a[s][2], e23);
+                e01 = ffma2(cZ.x, a[s][3], e01);
+                e23 = ffma2(cZ.y, a[s][3], e23);
+                float e0, e1, e2, e3, f0, f1, f2, f3;
+                unpack2(e01, e0, e1);
+                unpack2(e23, e2, e3);
+                unpack2(fadd2(e01, m2n), f0, f1);
+                unpack2(fadd2(e23, m2n), f2, f3);
+                acc[s] = push_sign(e0, push_sign(e1, push_sign(e2, push_sign(e3, acc[s]))));
+                bcc[s] = push_sign(f0, push_sign(f1, push_sign(f2, push_sign(f3, bcc[s]))));
             }
         }
 #pragma unroll
         for (int s = 0; s < kRowsPer; ++s) {
             A[s] |= (uint64_t)acc[s] << (32 * h);
-            if (D == 4 || TIES) B[s] |= (uint64_t)bcc[s] << (32 * h);
+            B[s] |= (uint64_t)bcc[s] << (32 * h);
         }
-    }
-    if (D == 2 && !TIES) {
-#pragma unroll
-        for (int s = 0; s < kRowsPer; ++s) B[s] = mn[s] == 0.f ? ~0ull : A[s];
     }
 }
 
@@ -314,7 +271,7 @@ __global__ void __launch_bounds__(kTile, kLinkMinBlocks)
 link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts, int n,
             const float *__restrict__ F) {
     constexpr int ND = D == 4 ? 4 : 2;             // double coordinates the exact test reads
-    __shared__ __align__(16) float cf[5][kTile];  // column screen values (negated for d=2)
+    __shared__ __align__(16) float cf[5][kTile];  // column screen values
     __shared__ double cd[ND][kTile];              // column coordinates in double
     __shared__ double rd[ND][kTile];              // row coordinates in double
     __shared__ uint64_t ow[kTileWords][kTile];    // row words: ow[q][r] = word q of tile row r
@@ -341,7 +298,6 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
     const int lane = r & 31, warp = r >> 5;
     const float *__restrict__ Fs = F + S.foff;
     const double *__restrict__ co = S.coords;
-    constexpr int base = D == 2 ? 2 : 0;           // first coordinate row the exact test reads
 
     // stage column K + r and row R + r (beyond N: zeros; no word reads them)
     {
@@ -349,12 +305,12 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
 #pragma unroll
         for (int a = 0; a < screen_floats(D); ++a) {
             const float x = kc < N ? Fs[a * N + kc] : 0.f;
-            cf[a][r] = D == 2 ? -x : x;
+            cf[a][r] = x;
         }
 #pragma unroll
         for (int a = 0; a < ND; ++a) {
-            cd[a][r] = kc < N ? co[(base + a) * N + kc] : 0.0;
-            rd[a][r] = i < N ? co[(base + a) * N + i] : 0.0;
+            cd[a][r] = kc < N ? co[a * N + kc] : 0.0;
+            rd[a][r] = i < N ? co[a * N + i] : 0.0;
         }
     }
     __syncthreads();
@@ -392,13 +348,10 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
     }
 
     uint64_t A[kRowsPer] = {0, 0, 0, 0}, B[kRowsPer] = {0, 0, 0, 0};
-    if constexpr (D != GEOM_DS2) {
+    if constexpr (D == 4) {
         if (any) {
             const float m2 = -(m + m);
-            if (D == 2 && diag)
-                word_packed<D, true>(q, cf, a, 0, A, B);
-            else
-                word_packed<D, false>(q, cf, a, pack2(m2, m2), A, B);
+            word_packed(q, cf, a, pack2(m2, m2), A, B);
         }
     }
 #pragma unroll
@@ -411,7 +364,7 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
             const int lo = diag ? max(rt + 1 - 64 * q, 0) : 0;
             const int hi = min(ncol - 64 * q, 64);
             const uint64_t mask = lo >= hi ? 0ull : ((hi == 64 ? ~0ull : (1ull << hi) - 1) & ~((1ull << lo) - 1));
-            if constexpr (D != GEOM_DS2) {
+            if constexpr (D == 4) {
                 // pairs the screen left open: decide them in double
                 wd = A[s] & mask;
                 uint64_t amb = B[s] & ~A[s] & mask;
@@ -465,6 +418,191 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
     }
 }
 
+
+// ------------------------------------------------------------------ d=2: dominance tiles
+//
+// In light-cone coordinates the d=2 relation is a product order: i < k iff u_i < u_k and
+// v_i < v_k.  For the rows of one row block sorted by u, the rows with u_i < u_k are the first
+// p_u(k) of them, p_u(k) = #{i : u_i < u_k}, found by a binary search of u_k in the sorted u;
+// so with Pu[p] (Pv[p]) the set of the first p rows in u (v) order, column k's row set is
+// Pu[p_u(k)] & Pv[p_v(k)].  A CTA sorts its row block once (bitonic networks in shared
+// memory, u and v side by side), lays each sorted order out as an implicit search tree
+// (breadth-first, so that the first levels of every search read a few shared words that the
+// lanes share), builds the 257 prefix sets of each order (a warp per 64-row word: per-lane
+// ORs, then a shuffle OR scan), and then runs kD2Chunk column blocks: one thread per column,
+// two tree searches and four ANDs give the column's 256 row bits (the mirrored half), and a
+// warp-shuffle transpose gives the row words; each thread writes its 32 bytes of a row with
+// one 32-byte store.  Coordinates are compared
+// as 64-bit integer keys that order exactly as the doubles do (-0 folded onto +0, negative
+// values' magnitude bits flipped), so every decision is the exact double one, on the integer
+// pipe rather than the few FP64 units; ties are no special case (equal values are not less),
+// and padding rows carry the largest key, which no finite coordinate reaches.  A pair i < k always has i earlier
+// in the time order (t is (u + v) / 2, its ties broken by u), so no mask is needed within
+// the diagonal block, whose row words and mirrored words are ORed.
+constexpr int kD2Chunk = 8;  // column blocks per CTA
+
+// sum_{n=1}^{M} ceil(n / kD2Chunk)
+__host__ __device__ __forceinline__ int64_t ceil_sum(int64_t M) {
+    const int64_t a = M / kD2Chunk, r = M % kD2Chunk;
+    return kD2Chunk * a * (a + 1) / 2 + r * (a + 1);
+}
+// CTAs before row block b: sum_{q<b} ceil((nbc - q) / kD2Chunk)
+__host__ __device__ __forceinline__ int64_t items_before(int64_t b, int64_t nbc) {
+    return ceil_sum(nbc) - ceil_sum(nbc - b);
+}
+
+// A 64-bit integer with the order of the double x: a < b as doubles iff key(a) < key(b)
+// (finite values; -0 and +0 get the same key).
+__device__ __forceinline__ long long order_key(double x) {
+    long long b = __double_as_longlong(x);
+    if (b == (long long)0x8000000000000000ull) b = 0;
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+constexpr long long kKeyPad = 0x7fffffffffffffffll;  // above every finite coordinate's key
+
+// In-order rank of node j (1..255) of the complete search tree of 255 keys whose node j has
+// children 2j and 2j + 1 (depth d = floor(log2 j)).
+__device__ __forceinline__ int tree_rank(int j) {
+    const int d = 31 - __clz(j);
+    return ((2 * (j - (1 << d)) + 1) << (7 - d)) - 1;
+}
+
+// #{q : sorted[q] < x} for 256 ascending keys held as the tree tree[1..255] of the first 255
+// and `last`: eight steps down the tree leave j - 256 = the count among the 255.
+__device__ __forceinline__ int count_below(const long long *tree, long long last, long long x) {
+    int j = 1;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) j = 2 * j + (tree[j] < x);
+    const int c = j - kTile;
+    return c + (c == kTile - 1 && last < x);
+}
+
+// 32 bytes to global memory in one store (dst 32-byte aligned)
+__device__ __forceinline__ void st_global_32B(uint64_t *dst, uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
+    asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(dst), "l"(a), "l"(b), "l"(c), "l"(d) : "memory");
+}
+
+__global__ void __launch_bounds__(kTile, 5)
+link_d2_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts, int n) {
+    __shared__ long long key[2][kTile];                 // row u (0) and v (1) keys, sorted
+    __shared__ long long tree[2][kTile];                // the first 255 as search trees (nodes 1..255)
+    __shared__ uint16_t idx[2][kTile];                  // tile rows in sorted order
+    __shared__ uint64_t pre[2][kTileWords][kTile + 1];  // pre[g][w][p]: word w of prefix set p
+    __shared__ uint32_t tb[kTile][9];                   // tb[r][g]: row r, columns 32g..32g+31
+
+    const LinkRow S = sets[find_set(starts, n, blockIdx.x)];
+    const int64_t t = blockIdx.x - S.tile_off;
+    int64_t lo = 0, hi = S.nb - 1;  // row block: largest b with items_before(b) <= t
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (items_before(mid, S.nbc) <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const int64_t bi = lo;
+    const int64_t bj0 = bi + (t - items_before(bi, S.nbc)) * kD2Chunk;
+    const int64_t bj1 = min(bj0 + kD2Chunk, S.nbc);
+    const int64_t R = bi * kTile, N = S.N, stride = S.stride;
+    const double *__restrict__ cu = S.coords + 2 * N;  // u, then v
+    const double *__restrict__ cv = S.coords + 3 * N;
+    const int r = threadIdx.x, lane = r & 31, warp = r >> 5;
+
+    {
+        const int64_t i = R + r;
+        key[0][r] = i < N ? order_key(cu[i]) : kKeyPad;
+        key[1][r] = i < N ? order_key(cv[i]) : kKeyPad;
+        idx[0][r] = idx[1][r] = (uint16_t)r;
+    }
+    // the first column block's coordinates, loaded while the rows sort
+    int64_t kc = bj0 * kTile + r;
+    long long xu = kc < N ? order_key(cu[kc]) : 0, xv = kc < N ? order_key(cv[kc]) : 0;
+    __syncthreads();
+    {
+        const int g = r >> 7, q = r & 127;  // threads 0-127 sort u, 128-255 sort v
+        for (int k = 2; k <= kTile; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const int a = 2 * q - (q & (j - 1)), b = a + j;
+                const long long ka = key[g][a], kb = key[g][b];
+                if ((ka > kb) == ((a & k) == 0)) {
+                    key[g][a] = kb;
+                    key[g][b] = ka;
+                    const uint16_t ia = idx[g][a];
+                    idx[g][a] = idx[g][b];
+                    idx[g][b] = ia;
+                }
+                __syncthreads();
+            }
+    }
+    {
+        // node j of each tree holds the key of in-order rank tree_rank(j)
+        const int g = r >> 7, j = r & 127;
+        if (j > 0) tree[g][j] = key[g][tree_rank(j)];
+        tree[g][j + 128] = key[g][tree_rank(j + 128)];
+    }
+    {
+        // warps 0-3: u order, 64-row word `warp`; warps 4-7: v order
+        const int g = warp >> 2, w = warp & 3;
+        uint64_t loc[8], x = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int rr = idx[g][8 * lane + j];
+            if ((rr >> 6) == w) x |= 1ull << (rr & 63);
+            loc[j] = x;
+        }
+        uint64_t inc = x;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc |= y;
+        }
+        uint64_t exc = __shfl_up_sync(0xffffffffu, inc, 1);
+        if (lane == 0) exc = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) pre[g][w][8 * lane + j + 1] = exc | loc[j];
+        if (lane == 0) pre[g][w][0] = 0;
+    }
+    __syncthreads();
+    const long long lastu = key[0][kTile - 1], lastv = key[1][kTile - 1];
+
+    uint64_t *rows = S.rows;
+    const int64_t i = R + r;
+    for (int64_t bj = bj0; bj < bj1; ++bj) {
+        const int64_t K = bj * kTile;
+        uint64_t cm[kTileWords] = {0, 0, 0, 0};  // column K + r: its rows i < (K + r)
+        const bool live = kc < N;
+        if (live) {
+            const int pu = count_below(tree[0], lastu, xu), pv = count_below(tree[1], lastv, xv);
+#pragma unroll
+            for (int w = 0; w < kTileWords; ++w) cm[w] = pre[0][w][pu] & pre[1][w][pv];
+        }
+        const int64_t kcur = kc;
+        kc += kTile;  // the next column block's coordinates, loaded during the transpose
+        if (bj + 1 < bj1) {
+            xu = kc < N ? order_key(cu[kc]) : 0;
+            xv = kc < N ? order_key(cv[kc]) : 0;
+        }
+        // lanes hold columns 32 warp + lane; after the transpose lane l holds row 32 c + l
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            tb[32 * c + lane][warp] = warp_transpose32((uint32_t)(cm[c >> 1] >> (32 * (c & 1))), lane);
+        __syncthreads();
+        uint64_t rw[kTileWords];
+#pragma unroll
+        for (int w = 0; w < kTileWords; ++w) rw[w] = (uint64_t)tb[r][2 * w] | ((uint64_t)tb[r][2 * w + 1] << 32);
+        if (bj == bi) {
+            if (i < N && CSG_IN_BOUNDS(K / 64 + kTileWords <= stride, 0x30, i))
+                st_global_32B(rows + i * stride + K / 64, rw[0] | cm[0], rw[1] | cm[1], rw[2] | cm[2], rw[3] | cm[3]);
+        } else {
+            if (i < N && CSG_IN_BOUNDS(K / 64 + kTileWords <= stride, 0x30, i))
+                st_global_32B(rows + i * stride + K / 64, rw[0], rw[1], rw[2], rw[3]);
+            if (live && CSG_IN_BOUNDS(R / 64 + kTileWords <= stride, 0x31, kcur))
+                st_global_32B(rows + kcur * stride + R / 64, cm[0], cm[1], cm[2], cm[3]);
+        }
+        __syncthreads();  // tb is rewritten by the next column block
+    }
+}
+
 }  // namespace
 
 unsigned long long check_word_link() { return take_check_word(); }
@@ -497,17 +635,22 @@ LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
                        : d == 4     ? 4e-6f * (float)(specs[s].coord_scale * specs[s].coord_scale)
                                     : 0.f;
             L.pad2 = 0.f;
-            if (L.stride % 16 != 0 || L.nbc < L.nb) {
-                set_error("link: stride %lld does not cover N=%lld", (long long)L.stride, (long long)L.N);
+            if (L.stride % 16 != 0 || L.nbc < L.nb || ((uintptr_t)L.rows & 31) != 0) {
+                set_error("link: stride %lld does not cover N=%lld, or the rows are not 32-byte aligned",
+                          (long long)L.stride, (long long)L.N);
                 *rc = CSG_E_INVAL;
                 return p;
             }
             starts.push_back(T);
             estarts.push_back(E);
             rows.push_back(L);
-            T += L.nb * L.nbc - L.nb * (L.nb - 1) / 2;
+            if (d == 2) {
+                T += items_before(L.nb, L.nbc);  // CTAs of kD2Chunk column blocks; no screen values
+            } else {
+                T += L.nb * L.nbc - L.nb * (L.nb - 1) / 2;
+                nf += (int64_t)screen_floats(d) * L.N;
+            }
             E += L.N;
-            nf += (int64_t)screen_floats(d) * L.N;
         }
         if (T > 0x7fffffffLL || (E + 255) / 256 > 0x7fffffffLL) {
             set_error("link: %lld tiles exceed one launch", (long long)T);
@@ -532,9 +675,13 @@ LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
 template <int D>
 static void link_part_launch(const LinkPlan::Part &P, const Arena &a, float *F, cudaStream_t st) {
     if (P.T == 0) return;
-    link_screen_kernel<D><<<(unsigned)((P.E + 255) / 256), 256, 0, st>>>(
-        a.tab<LinkRow>(P.t_rows), a.tab<int64_t>(P.t_estarts), P.n, P.E, F);
-    link_kernel<D><<<(unsigned)P.T, kTile, 0, st>>>(a.tab<LinkRow>(P.t_rows), a.tab<int64_t>(P.t_starts), P.n, F);
+    if constexpr (D == 2) {
+        link_d2_kernel<<<(unsigned)P.T, kTile, 0, st>>>(a.tab<LinkRow>(P.t_rows), a.tab<int64_t>(P.t_starts), P.n);
+    } else {
+        link_screen_kernel<D><<<(unsigned)((P.E + 255) / 256), 256, 0, st>>>(
+            a.tab<LinkRow>(P.t_rows), a.tab<int64_t>(P.t_estarts), P.n, P.E, F);
+        link_kernel<D><<<(unsigned)P.T, kTile, 0, st>>>(a.tab<LinkRow>(P.t_rows), a.tab<int64_t>(P.t_starts), P.n, F);
+    }
 }
 
 void link_launch(const LinkPlan &p, const Arena &a, cudaStream_t st) {
