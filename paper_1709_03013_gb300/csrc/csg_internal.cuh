@@ -108,11 +108,13 @@ struct LinkSpec {
 struct LinkPlan {
     struct Part {  // the sets of one geometry (part 0: d=2, 1: d=4, 2: 1+1 de Sitter)
         int n = 0;
-        int64_t T = 0, E = 0;  // tiles, elements
-        size_t t_rows = 0, t_starts = 0, t_estarts = 0;
+        int64_t T = 0, E = 0;  // CTAs of the link kernel, elements
+        int64_t RB = 0;        // d=2: row blocks, each sorted once by the pre-pass
+        size_t t_rows = 0, t_starts = 0, t_estarts = 0, t_rbstarts = 0;
     } part[3];
     int64_t T = 0;
     size_t s_screen = 0;  // scratch: per-element float screen values of every set
+    size_t s_sorted = 0;  // scratch: d=2 row blocks in u and v order
 };
 LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc);
 void link_launch(const LinkPlan &p, const Arena &a, cudaStream_t st);

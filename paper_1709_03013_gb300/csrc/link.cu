@@ -72,6 +72,7 @@ struct LinkRow {
     int64_t foff;     // first float of the set's screen values (screen_floats(d) rows of N)
     float margin;     // float-screen margin: d=4 4e-6 S^2 on e, de Sitter 1e-5
     float pad2;
+    int64_t rboff;    // d=2: the set's first row block in the sorted-block scratch
 };
 
 // float screen values per element: d=4 T, X, Y, Z, -H; de Sitter eta, theta
@@ -425,21 +426,30 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
 // v_i < v_k.  For the rows of one row block sorted by u, the rows with u_i < u_k are the first
 // p_u(k) of them, p_u(k) = #{i : u_i < u_k}, found by a binary search of u_k in the sorted u;
 // so with Pu[p] (Pv[p]) the set of the first p rows in u (v) order, column k's row set is
-// Pu[p_u(k)] & Pv[p_v(k)].  A CTA sorts its row block once (bitonic networks in shared
-// memory, u and v side by side), lays each sorted order out as an implicit search tree
-// (breadth-first, so that the first levels of every search read a few shared words that the
-// lanes share), builds the 257 prefix sets of each order (a warp per 64-row word: per-lane
+// Pu[p_u(k)] & Pv[p_v(k)].  A pre-pass sorts every row block once (a CTA per block: bitonic
+// networks in shared memory, u and v side by side) and stores each sorted order as an
+// implicit search tree (breadth-first, so that the first levels of every search read a few
+// shared words that the lanes share) with the rows in that order.  A link CTA loads its row
+// block's trees, builds the 257 prefix sets of each order (a warp per 64-row word: per-lane
 // ORs, then a shuffle OR scan), and then runs kD2Chunk column blocks: one thread per column,
 // two tree searches and four ANDs give the column's 256 row bits (the mirrored half), and a
 // warp-shuffle transpose gives the row words; each thread writes its 32 bytes of a row with
-// one 32-byte store.  Coordinates are compared
-// as 64-bit integer keys that order exactly as the doubles do (-0 folded onto +0, negative
-// values' magnitude bits flipped), so every decision is the exact double one, on the integer
-// pipe rather than the few FP64 units; ties are no special case (equal values are not less),
-// and padding rows carry the largest key, which no finite coordinate reaches.  A pair i < k always has i earlier
-// in the time order (t is (u + v) / 2, its ties broken by u), so no mask is needed within
-// the diagonal block, whose row words and mirrored words are ORed.
+// one 32-byte store.  Coordinates are compared as 64-bit integer keys that order exactly as
+// the doubles do (-0 folded onto +0, negative values' magnitude bits flipped), so every
+// decision is the exact double one, on the integer pipe rather than the few FP64 units; ties
+// are no special case (equal values are not less), and padding rows carry the largest key,
+// which no finite coordinate reaches.  A pair i < k always has i earlier in the time order
+// (t is (u + v) / 2, its ties broken by u), so no mask is needed within the diagonal block,
+// whose row words and mirrored words are ORed.
 constexpr int kD2Chunk = 8;  // column blocks per CTA
+
+// One row block in u (g = 0) and v (g = 1) order: tree[g][j], j = 1..255, the search tree
+// of the first 255 sorted keys (node j holds the key of in-order rank tree_rank(j)),
+// tree[g][0] the largest key; idx[g][q] the tile row of sorted position q.
+struct SortedBlock {
+    long long tree[2][kTile];
+    uint16_t idx[2][kTile];
+};
 
 // sum_{n=1}^{M} ceil(n / kD2Chunk)
 __host__ __device__ __forceinline__ int64_t ceil_sum(int64_t M) {
@@ -482,11 +492,53 @@ __device__ __forceinline__ void st_global_32B(uint64_t *dst, uint64_t a, uint64_
     asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(dst), "l"(a), "l"(b), "l"(c), "l"(d) : "memory");
 }
 
+// Pre-pass: one CTA per d=2 row block (numbered across the sets, rbstarts[s] = first row
+// block of set s) sorts the block's u and v keys with their rows and stores the result as
+// one SortedBlock.
+__global__ void __launch_bounds__(kTile)
+link_d2_sort_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ rbstarts, int n,
+                    SortedBlock *__restrict__ out) {
+    __shared__ long long key[2][kTile];
+    __shared__ uint16_t idx[2][kTile];
+    const int sidx = find_set(rbstarts, n, blockIdx.x);
+    const LinkRow &S = sets[sidx];
+    const int64_t R = (blockIdx.x - rbstarts[sidx]) * kTile, N = S.N;
+    const int r = threadIdx.x;
+    {
+        const int64_t i = R + r;
+        key[0][r] = i < N ? order_key(S.coords[2 * N + i]) : kKeyPad;  // u
+        key[1][r] = i < N ? order_key(S.coords[3 * N + i]) : kKeyPad;  // v
+        idx[0][r] = idx[1][r] = (uint16_t)r;
+    }
+    __syncthreads();
+    {
+        const int g = r >> 7, q = r & 127;  // threads 0-127 sort u, 128-255 sort v
+        for (int k = 2; k <= kTile; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const int a = 2 * q - (q & (j - 1)), b = a + j;
+                const long long ka = key[g][a], kb = key[g][b];
+                if ((ka > kb) == ((a & k) == 0)) {
+                    key[g][a] = kb;
+                    key[g][b] = ka;
+                    const uint16_t ia = idx[g][a];
+                    idx[g][a] = idx[g][b];
+                    idx[g][b] = ia;
+                }
+                __syncthreads();
+            }
+    }
+    SortedBlock &o = out[blockIdx.x];
+    const int g = r >> 7, j = r & 127;
+    o.tree[g][j] = j > 0 ? key[g][tree_rank(j)] : key[g][kTile - 1];
+    o.tree[g][j + 128] = key[g][tree_rank(j + 128)];
+    o.idx[0][r] = idx[0][r];
+    o.idx[1][r] = idx[1][r];
+}
+
 __global__ void __launch_bounds__(kTile, 5)
-link_d2_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts, int n) {
-    __shared__ long long key[2][kTile];                 // row u (0) and v (1) keys, sorted
-    __shared__ long long tree[2][kTile];                // the first 255 as search trees (nodes 1..255)
-    __shared__ uint16_t idx[2][kTile];                  // tile rows in sorted order
+link_d2_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts, int n,
+               const SortedBlock *__restrict__ sorted) {
+    __shared__ __align__(16) SortedBlock blk;           // the row block's trees and orders
     __shared__ uint64_t pre[2][kTileWords][kTile + 1];  // pre[g][w][p]: word w of prefix set p
     __shared__ uint32_t tb[kTile][9];                   // tb[r][g]: row r, columns 32g..32g+31
 
@@ -509,44 +561,22 @@ link_d2_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ sta
     const int r = threadIdx.x, lane = r & 31, warp = r >> 5;
 
     {
-        const int64_t i = R + r;
-        key[0][r] = i < N ? order_key(cu[i]) : kKeyPad;
-        key[1][r] = i < N ? order_key(cv[i]) : kKeyPad;
-        idx[0][r] = idx[1][r] = (uint16_t)r;
+        // the row block's SortedBlock, 16 bytes per thread and step
+        const uint4 *src = reinterpret_cast<const uint4 *>(sorted + S.rboff + bi);
+        uint4 *dst = reinterpret_cast<uint4 *>(&blk);
+        for (int q = r; q < (int)(sizeof(SortedBlock) / 16); q += kTile) dst[q] = src[q];
     }
-    // the first column block's coordinates, loaded while the rows sort
+    // the first column block's coordinates
     int64_t kc = bj0 * kTile + r;
     long long xu = kc < N ? order_key(cu[kc]) : 0, xv = kc < N ? order_key(cv[kc]) : 0;
     __syncthreads();
-    {
-        const int g = r >> 7, q = r & 127;  // threads 0-127 sort u, 128-255 sort v
-        for (int k = 2; k <= kTile; k <<= 1)
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                const int a = 2 * q - (q & (j - 1)), b = a + j;
-                const long long ka = key[g][a], kb = key[g][b];
-                if ((ka > kb) == ((a & k) == 0)) {
-                    key[g][a] = kb;
-                    key[g][b] = ka;
-                    const uint16_t ia = idx[g][a];
-                    idx[g][a] = idx[g][b];
-                    idx[g][b] = ia;
-                }
-                __syncthreads();
-            }
-    }
-    {
-        // node j of each tree holds the key of in-order rank tree_rank(j)
-        const int g = r >> 7, j = r & 127;
-        if (j > 0) tree[g][j] = key[g][tree_rank(j)];
-        tree[g][j + 128] = key[g][tree_rank(j + 128)];
-    }
     {
         // warps 0-3: u order, 64-row word `warp`; warps 4-7: v order
         const int g = warp >> 2, w = warp & 3;
         uint64_t loc[8], x = 0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const int rr = idx[g][8 * lane + j];
+            const int rr = blk.idx[g][8 * lane + j];
             if ((rr >> 6) == w) x |= 1ull << (rr & 63);
             loc[j] = x;
         }
@@ -563,7 +593,7 @@ link_d2_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ sta
         if (lane == 0) pre[g][w][0] = 0;
     }
     __syncthreads();
-    const long long lastu = key[0][kTile - 1], lastv = key[1][kTile - 1];
+    const long long lastu = blk.tree[0][0], lastv = blk.tree[1][0];
 
     uint64_t *rows = S.rows;
     const int64_t i = R + r;
@@ -572,7 +602,7 @@ link_d2_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ sta
         uint64_t cm[kTileWords] = {0, 0, 0, 0};  // column K + r: its rows i < (K + r)
         const bool live = kc < N;
         if (live) {
-            const int pu = count_below(tree[0], lastu, xu), pv = count_below(tree[1], lastv, xv);
+            const int pu = count_below(blk.tree[0], lastu, xu), pv = count_below(blk.tree[1], lastv, xv);
 #pragma unroll
             for (int w = 0; w < kTileWords; ++w) cm[w] = pre[0][w][pu] & pre[1][w][pv];
         }
@@ -615,8 +645,8 @@ LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
     for (int part = 0; part < 3; ++part) {
         const int d = part == 0 ? 2 : (part == 1 ? 4 : GEOM_DS2);
         std::vector<LinkRow> rows;
-        std::vector<int64_t> starts, estarts;
-        int64_t T = 0, E = 0;
+        std::vector<int64_t> starts, estarts, rbstarts;
+        int64_t T = 0, E = 0, RB = 0;
         for (int s = 0; s < n; ++s) {
             if (specs[s].d != d) continue;
             LinkRow L;
@@ -635,6 +665,7 @@ LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
                        : d == 4     ? 4e-6f * (float)(specs[s].coord_scale * specs[s].coord_scale)
                                     : 0.f;
             L.pad2 = 0.f;
+            L.rboff = RB;
             if (L.stride % 16 != 0 || L.nbc < L.nb || ((uintptr_t)L.rows & 31) != 0) {
                 set_error("link: stride %lld does not cover N=%lld, or the rows are not 32-byte aligned",
                           (long long)L.stride, (long long)L.N);
@@ -646,13 +677,15 @@ LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
             rows.push_back(L);
             if (d == 2) {
                 T += items_before(L.nb, L.nbc);  // CTAs of kD2Chunk column blocks; no screen values
+                rbstarts.push_back(RB);
+                RB += L.nb;                      // row blocks the pre-pass sorts
             } else {
                 T += L.nb * L.nbc - L.nb * (L.nb - 1) / 2;
                 nf += (int64_t)screen_floats(d) * L.N;
             }
             E += L.N;
         }
-        if (T > 0x7fffffffLL || (E + 255) / 256 > 0x7fffffffLL) {
+        if (T > 0x7fffffffLL || (E + 255) / 256 > 0x7fffffffLL || RB > 0x7fffffffLL) {
             set_error("link: %lld tiles exceed one launch", (long long)T);
             *rc = CSG_E_INVAL;
             return p;
@@ -661,22 +694,29 @@ LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
         P.n = (int)rows.size();
         P.T = T;
         P.E = E;
+        P.RB = RB;
         if (P.n) {
             P.t_rows = a.put(rows.data(), rows.size() * sizeof(LinkRow));
             P.t_starts = a.put(starts.data(), starts.size() * sizeof(int64_t));
             P.t_estarts = a.put(estarts.data(), estarts.size() * sizeof(int64_t));
+            if (!rbstarts.empty()) P.t_rbstarts = a.put(rbstarts.data(), rbstarts.size() * sizeof(int64_t));
         }
         p.T += T;
     }
     p.s_screen = a.reserve((size_t)nf * sizeof(float));
+    p.s_sorted = a.reserve((size_t)p.part[0].RB * sizeof(SortedBlock));
     return p;
 }
 
 template <int D>
-static void link_part_launch(const LinkPlan::Part &P, const Arena &a, float *F, cudaStream_t st) {
+static void link_part_launch(const LinkPlan::Part &P, const Arena &a, float *F, SortedBlock *sorted,
+                             cudaStream_t st) {
     if (P.T == 0) return;
     if constexpr (D == 2) {
-        link_d2_kernel<<<(unsigned)P.T, kTile, 0, st>>>(a.tab<LinkRow>(P.t_rows), a.tab<int64_t>(P.t_starts), P.n);
+        link_d2_sort_kernel<<<(unsigned)P.RB, kTile, 0, st>>>(a.tab<LinkRow>(P.t_rows), a.tab<int64_t>(P.t_rbstarts),
+                                                              P.n, sorted);
+        link_d2_kernel<<<(unsigned)P.T, kTile, 0, st>>>(a.tab<LinkRow>(P.t_rows), a.tab<int64_t>(P.t_starts), P.n,
+                                                        sorted);
     } else {
         link_screen_kernel<D><<<(unsigned)((P.E + 255) / 256), 256, 0, st>>>(
             a.tab<LinkRow>(P.t_rows), a.tab<int64_t>(P.t_estarts), P.n, P.E, F);
@@ -688,9 +728,10 @@ void link_launch(const LinkPlan &p, const Arena &a, cudaStream_t st) {
     if (p.T == 0) return;
     stage_begin(CSG_STAGE_LINK, st);
     float *F = a.scr<float>(p.s_screen);
-    link_part_launch<2>(p.part[0], a, F, st);
-    link_part_launch<4>(p.part[1], a, F, st);
-    link_part_launch<GEOM_DS2>(p.part[2], a, F, st);
+    SortedBlock *sorted = a.scr<SortedBlock>(p.s_sorted);
+    link_part_launch<2>(p.part[0], a, F, sorted, st);
+    link_part_launch<4>(p.part[1], a, F, sorted, st);
+    link_part_launch<GEOM_DS2>(p.part[2], a, F, sorted, st);
     stage_end(CSG_STAGE_LINK, st);
 }
 
