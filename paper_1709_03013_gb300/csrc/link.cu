@@ -441,7 +441,7 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
 // which no finite coordinate reaches.  A pair i < k always has i earlier in the time order
 // (t is (u + v) / 2, its ties broken by u), so no mask is needed within the diagonal block,
 // whose row words and mirrored words are ORed.
-constexpr int kD2Chunk = 8;  // column blocks per CTA
+constexpr int kD2Chunk = 16;  // column blocks per CTA
 
 // One row block in u (g = 0) and v (g = 1) order: tree[g][j], j = 1..255, the search tree
 // of the first 255 sorted keys (node j holds the key of in-order rank tree_rank(j)),
@@ -540,7 +540,7 @@ link_d2_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ sta
                const SortedBlock *__restrict__ sorted) {
     __shared__ __align__(16) SortedBlock blk;           // the row block's trees and orders
     __shared__ uint64_t pre[2][kTileWords][kTile + 1];  // pre[g][w][p]: word w of prefix set p
-    __shared__ uint32_t tb[kTile][9];                   // tb[r][g]: row r, columns 32g..32g+31
+    __shared__ uint32_t tb[2][kTile][9];                // tb[b][r][g]: row r, columns 32g..32g+31 (two buffers)
 
     const LinkRow S = sets[find_set(starts, n, blockIdx.x)];
     const int64_t t = blockIdx.x - S.tile_off;
@@ -597,6 +597,7 @@ link_d2_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ sta
 
     uint64_t *rows = S.rows;
     const int64_t i = R + r;
+    int buf = 0;
     for (int64_t bj = bj0; bj < bj1; ++bj) {
         const int64_t K = bj * kTile;
         uint64_t cm[kTileWords] = {0, 0, 0, 0};  // column K + r: its rows i < (K + r)
@@ -615,11 +616,12 @@ link_d2_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ sta
         // lanes hold columns 32 warp + lane; after the transpose lane l holds row 32 c + l
 #pragma unroll
         for (int c = 0; c < 8; ++c)
-            tb[32 * c + lane][warp] = warp_transpose32((uint32_t)(cm[c >> 1] >> (32 * (c & 1))), lane);
+            tb[buf][32 * c + lane][warp] = warp_transpose32((uint32_t)(cm[c >> 1] >> (32 * (c & 1))), lane);
         __syncthreads();
         uint64_t rw[kTileWords];
 #pragma unroll
-        for (int w = 0; w < kTileWords; ++w) rw[w] = (uint64_t)tb[r][2 * w] | ((uint64_t)tb[r][2 * w + 1] << 32);
+        for (int w = 0; w < kTileWords; ++w)
+            rw[w] = (uint64_t)tb[buf][r][2 * w] | ((uint64_t)tb[buf][r][2 * w + 1] << 32);
         if (bj == bi) {
             if (i < N && CSG_IN_BOUNDS(K / 64 + kTileWords <= stride, 0x30, i))
                 st_global_32B(rows + i * stride + K / 64, rw[0] | cm[0], rw[1] | cm[1], rw[2] | cm[2], rw[3] | cm[3]);
@@ -629,7 +631,9 @@ link_d2_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ sta
             if (live && CSG_IN_BOUNDS(R / 64 + kTileWords <= stride, 0x31, kcur))
                 st_global_32B(rows + kcur * stride + R / 64, cm[0], cm[1], cm[2], cm[3]);
         }
-        __syncthreads();  // tb is rewritten by the next column block
+        // No second barrier: the next block writes the other buffer, and this one is written
+        // again only after the next block's barrier, which every thread reaches after its reads.
+        buf ^= 1;
     }
 }
 
