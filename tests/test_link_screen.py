@@ -11,10 +11,11 @@ These tests replay that arithmetic operation by operation in numpy float32 (a fu
 multiply-add as the exact double product plus the addend, rounded to float) and check, on
 sprinkles, boxes and light-cone stress sets at scales 1 to 1e15, that no certain bit
 contradicts the double predicate (the oracle's link), that the error stays inside the bound,
-and that the pairs left to double are few.  The d=2 screen (float light-cone coordinates,
-ties to double) and the de Sitter slab's screen (arc against |d eta|, margin 1e-5) are
-checked the same way.  No GPU is involved: the kernel itself is compared
-with the oracle bit for bit by the GPU tests.
+and that the pairs left to double are few.  The de Sitter slab's screen (arc against
+|d eta|, margin 1e-5) is checked the same way, and the d=2 link, which has no float screen
+(integer keys that order as the doubles do, sorted per row block, searched as trees, with
+prefix row sets), is replayed step by step against the oracle's link.  No GPU is involved:
+the kernel itself is compared with the oracle bit for bit by the GPU tests.
 """
 import numpy as np
 import pytest
@@ -90,23 +91,80 @@ def test_d4_screen_never_contradicts_double_predicate(name, make):
     assert (b & ~a).sum() <= max(8, 0.01 * r.size)   # few pairs go to double
 
 
+def _order_key(x):
+    # the 64-bit integer with the order of the doubles: -0 folded onto +0, negative values'
+    # magnitude bits flipped
+    b = np.ascontiguousarray(x, dtype=np.float64).view(np.int64).copy()
+    b[b == np.iinfo(np.int64).min] = 0
+    return b ^ ((b >> 63) & np.int64(0x7FFFFFFFFFFFFFFF))
+
+
+def _tree_rank(j):
+    d = int(j).bit_length() - 1
+    return ((2 * (j - (1 << d)) + 1) << (7 - d)) - 1
+
+
+def _dominance_bitmap(c, rng):
+    """The d=2 link as the dominance tiles compute it: per 256-row block, the rows sorted by
+    the u and v keys (ties in any order), each order's first 255 keys as a breadth-first
+    search tree plus the largest key, the prefix row sets, and for every column k of the
+    block's tiles (k >= the block's first row) the row set Pu[#u below] & Pv[#v below];
+    the same bits are stored for row i (future) and, mirrored, for row k (past)."""
+    N = c.shape[1]
+    ku, kv = _order_key(c[2]), _order_key(c[3])
+    pad = np.iinfo(np.int64).max
+    C = np.zeros((N, N), dtype=bool)
+    for R in range(0, N, 256):
+        cols = np.arange(R, N)
+        masks = []
+        for key in (ku, kv):
+            rk = np.full(256, pad, dtype=np.int64)
+            rk[:min(256, N - R)] = key[R:R + 256]
+            order = np.lexsort((rng.random(256), rk))        # ascending, ties in random order
+            srt = rk[order]
+            tree = np.zeros(256, dtype=np.int64)
+            for j in range(1, 256):
+                tree[j] = srt[_tree_rank(j)]
+            x = key[cols]
+            j = np.ones(cols.size, dtype=np.int64)
+            for _ in range(8):
+                j = 2 * j + (tree[j] < x)
+            cnt = j - 256
+            cnt = cnt + ((cnt == 255) & (srt[255] < x))
+            pre = np.zeros((257, 256), dtype=bool)            # pre[p]: the first p rows in order
+            for p in range(1, 257):
+                pre[p] = pre[p - 1]
+                pre[p, order[p - 1]] = True
+            masks.append(pre[cnt])
+        m = masks[0] & masks[1]                               # (column, row of the block)
+        rows = np.arange(R, min(R + 256, N))
+        sub = m[:, :rows.size].T                              # (row, column)
+        C[np.ix_(rows, cols)] |= sub
+        C[np.ix_(cols, rows)] |= sub.T
+    return C
+
+
 @pytest.mark.parametrize("scale", [1.0, 1e3, 1e15])
-def test_d2_screen_order_and_ties(scale):
-    # d=2: related iff u_i < u_k and v_i < v_k in double.  In float, e = max(U_i - U_k,
-    # V_i - V_k) < 0 must mean related and e > 0 unrelated; e == 0 goes to double.
+def test_d2_dominance_tiles_match_double_predicate(scale):
+    # d=2: related iff u_i < u_k and v_i < v_k in double.  The link kernel compares integer
+    # keys that order as the doubles do; on light-cone stress sets (steps in u or v only,
+    # one-ulp nudges, duplicates, signed zeros) its arithmetic must give the oracle's bitmap.
     N = 1500
     c = oracle.sort(2, inputs.light_cone_coords(2, N, 4, scale=scale))[0]
     rel = oracle.link(2, c).astype(bool)
-    Uf, Vf = c[2].astype(f32), c[3].astype(f32)
-    Uf = np.where(Uf == 0, f32(0), Uf)   # -0 folded onto +0
-    Vf = np.where(Vf == 0, f32(0), Vf)
-    i, k = np.triu_indices(N, 1)
-    e = np.maximum((Uf[i] - Uf[k]).astype(f32), (Vf[i] - Vf[k]).astype(f32))
-    r = rel[i, k]
-    assert not ((e < 0) & ~r).any()
-    assert not ((e > 0) & r).any()
-    assert not np.signbit(e[e == 0]).any()   # ties are +0, not -0
-    assert (e == 0).any()                    # the stress set does hold float ties
+    got = _dominance_bitmap(c, np.random.default_rng(7))
+    assert np.array_equal(got, rel | rel.T)
+    assert (np.diff(np.sort(c[2])) == 0).any() or (c[2] == 0).any()  # the set holds ties or zeros
+
+
+def test_order_key_orders_as_doubles():
+    x = np.array([-np.inf, -1e300, -2.0, -1.0, -5e-324, -0.0, 0.0, 5e-324, 1e-300, 0.5, 1.0, 2.0, 1e15, np.inf])
+    k = _order_key(x)
+    assert (np.diff(k[:5]) > 0).all() and k[5] == k[6] and (np.diff(k[6:]) > 0).all()
+    rng = np.random.default_rng(3)
+    y = np.concatenate([rng.normal(size=4000) * 10.0 ** rng.integers(-300, 300, 4000), [0.0, -0.0]])
+    a, b = rng.choice(y, 20000), rng.choice(y, 20000)
+    assert np.array_equal(a < b, _order_key(a) < _order_key(b))
 
 
 @pytest.mark.parametrize("eta0,seed", [(0.5, 1), (1.2, 2), (1.5, 3)])
