@@ -152,6 +152,25 @@ def test_link_on_and_near_light_cones(ctx, d, scale):
     s.free()
 
 
+@pytest.mark.parametrize("N", [2305, 300])
+def test_d2_link_on_few_distinct_values(ctx, N):
+    """The d=2 link sorts each row block by u and v and searches column keys: u and v drawn
+    from eleven values (signed zeros, the smallest subnormals, negatives, 1e15) give ties
+    between rows, between columns and across blocks, and a ragged last block."""
+    rng = np.random.default_rng(123)
+    vals = np.array([-1e15, -2.0, -5e-324, -0.0, 0.0, 5e-324, 1e-300, 0.25, 0.5, 3.0, 1e15])
+    u, v = rng.choice(vals, N), rng.choice(vals, N)
+    c = np.stack([(u + v) / 2, (v - u) / 2, u, v])
+    s = ctx.set_from_coords(2, c)
+    sorted_c, _ = oracle.sort(2, c)
+    assert np.array_equal(s.coords(), sorted_c)
+    s.link()
+    rel = oracle.link(2, sorted_c)
+    assert np.array_equal(s.bitmap(), oracle.pack(rel, s.info()["stride"]))
+    _check_result(s.action(), oracle.action(rel), 2, N)
+    s.free()
+
+
 @pytest.mark.parametrize("method", [0, 1])
 @pytest.mark.parametrize("d,N", [(2, 3000), (4, 4100)])
 def test_action_rows(ctx, d, N, method):
