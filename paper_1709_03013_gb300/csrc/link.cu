@@ -59,6 +59,8 @@ constexpr int kTile = 256;      // rows and columns per tile
 constexpr int kTileWords = 4;   // 64-bit words per tile row
 constexpr int kRowsPer = 4;     // rows per thread (one 64-column word each)
 constexpr int kLinkMinBlocks = 4;  // resident CTAs per SM the register budget allows
+constexpr int kTileChunk = 4;      // column blocks per CTA of the tile kernel (d=4, de Sitter)
+constexpr int kD2Chunk = 16;       // column blocks per CTA of the d=2 kernel
 
 struct LinkRow {
     int32_t d;  // 2, 4 or GEOM_DS2
@@ -90,9 +92,38 @@ __device__ __forceinline__ int find_set(const int64_t *__restrict__ starts, int 
     return lo;
 }
 
-// tiles before row block b: sum_{q<b} (nbc - q)
-__device__ __forceinline__ int64_t tiles_before(int64_t b, int64_t nbc) {
-    return b * nbc - b * (b - 1) / 2;
+// A CTA takes up to C consecutive column blocks bj of one row block bi (bi <= bj < nbc).
+// sum_{n=1}^{M} ceil(n / C) = C a (a + 1) / 2 + r (a + 1) with M = a C + r.
+template <int C>
+__host__ __device__ __forceinline__ int64_t ceil_sum(int64_t M) {
+    const int64_t a = M / C, r = M % C;
+    return C * a * (a + 1) / 2 + r * (a + 1);
+}
+// CTAs before row block b: sum_{q<b} ceil((nbc - q) / C)
+template <int C>
+__host__ __device__ __forceinline__ int64_t items_before(int64_t b, int64_t nbc) {
+    return ceil_sum<C>(nbc) - ceil_sum<C>(nbc - b);
+}
+// The row block bi and column blocks [bj0, bj1) of the set's CTA t.
+template <int C>
+__device__ __forceinline__ void item_blocks(int64_t t, int64_t nb, int64_t nbc, int64_t &bi, int64_t &bj0,
+                                            int64_t &bj1) {
+    int64_t lo = 0, hi = nb - 1;  // largest b with items_before(b) <= t
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (items_before<C>(mid, nbc) <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    bi = lo;
+    bj0 = bi + (t - items_before<C>(bi, nbc)) * C;
+    bj1 = bj0 + C < nbc ? bj0 + C : nbc;
+}
+
+// 32 bytes to global memory in one store (dst 32-byte aligned)
+__device__ __forceinline__ void st_global_32B(uint64_t *dst, uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
+    asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(dst), "l"(a), "l"(b), "l"(c), "l"(d) : "memory");
 }
 
 // packed pairs of floats (f32x2): low half = first column, high half = second
@@ -278,51 +309,27 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
     __shared__ uint64_t ow[kTileWords][kTile];    // row words: ow[q][r] = word q of tile row r
     __shared__ uint32_t tb[kTile][9];             // mirrored bits: tb[c][g] = rows 32g..32g+31 of column c
 
-    const int s_idx = find_set(starts, n, blockIdx.x);
-    const LinkRow S = sets[s_idx];
-    const int64_t t = blockIdx.x - S.tile_off;
-    // row block: largest b with tiles_before(b) <= t
-    int64_t lo = 0, hi = S.nb - 1;
-    while (lo < hi) {
-        int64_t mid = (lo + hi + 1) >> 1;
-        if (tiles_before(mid, S.nbc) <= t)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    const int64_t bi = lo;
-    const int64_t bj = bi + (t - tiles_before(bi, S.nbc));
-    const int64_t R = bi * kTile, K = bj * kTile;
+    const LinkRow S = sets[find_set(starts, n, blockIdx.x)];
+    int64_t bi, bj0, bj1;
+    item_blocks<kTileChunk>(blockIdx.x - S.tile_off, S.nb, S.nbc, bi, bj0, bj1);
+    const int64_t R = bi * kTile;
     const int64_t N = S.N;
-    const bool diag = (bi == bj);
     const int r = threadIdx.x;
     const int lane = r & 31, warp = r >> 5;
     const float *__restrict__ Fs = F + S.foff;
     const double *__restrict__ co = S.coords;
-
-    // stage column K + r and row R + r (beyond N: zeros; no word reads them)
-    {
-        const int64_t kc = K + r, i = R + r;
-#pragma unroll
-        for (int a = 0; a < screen_floats(D); ++a) {
-            const float x = kc < N ? Fs[a * N + kc] : 0.f;
-            cf[a][r] = x;
-        }
-#pragma unroll
-        for (int a = 0; a < ND; ++a) {
-            cd[a][r] = kc < N ? co[a * N + kc] : 0.0;
-            rd[a][r] = i < N ? co[a * N + i] : 0.0;
-        }
-    }
-    __syncthreads();
-
-    const int ncol = N - K <= 0 ? 0 : (N - K >= kTile ? kTile : (int)(N - K));
     const int q = warp >> 1;                       // this warp's 64-column word
     const int rfirst = 32 * (warp & 1);            // tile rows rfirst + 64 s + lane
     const float m = S.margin;
 
-    // the rows' screen values, each duplicated into a packed pair; d=4 rows carry the
-    // signs of the space products and the margin: T, -X, -Y, -Z, fl(-H + m)
+    // the row block: row R + r in double (beyond N: zeros; no word reads them), and the
+    // rows' screen values, each duplicated into a packed pair; d=4 rows carry the signs of
+    // the space products and the margin: T, -X, -Y, -Z, fl(-H + m)
+    {
+        const int64_t i = R + r;
+#pragma unroll
+        for (int a = 0; a < ND; ++a) rd[a][r] = i < N ? co[a * N + i] : 0.0;
+    }
     uint64_t a[kRowsPer][5];
 #pragma unroll
     for (int s = 0; s < kRowsPer; ++s) {
@@ -337,85 +344,92 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
         }
     }
 
-    // Rows of this slot with any column of the word after them and before N (the same for
-    // all lanes of the warp: slots start at multiples of 32, words at multiples of 64).
-    bool any = false;
-    bool live[kRowsPer];
-#pragma unroll
-    for (int s = 0; s < kRowsPer; ++s) {
-        const int rlo = rfirst + 64 * s;
-        live[s] = 64 * q < ncol && !(diag && rlo >= 64 * q + 64);
-        any |= live[s];
-    }
-
-    uint64_t A[kRowsPer] = {0, 0, 0, 0}, B[kRowsPer] = {0, 0, 0, 0};
-    if constexpr (D == 4) {
-        if (any) {
-            const float m2 = -(m + m);
-            word_packed(q, cf, a, pack2(m2, m2), A, B);
-        }
-    }
-#pragma unroll
-    for (int s = 0; s < kRowsPer; ++s) {
-        const int rt = rfirst + 64 * s + lane;     // tile row
-        const int64_t i = R + rt;
-        uint64_t wd = 0;
-        if (i < N && live[s]) {
-            // the word's columns after the row (diagonal tile) and before N
-            const int lo = diag ? max(rt + 1 - 64 * q, 0) : 0;
-            const int hi = min(ncol - 64 * q, 64);
-            const uint64_t mask = lo >= hi ? 0ull : ((hi == 64 ? ~0ull : (1ull << hi) - 1) & ~((1ull << lo) - 1));
-            if constexpr (D == 4) {
-                // pairs the screen left open: decide them in double
-                wd = A[s] & mask;
-                uint64_t amb = B[s] & ~A[s] & mask;
-                while (amb) {
-                    const int b = __ffsll((long long)amb) - 1;
-                    amb &= amb - 1;
-                    if (exact_pair<D>(rd, cd, rt, 64 * q + b))
-                        wd |= 1ull << b;
-                    else
-                        wd &= ~(1ull << b);
-                }
-            } else {
-                wd = word_by_pair_ds(q, lo + 64 * q, ncol, cf, rd, cd, rt, Fs, N, i, m);
-            }
-        }
-        ow[q][rt] = wd;
-        // mirrored half: columns 64 q + 32 h + lane get the bits of rows 32 g .. 32 g + 31
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-            tb[64 * q + 32 * h + lane][(warp & 1) + 2 * s] = warp_transpose32((uint32_t)(wd >> (32 * h)), lane);
-    }
-    __syncthreads();
-
     uint64_t *rows = S.rows;
     const int64_t stride = S.stride;
-    const int64_t i = R + r;
-    const int64_t kc = K + r;
-    if (diag) {
-        // both halves land in the same words: OR them
-        if (i < N && CSG_IN_BOUNDS(K / 64 + kTileWords <= stride, 0x30, i)) {
-            uint64_t *dst = rows + i * stride + K / 64;
+    for (int64_t bj = bj0; bj < bj1; ++bj) {
+        const int64_t K = bj * kTile;
+        const bool diag = (bi == bj);
+        // stage column K + r (beyond N: zeros; no word reads them)
+        {
+            const int64_t kc = K + r;
 #pragma unroll
-            for (int w = 0; w < kTileWords; ++w)
-                dst[w] = ow[w][r] | (uint64_t)tb[r][2 * w] | ((uint64_t)tb[r][2 * w + 1] << 32);
-        }
-    } else {
-        if (i < N && CSG_IN_BOUNDS(K / 64 + kTileWords <= stride, 0x30, i)) {
-            uint64_t *dst = rows + i * stride + K / 64;
-            reinterpret_cast<ulonglong2 *>(dst)[0] = make_ulonglong2(ow[0][r], ow[1][r]);
-            reinterpret_cast<ulonglong2 *>(dst)[1] = make_ulonglong2(ow[2][r], ow[3][r]);
-        }
-        if (kc < N && CSG_IN_BOUNDS(R / 64 + kTileWords <= stride, 0x31, kc)) {
-            uint64_t mw[kTileWords];
+            for (int a = 0; a < screen_floats(D); ++a) cf[a][r] = kc < N ? Fs[a * N + kc] : 0.f;
 #pragma unroll
-            for (int w = 0; w < kTileWords; ++w)
-                mw[w] = (uint64_t)tb[r][2 * w] | ((uint64_t)tb[r][2 * w + 1] << 32);
-            uint64_t *dst = rows + kc * stride + R / 64;
-            reinterpret_cast<ulonglong2 *>(dst)[0] = make_ulonglong2(mw[0], mw[1]);
-            reinterpret_cast<ulonglong2 *>(dst)[1] = make_ulonglong2(mw[2], mw[3]);
+            for (int a = 0; a < ND; ++a) cd[a][r] = kc < N ? co[a * N + kc] : 0.0;
         }
+        __syncthreads();
+
+        const int ncol = N - K <= 0 ? 0 : (N - K >= kTile ? kTile : (int)(N - K));
+        // Rows of this slot with any column of the word after them and before N (the same
+        // for all lanes of the warp: slots start at multiples of 32, words at multiples of 64).
+        bool any = false;
+        bool live[kRowsPer];
+#pragma unroll
+        for (int s = 0; s < kRowsPer; ++s) {
+            const int rlo = rfirst + 64 * s;
+            live[s] = 64 * q < ncol && !(diag && rlo >= 64 * q + 64);
+            any |= live[s];
+        }
+
+        uint64_t A[kRowsPer] = {0, 0, 0, 0}, B[kRowsPer] = {0, 0, 0, 0};
+        if constexpr (D == 4) {
+            if (any) {
+                const float m2 = -(m + m);
+                word_packed(q, cf, a, pack2(m2, m2), A, B);
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < kRowsPer; ++s) {
+            const int rt = rfirst + 64 * s + lane;     // tile row
+            const int64_t i = R + rt;
+            uint64_t wd = 0;
+            if (i < N && live[s]) {
+                // the word's columns after the row (diagonal tile) and before N
+                const int lo = diag ? max(rt + 1 - 64 * q, 0) : 0;
+                const int hi = min(ncol - 64 * q, 64);
+                const uint64_t mask =
+                    lo >= hi ? 0ull : ((hi == 64 ? ~0ull : (1ull << hi) - 1) & ~((1ull << lo) - 1));
+                if constexpr (D == 4) {
+                    // pairs the screen left open: decide them in double
+                    wd = A[s] & mask;
+                    uint64_t amb = B[s] & ~A[s] & mask;
+                    while (amb) {
+                        const int b = __ffsll((long long)amb) - 1;
+                        amb &= amb - 1;
+                        if (exact_pair<D>(rd, cd, rt, 64 * q + b))
+                            wd |= 1ull << b;
+                        else
+                            wd &= ~(1ull << b);
+                    }
+                } else {
+                    wd = word_by_pair_ds(q, lo + 64 * q, ncol, cf, rd, cd, rt, Fs, N, i, m);
+                }
+            }
+            ow[q][rt] = wd;
+            // mirrored half: columns 64 q + 32 h + lane get the bits of rows 32 g .. 32 g + 31
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                tb[64 * q + 32 * h + lane][(warp & 1) + 2 * s] = warp_transpose32((uint32_t)(wd >> (32 * h)), lane);
+        }
+        __syncthreads();
+
+        const int64_t i = R + r;
+        const int64_t kc = K + r;
+        uint64_t mw[kTileWords];
+#pragma unroll
+        for (int w = 0; w < kTileWords; ++w) mw[w] = (uint64_t)tb[r][2 * w] | ((uint64_t)tb[r][2 * w + 1] << 32);
+        if (diag) {
+            // both halves land in the same words: OR them
+            if (i < N && CSG_IN_BOUNDS(K / 64 + kTileWords <= stride, 0x30, i))
+                st_global_32B(rows + i * stride + K / 64, ow[0][r] | mw[0], ow[1][r] | mw[1], ow[2][r] | mw[2],
+                              ow[3][r] | mw[3]);
+        } else {
+            if (i < N && CSG_IN_BOUNDS(K / 64 + kTileWords <= stride, 0x30, i))
+                st_global_32B(rows + i * stride + K / 64, ow[0][r], ow[1][r], ow[2][r], ow[3][r]);
+            if (kc < N && CSG_IN_BOUNDS(R / 64 + kTileWords <= stride, 0x31, kc))
+                st_global_32B(rows + kc * stride + R / 64, mw[0], mw[1], mw[2], mw[3]);
+        }
+        __syncthreads();  // cf, cd, ow and tb are rewritten by the next column block
     }
 }
 
@@ -441,8 +455,6 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
 // which no finite coordinate reaches.  A pair i < k always has i earlier in the time order
 // (t is (u + v) / 2, its ties broken by u), so no mask is needed within the diagonal block,
 // whose row words and mirrored words are ORed.
-constexpr int kD2Chunk = 16;  // column blocks per CTA
-
 // One row block in u (g = 0) and v (g = 1) order: tree[g][j], j = 1..255, the search tree
 // of the first 255 sorted keys (node j holds the key of in-order rank tree_rank(j)),
 // tree[g][0] the largest key; idx[g][q] the tile row of sorted position q.
@@ -450,16 +462,6 @@ struct SortedBlock {
     long long tree[2][kTile];
     uint16_t idx[2][kTile];
 };
-
-// sum_{n=1}^{M} ceil(n / kD2Chunk)
-__host__ __device__ __forceinline__ int64_t ceil_sum(int64_t M) {
-    const int64_t a = M / kD2Chunk, r = M % kD2Chunk;
-    return kD2Chunk * a * (a + 1) / 2 + r * (a + 1);
-}
-// CTAs before row block b: sum_{q<b} ceil((nbc - q) / kD2Chunk)
-__host__ __device__ __forceinline__ int64_t items_before(int64_t b, int64_t nbc) {
-    return ceil_sum(nbc) - ceil_sum(nbc - b);
-}
 
 // A 64-bit integer with the order of the double x: a < b as doubles iff key(a) < key(b)
 // (finite values; -0 and +0 get the same key).
@@ -485,11 +487,6 @@ __device__ __forceinline__ int count_below(const long long *tree, long long last
     for (int l = 0; l < 8; ++l) j = 2 * j + (tree[j] < x);
     const int c = j - kTile;
     return c + (c == kTile - 1 && last < x);
-}
-
-// 32 bytes to global memory in one store (dst 32-byte aligned)
-__device__ __forceinline__ void st_global_32B(uint64_t *dst, uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
-    asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(dst), "l"(a), "l"(b), "l"(c), "l"(d) : "memory");
 }
 
 // Pre-pass: one CTA per d=2 row block (numbered across the sets, rbstarts[s] = first row
@@ -543,18 +540,8 @@ link_d2_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ sta
     __shared__ uint32_t tb[2][kTile][9];                // tb[b][r][g]: row r, columns 32g..32g+31 (two buffers)
 
     const LinkRow S = sets[find_set(starts, n, blockIdx.x)];
-    const int64_t t = blockIdx.x - S.tile_off;
-    int64_t lo = 0, hi = S.nb - 1;  // row block: largest b with items_before(b) <= t
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (items_before(mid, S.nbc) <= t)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    const int64_t bi = lo;
-    const int64_t bj0 = bi + (t - items_before(bi, S.nbc)) * kD2Chunk;
-    const int64_t bj1 = min(bj0 + kD2Chunk, S.nbc);
+    int64_t bi, bj0, bj1;
+    item_blocks<kD2Chunk>(blockIdx.x - S.tile_off, S.nb, S.nbc, bi, bj0, bj1);
     const int64_t R = bi * kTile, N = S.N, stride = S.stride;
     const double *__restrict__ cu = S.coords + 2 * N;  // u, then v
     const double *__restrict__ cv = S.coords + 3 * N;
@@ -680,11 +667,11 @@ LinkPlan link_plan(const LinkSpec *specs, int n, Arena &a, int *rc) {
             estarts.push_back(E);
             rows.push_back(L);
             if (d == 2) {
-                T += items_before(L.nb, L.nbc);  // CTAs of kD2Chunk column blocks; no screen values
+                T += items_before<kD2Chunk>(L.nb, L.nbc);  // no screen values
                 rbstarts.push_back(RB);
                 RB += L.nb;                      // row blocks the pre-pass sorts
             } else {
-                T += L.nb * L.nbc - L.nb * (L.nb - 1) / 2;
+                T += items_before<kTileChunk>(L.nb, L.nbc);
                 nf += (int64_t)screen_floats(d) * L.N;
             }
             E += L.N;
