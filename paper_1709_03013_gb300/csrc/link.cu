@@ -126,6 +126,22 @@ __device__ __forceinline__ void st_global_32B(uint64_t *dst, uint64_t a, uint64_
     asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(dst), "l"(a), "l"(b), "l"(c), "l"(d) : "memory");
 }
 
+// Asynchronous copies of 4 or 8 bytes from global to shared memory (cp.async): `ok` false
+// copies nothing and zero-fills the destination.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool ok) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool ok) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(ok ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+
 // packed pairs of floats (f32x2): low half = first column, high half = second
 __device__ __forceinline__ uint64_t pack2(float lo, float hi) {
     uint64_t r;
@@ -303,7 +319,7 @@ __global__ void __launch_bounds__(kTile, kLinkMinBlocks)
 link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts, int n,
             const float *__restrict__ F) {
     constexpr int ND = D == 4 ? 4 : 2;             // double coordinates the exact test reads
-    __shared__ __align__(16) float cf[5][kTile];  // column screen values
+    __shared__ __align__(16) float cf[2][5][kTile];  // column screen values (two buffers)
     __shared__ double cd[ND][kTile];              // column coordinates in double
     __shared__ double rd[ND][kTile];              // row coordinates in double
     __shared__ uint64_t ow[kTileWords][kTile];    // row words: ow[q][r] = word q of tile row r
@@ -346,17 +362,31 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
 
     uint64_t *rows = S.rows;
     const int64_t stride = S.stride;
+    // Column K + r is staged by asynchronous copies (beyond N: zeros; no word reads them):
+    // the screen values of the next column block while this one is screened, the doubles
+    // (read only for the pairs inside the margin) while the screen runs.
+    auto stage_cf = [&](int64_t K, int buf) {
+        const int64_t kc = K + r;
+#pragma unroll
+        for (int a = 0; a < screen_floats(D); ++a) cp_async4(&cf[buf][a][r], Fs + a * N + (kc < N ? kc : 0), kc < N);
+        cp_async_commit();
+    };
+    stage_cf(bj0 * kTile, 0);
+    int buf = 0;
     for (int64_t bj = bj0; bj < bj1; ++bj) {
         const int64_t K = bj * kTile;
         const bool diag = (bi == bj);
-        // stage column K + r (beyond N: zeros; no word reads them)
         {
             const int64_t kc = K + r;
 #pragma unroll
-            for (int a = 0; a < screen_floats(D); ++a) cf[a][r] = kc < N ? Fs[a * N + kc] : 0.f;
-#pragma unroll
-            for (int a = 0; a < ND; ++a) cd[a][r] = kc < N ? co[a * N + kc] : 0.0;
+            for (int a = 0; a < ND; ++a) cp_async8(&cd[a][r], co + a * N + (kc < N ? kc : 0), kc < N);
+            cp_async_commit();
         }
+        if (bj + 1 < bj1)
+            stage_cf(K + kTile, buf ^ 1);
+        else
+            cp_async_commit();  // an empty group keeps the count of groups in flight fixed
+        cp_async_wait<2>();     // this block's screen values have landed
         __syncthreads();
 
         const int ncol = N - K <= 0 ? 0 : (N - K >= kTile ? kTile : (int)(N - K));
@@ -375,9 +405,11 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
         if constexpr (D == 4) {
             if (any) {
                 const float m2 = -(m + m);
-                word_packed(q, cf, a, pack2(m2, m2), A, B);
+                word_packed(q, cf[buf], a, pack2(m2, m2), A, B);
             }
         }
+        cp_async_wait<1>();  // and this block's doubles
+        __syncthreads();
 #pragma unroll
         for (int s = 0; s < kRowsPer; ++s) {
             const int rt = rfirst + 64 * s + lane;     // tile row
@@ -402,7 +434,7 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
                             wd &= ~(1ull << b);
                     }
                 } else {
-                    wd = word_by_pair_ds(q, lo + 64 * q, ncol, cf, rd, cd, rt, Fs, N, i, m);
+                    wd = word_by_pair_ds(q, lo + 64 * q, ncol, cf[buf], rd, cd, rt, Fs, N, i, m);
                 }
             }
             ow[q][rt] = wd;
@@ -429,8 +461,12 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
             if (kc < N && CSG_IN_BOUNDS(R / 64 + kTileWords <= stride, 0x31, kc))
                 st_global_32B(rows + kc * stride + R / 64, mw[0], mw[1], mw[2], mw[3]);
         }
-        __syncthreads();  // cf, cd, ow and tb are rewritten by the next column block
+        // No barrier here: the next block's copies into cd and into this cf buffer, and its
+        // writes of ow and tb, all come after a barrier that every thread reaches only once
+        // its reads of this block are done.
+        buf ^= 1;
     }
+    cp_async_wait<0>();
 }
 
 
