@@ -2,15 +2,17 @@
 // "Optimized GPU Linking Algorithm": tiles of the adjacency matrix, coordinates
 // staged in shared memory, dense output).
 //
-// d=4 and the de Sitter slab: a CTA owns a 256 x 256 tile (row block bi <= column block
-// bj) of the upper triangle.  Warp w computes the 64-column word q = w / 2 of the tile for
-// 4 x 32 rows (rows 32 (w & 1) + 64 s + lane, s = 0..3), so the column coordinates it reads from
-// shared memory are the same for all of its lanes (broadcast 16-byte loads, one load
-// per coordinate for four columns, used for four rows).  Row words are staged in shared
-// memory and written as 32-byte row segments.  The lower triangle is the same tile
-// transposed: a five-step warp-shuffle transpose per 32 x 32 block, staged in shared
-// memory and written the same way.  Column blocks run to the row stride, so every word
-// of every row -- padding included -- is written exactly once and no memset is needed.
+// d=4 and the de Sitter slab: a CTA takes up to kTileChunk 256 x 256 tiles (row block
+// bi <= column block bj) of one row block of the upper triangle, setting up the rows once
+// and staging each next column block by asynchronous copies while the current one is
+// screened.  Warp w computes the 64-column word q = w / 2 of the tile for 4 x 32 rows (rows
+// 32 (w & 1) + 64 s + lane, s = 0..3), so the column coordinates it reads from shared memory
+// are the same for all of its lanes (broadcast 16-byte loads, one load per coordinate for
+// four columns, used for four rows).  Row words are staged in shared memory and written as
+// 32-byte row segments, one store each.  The lower triangle is the same tile transposed: a
+// five-step warp-shuffle transpose per 32 x 32 block, staged in shared memory and written
+// the same way.  Column blocks run to the row stride, so every word of every row --
+// padding included -- is written exactly once and no memset is needed.
 //
 // Each pair is settled by a float screen, and the few pairs the screen cannot settle are
 // decided exactly in double, so the bitmap equals the one of the exact (IEEE double)
@@ -58,7 +60,7 @@ namespace {
 constexpr int kTile = 256;      // rows and columns per tile
 constexpr int kTileWords = 4;   // 64-bit words per tile row
 constexpr int kRowsPer = 4;     // rows per thread (one 64-column word each)
-constexpr int kLinkMinBlocks = 4;  // resident CTAs per SM the register budget allows
+constexpr int kLinkMinBlocks = 3;  // resident CTAs per SM of the tile kernel (80 registers)
 constexpr int kTileChunk = 4;      // column blocks per CTA of the tile kernel (d=4, de Sitter)
 constexpr int kD2Chunk = 16;       // column blocks per CTA of the d=2 kernel
 
