@@ -206,8 +206,15 @@ __global__ void sprinkle_keys_kernel(const SetRow *__restrict__ sets, const int6
                 g = next + __popc(dm & below);
                 a = 0;
                 if (g < r1) {
-                    s = find_set(starts, n, g);
-                    S = sets[s];
+                    // a lane's elements only move forward: step over at most four set
+                    // boundaries, else search
+                    int s2 = s;
+                    for (int k = 0; k < 4 && s2 + 1 < n && starts[s2 + 1] <= g; ++k) ++s2;
+                    if (s2 + 1 < n && starts[s2 + 1] <= g) s2 = find_set(starts, n, g);
+                    if (s2 != s) {
+                        s = s2;
+                        S = sets[s];
+                    }
                 }
             }
             next += __popc(dm);
