@@ -13,9 +13,10 @@
 // above the largest interval (N - 2 <= 2^18).  The result is converted back to an
 // integer before it is used, so the counts are bit-exact in either format.
 //
-// Pass 1 (expand): one warp per operand row, one lane per packed word, writes the operand
-// bytes of U and of P the word covers (64 fp8 bytes or 32 fp4 bytes each); only the column
-// ranges the product reads are written.
+// Pass 1 (expand): one warp per operand row (per group of four consecutive rows in a batch
+// of many sets), one lane per packed word, writes the operand bytes of U and of P the word
+// covers (64 fp8 bytes or 32 fp4 bytes each); only the column ranges the product reads are
+// written.
 // Pass 2 (product): persistent CTA pairs (clusters of two CTAs, one per SM) take pair tiles
 // (256 rows i x 256 columns j, upper triangle only, K from the first row of the tile to its
 // last column) from a global work queue: the leader CTA claims each tile with an atomic
@@ -148,52 +149,59 @@ __device__ __forceinline__ void put64(uint8_t *dst, uint64_t m) {
     }
 }
 
-// One warp per operand row of the sets [set_lo, set_lo + nset) (rows numbered across the
-// sets, rstarts[s] = first row of set s): the lanes walk the row's words and write the
+// Warps take groups of `group` consecutive operand rows of the sets [set_lo, set_lo + nset)
+// (rows numbered across the sets, rstarts[s] = first row of set s; a set lookup per group,
+// then a step forward at set boundaries; groups of four pay off for batches of many sets):
+// the lanes walk the row's words and write the
 // operand bytes (64 fp8 bytes or 32 packed fp4 bytes per word) where the product reads them:
 // U row i from the first column of its pair tile, 2*BM*floor(i/(2*BM)) (a whole number of
 // stages in either format), P row i up to column BN*(floor(i/BN)+1).
 // FMT 0: fp8 e4m3, 128 elements per stage; FMT 1: fp4 e2m1, 256.
 template <int FMT>
 __global__ void expand_kernel(const TcSetDesc *__restrict__ sets, const int64_t *__restrict__ rstarts,
-                              int set_lo, int nset, int64_t total_rows) {
+                              int set_lo, int nset, int64_t total_rows, int group) {
     const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t gr = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); gr < total_rows; gr += warps) {
-        const int ls = find_set(rstarts, nset, gr);  // warp-uniform
-        const TcSetDesc &S = sets[set_lo + ls];
-        const int64_t i = gr - rstarts[ls];
-        const int64_t wpr = (FMT ? 2 * S.kp : S.kp) / 64;  // words per operand row
-        const uint64_t *__restrict__ row = S.rows + i * S.stride;
-        uint8_t *__restrict__ urow = S.U + i * S.kp;
-        uint8_t *__restrict__ prow = S.P + i * S.kp;
-        const int64_t u0 = (i / (2 * BM)) * (2 * BM) / 64;                  // first U word read
-        const int64_t p1 = min(wpr, (i / BN + 1) * BN / 64);                // P words read: [0, p1)
-        for (int64_t w = u0 + lane; w < wpr; w += 32) {
-            const int64_t k0 = w * 64;
-            uint64_t m = CSG_IN_BOUNDS(w < S.stride, 0x20, w) ? __ldg(row + w) : 0ull;
-            if (k0 + 63 <= i)
-                m = 0;
-            else if (k0 <= i)
-                m &= ~((2ull << (i - k0)) - 1ull);  // keep k > i
-            if (!CSG_IN_BOUNDS(i < S.N && (FMT ? k0 / 2 + 32 : k0 + 64) <= S.kp, 0x21, w)) continue;
-            if (FMT)
-                put64_fp4(urow + k0 / 2, m);
-            else
-                put64(urow + k0, m);
-        }
-        for (int64_t w = lane; w < p1; w += 32) {
-            const int64_t k0 = w * 64;
-            uint64_t m = CSG_IN_BOUNDS(w < S.stride, 0x20, w) ? __ldg(row + w) : 0ull;
-            if (k0 >= i)
-                m = 0;
-            else if (k0 + 63 >= i)
-                m &= (1ull << (i - k0)) - 1ull;  // keep k < i
-            if (!CSG_IN_BOUNDS(i < S.N && (FMT ? k0 / 2 + 32 : k0 + 64) <= S.kp, 0x21, w)) continue;
-            if (FMT)
-                put64_fp4(prow + k0 / 2, m);
-            else
-                put64(prow + k0, m);
+    const int64_t step = (int64_t)gridDim.x * (blockDim.x >> 5) * group;
+    for (int64_t g0 = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * group; g0 < total_rows;
+         g0 += step) {
+        int ls = find_set(rstarts, nset, g0);  // warp-uniform
+        const int64_t g1 = min(g0 + group, total_rows);
+        for (int64_t gr = g0; gr < g1; ++gr) {
+            while (ls + 1 < nset && rstarts[ls + 1] <= gr) ++ls;  // sets without rows are stepped over
+            const TcSetDesc &S = sets[set_lo + ls];
+            const int64_t i = gr - rstarts[ls];
+            const int64_t wpr = (FMT ? 2 * S.kp : S.kp) / 64;  // words per operand row
+            const uint64_t *__restrict__ row = S.rows + i * S.stride;
+            uint8_t *__restrict__ urow = S.U + i * S.kp;
+            uint8_t *__restrict__ prow = S.P + i * S.kp;
+            const int64_t u0 = (i / (2 * BM)) * (2 * BM) / 64;                  // first U word read
+            const int64_t p1 = min(wpr, (i / BN + 1) * BN / 64);                // P words read: [0, p1)
+            for (int64_t w = u0 + lane; w < wpr; w += 32) {
+                const int64_t k0 = w * 64;
+                uint64_t m = CSG_IN_BOUNDS(w < S.stride, 0x20, w) ? __ldg(row + w) : 0ull;
+                if (k0 + 63 <= i)
+                    m = 0;
+                else if (k0 <= i)
+                    m &= ~((2ull << (i - k0)) - 1ull);  // keep k > i
+                if (!CSG_IN_BOUNDS(i < S.N && (FMT ? k0 / 2 + 32 : k0 + 64) <= S.kp, 0x21, w)) continue;
+                if (FMT)
+                    put64_fp4(urow + k0 / 2, m);
+                else
+                    put64(urow + k0, m);
+            }
+            for (int64_t w = lane; w < p1; w += 32) {
+                const int64_t k0 = w * 64;
+                uint64_t m = CSG_IN_BOUNDS(w < S.stride, 0x20, w) ? __ldg(row + w) : 0ull;
+                if (k0 >= i)
+                    m = 0;
+                else if (k0 + 63 >= i)
+                    m &= (1ull << (i - k0)) - 1ull;  // keep k < i
+                if (!CSG_IN_BOUNDS(i < S.N && (FMT ? k0 / 2 + 32 : k0 + 64) <= S.kp, 0x21, w)) continue;
+                if (FMT)
+                    put64_fp4(prow + k0 / 2, m);
+                else
+                    put64(prow + k0, m);
+            }
         }
     }
 }
@@ -1105,10 +1113,12 @@ static int tc_launch_fmt(const TcPlan &p, const Arena &a, cudaStream_t st) {
     for (size_t ci = 0; ci < p.chunks.size(); ++ci) {
         const TcPlan::Chunk &c = p.chunks[ci];
         if (c.rows > 0) {
-            const int blocks = (int)std::min<int64_t>((c.rows + 7) / 8, (int64_t)sms * 16);  // a warp per row
+            const int group = c.set_hi - c.set_lo > 1 ? 4 : 1;  // rows per warp and step
+            const int64_t groups = (c.rows + group - 1) / group;
+            const int blocks = (int)std::min<int64_t>((groups + 7) / 8, (int64_t)sms * 16);
             stage_begin(CSG_STAGE_EXPAND, st);
             expand_kernel<FMT><<<blocks, 256, 0, st>>>(d_sets, a.tab<int64_t>(c.t_rstarts), c.set_lo,
-                                                       c.set_hi - c.set_lo, c.rows);
+                                                       c.set_hi - c.set_lo, c.rows, group);
             stage_end(CSG_STAGE_EXPAND, st);
         }
         if (c.n_tiles > 0) {
