@@ -186,3 +186,34 @@ def test_desitter_screen_margin(eta0, seed):
     assert not ((diff > m) & ~r).any()
     assert not ((diff < -m) & r).any()
     assert (np.abs(diff) <= m).sum() <= 0.01 * r.size
+
+
+@pytest.mark.parametrize("C", [4, 16])
+def test_link_work_items_cover_the_upper_triangle_once(C):
+    # A link CTA takes up to C consecutive column blocks of one row block (C = 4 for the
+    # d=4 and de Sitter tile kernel, 16 for d=2): CTA t of a set is decoded with the closed
+    # form sum_{n=1}^{M} ceil(n / C) = C a (a + 1) / 2 + r (a + 1), M = a C + r.  Every tile
+    # bi <= bj < nbc must be visited exactly once, for row blocks nb <= nbc.
+    def ceil_sum(M):
+        a, r = divmod(M, C)
+        return C * a * (a + 1) // 2 + r * (a + 1)
+
+    def items_before(b, nbc):
+        return ceil_sum(nbc) - ceil_sum(nbc - b)
+
+    for nbc in list(range(1, 40)) + [160, 512]:
+        for nb in sorted({0, 1, nbc // 3, nbc - 1, nbc}):
+            seen = set()
+            for t in range(items_before(nb, nbc)):
+                lo, hi = 0, nb - 1
+                while lo < hi:
+                    mid = (lo + hi + 1) >> 1
+                    if items_before(mid, nbc) <= t:
+                        lo = mid
+                    else:
+                        hi = mid - 1
+                bj0 = lo + (t - items_before(lo, nbc)) * C
+                for bj in range(bj0, min(bj0 + C, nbc)):
+                    assert (lo, bj) not in seen
+                    seen.add((lo, bj))
+            assert seen == {(a, b) for a in range(nb) for b in range(a, nbc)}
