@@ -491,8 +491,9 @@ link_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ starts
 // decision is the exact double one, on the integer pipe rather than the few FP64 units; ties
 // are no special case (equal values are not less), and padding rows carry the largest key,
 // which no finite coordinate reaches.  A pair i < k always has i earlier in the time order
-// (t is (u + v) / 2, its ties broken by u), so no mask is needed within the diagonal block,
-// whose row words and mirrored words are ORed.
+// (t is (u + v) / 2, its ties broken by u); the diagonal block, whose row words and mirrored
+// words are ORed, still keeps only rows before each column, as the tile kernel does, so a
+// caller's set with some other t gets the same matrix from both.
 // One row block in u (g = 0) and v (g = 1) order: tree[g][j], j = 1..255, the search tree
 // of the first 255 sorted keys (node j holds the key of in-order rank tree_rank(j)),
 // tree[g][0] the largest key; idx[g][q] the tile row of sorted position q.
@@ -631,6 +632,14 @@ link_d2_kernel(const LinkRow *__restrict__ sets, const int64_t *__restrict__ sta
             const int pu = count_below(blk.tree[0], lastu, xu), pv = count_below(blk.tree[1], lastv, xv);
 #pragma unroll
             for (int w = 0; w < kTileWords; ++w) cm[w] = pre[0][w][pu] & pre[1][w][pv];
+            if (bj == bi) {
+                // within the diagonal block only the rows before the column count, as the
+                // other tiles see only later columns (for coordinates whose t is (u + v) / 2
+                // this removes nothing)
+#pragma unroll
+                for (int w = 0; w < kTileWords; ++w)
+                    cm[w] &= r >= 64 * w + 64 ? ~0ull : (r <= 64 * w ? 0ull : (1ull << (r - 64 * w)) - 1ull);
+            }
         }
         const int64_t kcur = kc;
         kc += kTile;  // the next column block's coordinates, loaded during the transpose

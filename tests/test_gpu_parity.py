@@ -171,6 +171,23 @@ def test_d2_link_on_few_distinct_values(ctx, N):
     s.free()
 
 
+def test_d2_link_with_a_caller_time_order(ctx):
+    """A caller's d=2 set whose t is not (u + v) / 2: the elements are ordered by that t, and
+    the matrix, like the oracle's, relates each pair by u and v in that order only (i before
+    k and u_i < u_k, v_i < v_k), inside the diagonal blocks as everywhere else."""
+    rng = np.random.default_rng(321)
+    N = 1300
+    u, v = rng.random(N), rng.random(N)
+    c = np.stack([rng.random(N), (v - u) / 2, u, v])
+    s = ctx.set_from_coords(2, c)
+    sorted_c, _ = oracle.sort(2, c)
+    assert np.array_equal(s.coords(), sorted_c)
+    s.link()
+    rel = oracle.link(2, sorted_c)
+    assert np.array_equal(s.bitmap(), oracle.pack(rel, s.info()["stride"]))
+    s.free()
+
+
 @pytest.mark.parametrize("method", [0, 1])
 @pytest.mark.parametrize("d,N", [(2, 3000), (4, 4100)])
 def test_action_rows(ctx, d, N, method):
