@@ -12,8 +12,10 @@ Prints ONE JSON line (rank 0).  `value` is related-pair interval counts per seco
 through the public API from host coordinates (copied in every step) to the host
 result.  `roofline` is the action kernel of the chosen method (default: the tensor-core
 form with fp4 operands, against the fp4 tensor peak; the popcount form against the
-integer-pipe popcount peak is reported beside it, and the link kernel against the fp32
-pipe for d=4 and HBM write bandwidth for d=2); `cpu_baseline` is the CPU oracle on a
+integer-pipe popcount peak is reported beside it, the tensor form's operand feed against
+the per-SM L2-to-shared-memory rate a probe measures in the run (`roofline_tc_feed`), and
+the link kernel against the fp32 pipe for d=4 and HBM write bandwidth for d=2);
+`cpu_baseline` is the CPU oracle on a
 bounded, stratified sample of the same workload (the same measurement as
 `--impl reference`).  `batch` compares the batched (CUDA-graph) path with
 one-set-at-a-time calls on 4096 mixed diamonds, and `serve` gives p50/p99 latency of the
@@ -840,6 +842,21 @@ def main():
                "kernel_ms": tc_ms,
                "peak_basis": (f"{'fp4 = 6' if fp4 else 'fp8 = 2'} x measured bf16 dense burst "
                               "(MEASURED_PEAKS.json; nominal dense ratio), of measured")}
+    # the tensor form's second bound: the operand feed from L2 into shared memory, against
+    # the per-SM rate a bulk-copy probe sustains (measured live).  Tile (I, J) of the pair
+    # streams K = [256 I, 256 (J + 1)) in 32 KB stages per CTA (256 elements of K in fp4, 128
+    # in fp8) and one 4 KB slot of relation words per CTA.
+    feed_rate = csg.measure_l2_feed(local)                          # bytes per SM per second
+    nb = (N + 255) // 256
+    pair_stages = (256 // (256 if fp4 else 128)) * nb * (nb + 1) * (nb + 2) // 6
+    feed_bytes = pair_stages * 2 * 32768 + nb * (nb + 1) // 2 * 2 * 4096
+    feed_ach = feed_bytes / SMS / (tc_ms / 1e3)
+    feed_roof = {"bound": "l2_to_smem", "achieved": feed_ach / 1e9, "peak": feed_rate / 1e9,
+                 "unit": "GB/s per SM", "frac": feed_ach / feed_rate, "kernel_ms": tc_ms,
+                 "bytes_per_launch": feed_bytes,
+                 "peak_basis": "csg_measure_l2_feed: the kernel's copies (2D tensor-map loads, 128 rows x "
+                               "128 B, 128-byte swizzle), six 32 KB stages in flight per SM, all SMs pulling "
+                               "from an L2-resident matrix, measured in this run"}
     # link: d=4 against the fp32 pipe its screen runs on (the expanded interval of each pair
     # i < k as one add and four fused multiply-adds, and the margin's second sign: 10 flops a
     # pair), d=2 against HBM bandwidth for the bitmap it writes (every word once)
@@ -873,6 +890,7 @@ def main():
         "bitops_per_s": res.W / (act_ms / 1e3),
         "roofline": tc_roof if is_tc else popc_roof,
         "roofline_other_method": popc_roof if is_tc else tc_roof,
+        "roofline_tc_feed": feed_roof,
         "roofline_link": link_roof,
         "e2e": {"value": e_pairs / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(host_np.nbytes),
                 "d2h_bytes_per_step": 88},

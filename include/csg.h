@@ -288,6 +288,15 @@ int csg_check_words(uint64_t *words, int n);
  * device. */
 int csg_measure_popc_rate(int device, double *popc_per_second);
 
+/* Throughput probe of the operand feed from L2 into shared memory, the second bound of the
+ * tensor-core interval counts (each SM of a CTA pair stages 32 KB of operands per 256-deep K
+ * step).  One CTA per SM keeps six 32 KB stages in flight, each two 2D tensor-map loads of
+ * 128 rows x 128 bytes with 128-byte swizzle (the tensor kernel's kind of copy), from a 32 MB
+ * matrix that stays in L2; *bytes_per_sm_per_second receives the bytes one SM receives per
+ * second with every SM pulling at once.  Allocates and frees the matrix; synchronises the
+ * device; every device wait is bounded (CSG_E_TIMEOUT if one runs out). */
+int csg_measure_l2_feed(int device, double *bytes_per_sm_per_second);
+
 /* Failure injection for tests of the error paths (not for production use; process-wide,
  * off by default).  No GPU faults, traps or hangs in either: the failures are made on the
  * host or by a wait that nothing completes, and every device wait is bounded.

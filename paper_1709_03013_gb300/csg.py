@@ -86,7 +86,7 @@ EXPORTS = [
     "csg_serve_cancel", "csg_export_coords", "csg_export_bitmap", "csg_set_info", "csg_set_free",
     "csg_action_noalloc", "csg_set_timing", "csg_stage_times", "csg_action_smeared",
     "csg_sprinkle_desitter", "csg_dalembertian", "csg_test_wait_expiry", "csg_test_fail_alloc",
-    "csg_measure_popc_rate", "csg_check_words",
+    "csg_measure_popc_rate", "csg_measure_l2_feed", "csg_check_words",
 ]
 
 _lib = None
@@ -134,6 +134,7 @@ def load(path: str = LIB_PATH):
         "csg_test_wait_expiry": (i32, [u64, i32]),
         "csg_test_fail_alloc": (i32, [i32]),
         "csg_measure_popc_rate": (i32, [i32, ctypes.POINTER(ctypes.c_double)]),
+        "csg_measure_l2_feed": (i32, [i32, ctypes.POINTER(ctypes.c_double)]),
         "csg_check_words": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
@@ -208,6 +209,13 @@ def measure_popc_rate(device: int = 0) -> float:
     """Sustained 32-bit popcounts per second of the whole GPU (csg_measure_popc_rate)."""
     v = ctypes.c_double()
     _check(load().csg_measure_popc_rate(device, ctypes.byref(v)), "csg_measure_popc_rate")
+    return v.value
+
+
+def measure_l2_feed(device: int = 0) -> float:
+    """Bytes per second one SM receives from L2 into shared memory (csg_measure_l2_feed)."""
+    v = ctypes.c_double()
+    _check(load().csg_measure_l2_feed(device, ctypes.byref(v)), "csg_measure_l2_feed")
     return v.value
 
 

@@ -553,3 +553,12 @@ def test_popc_pipe_probe_rate(csg):
     per_sm = rate / sms
     # 12 to 17 results per SM per clock at a clock between 1.4 and 2.1 GHz
     assert 12 * 1.4e9 < per_sm < 17 * 2.1e9, per_sm
+
+
+def test_l2_feed_probe_rate(csg):
+    """The tensor form's second roofline: bytes per SM per second from L2 into shared memory
+    through swizzled 2D tensor-map loads with six 32 KB stages in flight on every SM (about
+    68 bytes per clock on this GPU)."""
+    rate = csg.measure_l2_feed(0)
+    # 40 to 80 bytes per SM per clock at a clock between 1.4 and 2.1 GHz
+    assert 40 * 1.4e9 < rate < 80 * 2.1e9, rate
