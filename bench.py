@@ -846,17 +846,23 @@ def main():
     # the per-SM rate a bulk-copy probe sustains (measured live).  Tile (I, J) of the pair
     # streams K = [256 I, 256 (J + 1)) in 32 KB stages per CTA (256 elements of K in fp4, 128
     # in fp8) and one 4 KB slot of relation words per CTA.
-    feed_rate = csg.measure_l2_feed(local)                          # bytes per SM per second
+    try:
+        feed_rate = csg.measure_l2_feed(local)                      # bytes per SM per second
+    except csg.CsgError as exc:
+        feed_rate, feed_err = None, str(exc)
     nb = (N + 255) // 256
     pair_stages = (256 // (256 if fp4 else 128)) * nb * (nb + 1) * (nb + 2) // 6
     feed_bytes = pair_stages * 2 * 32768 + nb * (nb + 1) // 2 * 2 * 4096
     feed_ach = feed_bytes / SMS / (tc_ms / 1e3)
-    feed_roof = {"bound": "l2_to_smem", "achieved": feed_ach / 1e9, "peak": feed_rate / 1e9,
-                 "unit": "GB/s per SM", "frac": feed_ach / feed_rate, "kernel_ms": tc_ms,
+    feed_roof = {"bound": "l2_to_smem", "achieved": feed_ach / 1e9,
+                 "peak": feed_rate / 1e9 if feed_rate else None,
+                 "unit": "GB/s per SM", "frac": feed_ach / feed_rate if feed_rate else None, "kernel_ms": tc_ms,
                  "bytes_per_launch": feed_bytes,
                  "peak_basis": "csg_measure_l2_feed: the kernel's copies (2D tensor-map loads, 128 rows x "
                                "128 B, 128-byte swizzle), six 32 KB stages in flight per SM, all SMs pulling "
                                "from an L2-resident matrix, measured in this run"}
+    if feed_rate is None:
+        feed_roof["probe_error"] = feed_err
     # link: d=4 against the fp32 pipe its screen runs on (the expanded interval of each pair
     # i < k as one add and four fused multiply-adds, and the margin's second sign: 10 flops a
     # pair), d=2 against HBM bandwidth for the bitmap it writes (every word once)
