@@ -372,6 +372,23 @@ def test_desitter_slab(ctx, csg, N):
     s.free()
 
 
+def test_desitter_slab_at_the_distribution_size(ctx, csg):
+    """The slab of the interval-abundance experiment (Sec. 5.2, N = 2^15, eta0 = 0.5): the
+    whole bitmap (128 row blocks, many CTAs of the chunked tile kernel) equals the oracle's
+    link of the GPU's coordinates, and both interval-count kernels agree on every count."""
+    N, eta0 = 2 ** 15, 0.5
+    s = ctx.sprinkle_desitter(N, eta0, 5, 0).link()
+    got_c = s.coords()
+    rel = oracle.link(oracle.DS2, got_c)
+    assert np.array_equal(s.bitmap(), oracle.pack(rel, s.info()["stride"]))
+    R = int(rel.sum(dtype=np.int64)) // 2  # symmetric, zero diagonal
+    del rel
+    a, b = s.action(csg.POPC), s.action(csg.TC)
+    assert (a.R, list(a.Nk), a.sum_m, a.W) == (b.R, list(b.Nk), b.sum_m, b.W)
+    assert a.R == R and a.status == 0 and b.status == 0
+    s.free()
+
+
 # ------------------------------------------------------------ d'Alembertian (Eq. b_local)
 
 def _dalembert_tol(phi, L, l):
