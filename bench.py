@@ -13,7 +13,8 @@ through the public API from host coordinates (copied in every step) to the host
 result.  `roofline` is the action kernel of the chosen method (default: the tensor-core
 form with fp4 operands, against the fp4 tensor peak; the popcount form against the
 integer-pipe popcount peak is reported beside it, the tensor form's operand feed against
-the per-SM L2-to-shared-memory rate a probe measures in the run (`roofline_tc_feed`), and
+the per-SM L2-to-shared-memory rate a probe measures in the run (`roofline_tc_feed`), the
+tensor rate also against the pair MMA's own rate on resident operands (`mma_probe_tflops`), and
 the link kernel against the fp32 pipe for d=4 and HBM write bandwidth for d=2);
 `cpu_baseline` is the CPU oracle on a
 bounded, stratified sample of the same workload (the same measurement as
@@ -835,8 +836,13 @@ def main():
                                 f"{sm_max:.0f} MHz"),
                  "popc_probe_per_sm_clk": popc_rate / SMS / (sm_max * 1e6)}
     tc_ach = tc_flops / (tc_ms / 1e3) / 1e12
+    try:  # the pair MMA itself on resident operands, measured live (beside the contract's peak)
+        mma_probe = csg.measure_mma_rate(csg.TC_FP4 if fp4 else csg.TC_FP8, local) / 1e12
+    except csg.CsgError:
+        mma_probe = None
     tc_roof = {"bound": "tensor", "achieved": tc_ach, "peak": tc_peak, "unit": "TFLOP/s",
                "frac": tc_ach / tc_peak,
+               "mma_probe_tflops": mma_probe, "frac_of_mma_probe": tc_ach / mma_probe if mma_probe else None,
                "traffic": recorded_traffic(f"action_tc_kernel<{1 if fp4 else 0}>", f"d={d} N={N} seed {seed}"),
                "traffic_basis": TRAFFIC_BASIS,
                "kernel_ms": tc_ms,

@@ -297,6 +297,15 @@ int csg_measure_popc_rate(int device, double *popc_per_second);
  * device; every device wait is bounded (CSG_E_TIMEOUT if one runs out). */
 int csg_measure_l2_feed(int device, double *bytes_per_sm_per_second);
 
+/* Throughput probe of the tensor cores as the interval counts use them: the same 2-SM MMA
+ * (tcgen05.mma.cta_group::2, M = 256, N = 256; method CSG_TC or CSG_TC_FP4: kind::mxf4 with
+ * unit block scales, CSG_TC_FP8: kind::f8f6f4), instruction descriptor and TMEM layout as the
+ * product kernel, issued back to back on operands resident in shared memory by one CTA pair
+ * per two SMs.  *flops_per_second receives the whole GPU's rate (2 flops per product).
+ * Synchronises the device; every device wait is bounded (CSG_E_TIMEOUT if one runs out);
+ * CSG_E_INVAL for another method. */
+int csg_measure_mma_rate(int device, int method, double *flops_per_second);
+
 /* Failure injection for tests of the error paths (not for production use; process-wide,
  * off by default).  No GPU faults, traps or hangs in either: the failures are made on the
  * host or by a wait that nothing completes, and every device wait is bounded.

@@ -86,7 +86,7 @@ EXPORTS = [
     "csg_serve_cancel", "csg_export_coords", "csg_export_bitmap", "csg_set_info", "csg_set_free",
     "csg_action_noalloc", "csg_set_timing", "csg_stage_times", "csg_action_smeared",
     "csg_sprinkle_desitter", "csg_dalembertian", "csg_test_wait_expiry", "csg_test_fail_alloc",
-    "csg_measure_popc_rate", "csg_measure_l2_feed", "csg_check_words",
+    "csg_measure_popc_rate", "csg_measure_l2_feed", "csg_measure_mma_rate", "csg_check_words",
 ]
 
 _lib = None
@@ -135,6 +135,7 @@ def load(path: str = LIB_PATH):
         "csg_test_fail_alloc": (i32, [i32]),
         "csg_measure_popc_rate": (i32, [i32, ctypes.POINTER(ctypes.c_double)]),
         "csg_measure_l2_feed": (i32, [i32, ctypes.POINTER(ctypes.c_double)]),
+        "csg_measure_mma_rate": (i32, [i32, i32, ctypes.POINTER(ctypes.c_double)]),
         "csg_check_words": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
@@ -209,6 +210,14 @@ def measure_popc_rate(device: int = 0) -> float:
     """Sustained 32-bit popcounts per second of the whole GPU (csg_measure_popc_rate)."""
     v = ctypes.c_double()
     _check(load().csg_measure_popc_rate(device, ctypes.byref(v)), "csg_measure_popc_rate")
+    return v.value
+
+
+def measure_mma_rate(method: int = TC, device: int = 0) -> float:
+    """Flops per second of the pair MMA the tensor method issues, on resident operands
+    (csg_measure_mma_rate)."""
+    v = ctypes.c_double()
+    _check(load().csg_measure_mma_rate(device, method, ctypes.byref(v)), "csg_measure_mma_rate")
     return v.value
 
 

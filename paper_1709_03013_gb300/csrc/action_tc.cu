@@ -854,6 +854,85 @@ action_tc_kernel(const TcArgs args) {
     }
 }
 
+// ------------------------------------------------------------------ MMA rate probe
+
+// Throughput probe of the pair MMA the product issues: the same instruction, instruction
+// descriptor, TMEM layout (accumulator at column 0; the fp4 form's unit scale factors at
+// columns 256 and 384) and shared-memory descriptors, on one 32 KB stage of zeros resident in
+// each CTA's shared memory.  The leader issues `iters` groups of four MMAs (one 128-byte K
+// stage) back to back and commits once; both CTAs wait for that commit (bounded) before
+// freeing TMEM.  One CTA per SM (the dynamic shared memory is sized for it).
+constexpr int PROBE_THREADS = 192;
+
+template <int FMT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PROBE_THREADS, 1)
+mma_probe_kernel(int iters, uint64_t limit, unsigned long long *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *done = reinterpret_cast<uint64_t *>(base + STAGE_BYTES);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    const uint32_t rank = cluster_rank();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = threadIdx.x; q < STAGE_BYTES / 16; q += PROBE_THREADS)
+        reinterpret_cast<uint4 *>(base)[q] = make_uint4(0u, 0u, 0u, 0u);
+    ptx::fence_proxy_async_smem();  // the zeros are visible to the tensor cores
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(done, 1);
+        ptx::fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         ptx::smem_addr(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    if (FMT && warp >= 2 && warp < 6) {
+        const uint32_t one4 = 0x7F7F7F7Fu;  // scale factors 1.0 in columns 256..511
+        for (uint32_t c = 256; c < TMEM_COLS; c += 32) {
+            const uint32_t addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + c;
+            asm volatile(
+                "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+                "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(addr),
+                "r"(one4)
+                : "memory");
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();  // both CTAs' operands, barrier and scale factors exist
+    tc_fence_after();
+    if (rank == 0 && warp == 1 && lane == 0) {
+        const uint32_t sa = ptx::smem_addr(base);
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < BKB / 32; ++k) {
+                const uint64_t ad = smem_desc_sw128(sa + 32 * k);
+                const uint64_t bd = smem_desc_sw128(sa + A_BYTES + 32 * k);
+                if (FMT)
+                    mma_f4(tmem, ad, bd, tmem + kSfA, tmem + kSfB, (it > 0 || k > 0) ? 1u : 0u);
+                else
+                    mma_f8(tmem, ad, bd, (it > 0 || k > 0) ? 1u : 0u);
+            }
+        }
+        mma_commit_pair(done);  // arrives in both CTAs once every MMA has completed
+    }
+    if (warp == 1 && lane == 0 && !mbar_wait_cl(done, 0u, limit)) atomicAdd(err, 1ull);
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();  // neither CTA frees TMEM while the other's MMAs may still write it
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
 // ------------------------------------------------------------------ host side
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
@@ -1147,3 +1226,78 @@ int tc_launch(const TcPlan &p, const Arena &a, cudaStream_t st) {
 }
 
 }  // namespace csg
+
+namespace csg {
+namespace {
+
+template <int FMT>
+int measure_mma_rate(int device, double *flops_per_second) {
+    CSG_CUDA_TRY(cudaSetDevice(device));
+    int sms = 0;
+    CSG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    const int smem = 200 * 1024;  // one CTA per SM, as the product kernel
+    CSG_CUDA_TRY(cudaFuncSetAttribute(mma_probe_kernel<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int pairs = sms / 2;
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * pairs);
+        cfg.blockDim = dim3(PROBE_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, (const void *)mma_probe_kernel<FMT>, &cfg) == cudaSuccess &&
+            clusters > 0 && clusters < pairs)
+            pairs = clusters;
+        cudaGetLastError();
+    }
+    unsigned long long *err = nullptr;
+    if (dev_malloc((void **)&err, 8) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("csg_measure_mma_rate: allocation failed");
+        return CSG_E_NOMEM;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = CSG_OK;
+    float ms = 0.f;
+    unsigned long long h_err = 0;
+    const int iters = 20000;
+    if (cudaMemset(err, 0, 8) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess)
+        rc = CSG_E_CUDA;
+    if (rc == CSG_OK) {
+        const uint64_t limit = wait_limit_ns(kWaitNs);
+        mma_probe_kernel<FMT><<<2 * pairs, PROBE_THREADS, smem>>>(200, limit, err);  // warm-up
+        cudaEventRecord(e0);
+        mma_probe_kernel<FMT><<<2 * pairs, PROBE_THREADS, smem>>>(iters, limit, err);
+        cudaEventRecord(e1);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || ms <= 0.f ||
+            cudaMemcpy(&h_err, err, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = CSG_E_CUDA;
+        else if (h_err != 0)
+            rc = CSG_E_TIMEOUT;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(err);
+    if (rc != CSG_OK) {
+        set_error(rc == CSG_E_TIMEOUT ? "csg_measure_mma_rate: a bounded wait expired"
+                                      : "csg_measure_mma_rate: the probe failed");
+        return rc;
+    }
+    // each MMA: M = 256 rows x N = 256 columns x K = 64 fp4 or 32 fp8 elements, 2 flops a product
+    const double per_mma = 2.0 * (2 * BM) * BN * (FMT ? 64 : 32);
+    *flops_per_second = (double)pairs * iters * (BKB / 32) * per_mma / (ms * 1e-3);
+    return CSG_OK;
+}
+
+}  // namespace
+}  // namespace csg
+
+extern "C" int csg_measure_mma_rate(int device, int method, double *flops_per_second) {
+    if (device < 0 || !flops_per_second || (method != CSG_TC && method != CSG_TC_FP4 && method != CSG_TC_FP8)) {
+        csg::set_error("csg_measure_mma_rate: bad arguments");
+        return CSG_E_INVAL;
+    }
+    return method == CSG_TC_FP8 ? csg::measure_mma_rate<0>(device, flops_per_second)
+                                : csg::measure_mma_rate<1>(device, flops_per_second);
+}

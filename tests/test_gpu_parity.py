@@ -572,6 +572,18 @@ def test_popc_pipe_probe_rate(csg):
     assert 12 * 1.4e9 < per_sm < 17 * 2.1e9, per_sm
 
 
+def test_mma_probe_rate(csg):
+    """The pair MMA on resident operands: fp4 (kind::mxf4) at about twice the fp8 rate
+    (kind::f8f6f4; on this GPU it reaches about 4.85 PFLOP/s at 2.07 GHz, a little above the
+    nominal dense 4.5), below the nominal dense fp4 peak of 13.5 PFLOP/s; a non-tensor
+    method is rejected."""
+    f4, f8 = csg.measure_mma_rate(csg.TC_FP4, 0), csg.measure_mma_rate(csg.TC_FP8, 0)
+    assert 4e15 < f4 < 13.5e15 and 2e15 < f8 < 6e15, (f4, f8)
+    assert 1.6 < f4 / f8 < 2.4
+    with pytest.raises(csg.CsgError):
+        csg.measure_mma_rate(csg.POPC, 0)
+
+
 def test_l2_feed_probe_rate(csg):
     """The tensor form's second roofline: bytes per SM per second from L2 into shared memory
     through swizzled 2D tensor-map loads with six 32 KB stages in flight on every SM (about
